@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Benchmark of the checkerboard local-update sweep on one GB300 (or N, as
+independent replicas).
+
+Workload (one "step" = one Metropolis sweep, with E and M measured, of every
+chain): the multi-spin-coded 2D Ising batch L in {1024, 4096, 16384} x
+beta in {0.30, 0.40, 0.4406868, 0.50, 0.60}, periodic, hot start, 15 chains;
+rank r runs the same 15 lattices with its own chain ids (weak scaling, no
+data-path collective: chains are independent).  value = attempted spin flips
+per second over all ranks.  The SU(2) heat-bath on 32^4 at beta in
+{1.5, 2.0, 2.3, 2.6} is timed in the same run and reported under "components".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+The reference arm times the CPU oracle (oracle/, plain C, one core) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Ising spin-flips/s, SU(2) link-updates/s, eff. samples/s at beta_c vs plain"
+BETAS = [0.30, 0.40, 0.4406868, 0.50, 0.60]
+SIZES = [1024, 4096, 16384]
+SU2_BETAS = [1.5, 2.0, 2.3, 2.6]
+SU2_L = 32
+# Algorithmic integer operations per attempted flip in the MSC half-sweep: a
+# quarter of a Philox4x32-10 block (10 rounds x [2 wide multiplies + 2
+# three-input xors]) = 10, one threshold compare + insert = 2, and the
+# bit-sliced neighbour count, flip and measurement logic (~30 per 32-spin word)
+# ~ 1.
+ALU_OPS_PER_FLIP = 13.0
+# Lane-instruction issue rate of a GB300: 152 SMs x 4 schedulers x 32 lanes at
+# the 2070 MHz maximum SM clock.
+SM_COUNT, ISSUE_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+ALU_PEAK_OPS = SM_COUNT * ISSUE_LANES_PER_SM * SM_MAX_MHZ * 1e6
+# Algorithmic bytes per SU(2) link update: read + write of the link once per sweep.
+SU2_BYTES_PER_UPDATE = 32.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- workload
+def ising_chains(rank: int):
+    import paper_0903_3053_gb300 as mc
+    out = []
+    for i, L in enumerate(SIZES):
+        for j, b in enumerate(BETAS):
+            idx = i * len(BETAS) + j
+            out.append(mc.ising(L, b, seed=1, chain_id=rank * 1000 + idx, hot=True))
+    return out
+
+
+def flips_per_step() -> int:
+    return len(BETAS) * sum(L * L for L in SIZES)
+
+
+def run_gb300(args):
+    import torch
+
+    import paper_0903_3053_gb300 as mc
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev_props = torch.cuda.get_device_properties(local)
+    stream = torch.cuda.current_stream()
+    K, W = args.steps, args.warmup
+
+    # ---- device-resident timed region ------------------------------------------
+    chains = ising_chains(rank)
+    batch = mc.Batch(chains, layout=mc.MC_LAYOUT_MSC32, series_capacity=K + W + 8)
+    batch.set_mode(mc.MC_MODE_GRID, args.threads)
+    batch.sweep(W, 1)
+    batch.read_series()
+    batch.profile(True)
+    batch.profile_read()
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(K):
+        batch.sweep(1, 1)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clock_info = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    launches, kernel_ms = batch.profile_read()
+    series = batch.read_series()
+    assert series.shape[1] == K, series.shape
+    batch.profile(False)
+    ms_max = max_over_ranks(ms, world)
+    flips = flips_per_step() * K * world
+    value = flips / (ms_max / 1e3)
+    # dominant kernel: the MSC half-sweep (launches = 2 per step)
+    half_ms = kernel_ms / max(launches, 1)
+    ops_per_launch = ALU_OPS_PER_FLIP * flips_per_step() / 2
+    achieved = ops_per_launch / (half_ms / 1e3)
+    batch.close()
+    del batch
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the C ABI, host buffers -----------------------------
+    e2e = run_e2e(mc, torch, rank, min(K, args.e2e_steps), world)
+
+    # ---- SU(2) component ------------------------------------------------------------
+    su2 = run_su2(mc, torch, rank, args.su2_steps, world)
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "spin-flips/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms_max / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {
+            "workload": "2D Ising, multi-spin-coded uint32 (32 spins/word), L in {1024, 4096, 16384} x beta in "
+                        "{0.30, 0.40, 0.4406868, 0.50, 0.60}, periodic, hot start seed 1, E/M every sweep",
+            "chains_per_gpu": len(chains),
+            "step": "one sweep of every chain (2 half-sweep launches + E/M reduction fused)",
+            "l2": "inputs larger than L2: 170 MiB of spins per GPU (L2 = 129 MB)",
+            "parallelism": f"replicas{world}",
+            "threads_per_block": args.threads,
+        },
+        "roofline": {
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": ALU_PEAK_OPS,
+            "unit": "int-op/s",
+            "frac": achieved / ALU_PEAK_OPS,
+            "traffic": None,
+            "kernel": "k_half_sweep<C, MSC32> (Ising half-sweep)",
+            "kernel_ms_per_launch": half_ms,
+            "kernel_share_of_step": kernel_ms / ms if ms > 0 else None,
+            "peak_source": "derived: 152 SMs x 128 lane-instr/clk x 2070 MHz (no ALU figure in MEASURED_PEAKS.json)",
+        },
+        "e2e": e2e,
+        "gpu_launches": launches + K,  # 2 half-sweeps + 1 state-advance kernel per step
+        "clocks": clock_info,
+        "components": {"su2": su2},
+        "device": dev_props.name,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(mc, torch, rank, K, world):
+    """Per step: upload every chain's configuration from page-locked host memory
+    (canonical bit rows), one sweep with measurement, read the step's records
+    back to the host -- all through the C ABI."""
+    chains = ising_chains(rank)
+    batch = mc.Batch(chains, layout=mc.MC_LAYOUT_MSC32, series_capacity=4)
+    batch.set_mode(mc.MC_MODE_GRID, 256)
+    host = []
+    h2d = 0
+    for k, c in enumerate(chains):
+        cfg = batch.get_config(k, mc.MC_FMT_BITS)
+        t = torch.from_numpy(cfg.view(np.int32)).pin_memory()
+        host.append(t)
+        h2d += t.numel() * 4
+    d2h = len(chains) * 48
+    for _ in range(2):
+        for k in range(len(chains)):
+            batch.set_config_host_async(k, host[k], mc.MC_FMT_BITS)
+        batch.sweep(1, 1)
+        batch.read_series()
+    barrier(world)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(K):
+        for k in range(len(chains)):
+            batch.set_config_host_async(k, host[k], mc.MC_FMT_BITS)
+        batch.sweep(1, 1)
+        batch.read_series()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    barrier(world)
+    dt = max_over_ranks(dt, world)
+    batch.close()
+    return {"value": flips_per_step() * K * world / dt, "unit": "spin-flips/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": K}
+
+
+def run_su2(mc, torch, rank, K, world):
+    chains = [mc.su2(SU2_L, b, seed=1, chain_id=rank * 1000 + i, hot=True) for i, b in enumerate(SU2_BETAS)]
+    batch = mc.Batch(chains, series_capacity=K + 8)
+    batch.sweep(3, 1)
+    batch.read_series()
+    batch.profile(True)
+    batch.profile_read()
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(K):
+        batch.sweep(1, 1)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(t0.elapsed_time(t1), world)
+    launches, kernel_ms = batch.profile_read()
+    P = batch.read_series()["P"][:, -1].tolist()
+    batch.close()
+    updates = len(chains) * 4 * SU2_L ** 4 * K * world
+    phase_ms = kernel_ms / max(launches, 1)
+    per_launch_updates = len(chains) * SU2_L ** 4 / 2
+    hbm = 6777.3e9
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] * 1e9
+    except (OSError, KeyError, ValueError):
+        pass
+    achieved_bw = SU2_BYTES_PER_UPDATE * per_launch_updates / (phase_ms / 1e3)
+    return {"metric": "SU(2) link-updates/s", "value": updates / (ms / 1e3), "unit": "link-updates/s",
+            "workload": f"4D SU(2) {SU2_L}^4, beta in {SU2_BETAS}, hot start, heat-bath (KP+Creutz), plaquette "
+                        "every sweep", "steps": K, "ms_per_sweep": ms / K, "phase_kernel_ms": phase_ms,
+            "last_plaquette": P,
+            "roofline_hbm": {"achieved": achieved_bw, "peak": hbm, "unit": "B/s", "frac": achieved_bw / hbm,
+                             "bytes_per_update": SU2_BYTES_PER_UPDATE}}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(seconds: float) -> dict:
+    """The oracle as it stands (plain C, one thread) on a bounded sample of the
+    workload: a 1024^2 chain at beta_c, as many sweeps as fit in ~`seconds`."""
+    import oracle
+    oracle.build()
+    s = oracle.ising_init(1024, seed=1, chain=0, hot=True)
+    t = time.perf_counter()
+    oracle.ising_run(s, 0.4406868, 1, 0, 0, 1, record=False)
+    one = time.perf_counter() - t
+    n = max(1, int(seconds / max(one, 1e-6)))
+    t = time.perf_counter()
+    oracle.ising_run(s, 0.4406868, 1, 0, 1, n, record=False)
+    dt = time.perf_counter() - t
+    return {"value": 1024 * 1024 * n / dt, "unit": "spin-flips/s", "cores": 1, "kind": "oracle",
+            "sample": f"1024x1024 chain at beta=0.4406868, {n} sweeps (int8 oracle, one thread), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    # one step = one oracle sweep of a 1024^2 chain (a bounded sample of the workload)
+    s = oracle.ising_init(1024, seed=1, chain=0, hot=True)
+    for w in range(args.warmup):
+        oracle.ising_run(s, 0.4406868, 1, 0, w, 1)
+    t = time.perf_counter()
+    for k in range(args.steps):
+        oracle.ising_run(s, 0.4406868, 1, 0, args.warmup + k, 1)
+    dt = time.perf_counter() - t
+    value = 1024 * 1024 * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "spin-flips/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i8", "data": "synthetic",
+        "config": {"workload": "2D Ising 1024x1024 sample of the multi-spin-coded batch, beta=0.4406868, hot start, "
+                               "E/M every sweep (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": "spin-flips/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} sweeps of a 1024x1024 chain"},
+        "e2e": {"value": value, "unit": "spin-flips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--su2-steps", type=int, default=40)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

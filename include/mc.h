@@ -1,0 +1,191 @@
+/*
+ * mc.h -- C ABI of libmc.so: the checkerboard local-update sweep of
+ * Demchik & Strelchenko, "Monte Carlo simulations on Graphics Processing Units"
+ * (arXiv:0903.3053), for one NVIDIA GB300 (sm_103a).
+ *
+ * Models
+ *   Ising : 2D Ising model of Eq. (1), H = -sum_<ij> s_i s_j, on an Lx x Ly
+ *           periodic torus, Metropolis single-spin updates on the red/black
+ *           checkerboard (Sec. 2.3); a sweep updates colour 0 ((x+y) even), then
+ *           colour 1 (Sec. 2.1).
+ *   SU(2) : 4D SU(2) Wilson gauge theory, Eqs. (2)-(3), on an L0 x L1 x L2 x L3
+ *           periodic hypertorus (mu = 0 is time, Sec. 2.4); heat-bath
+ *           replacement of each link by Eqs. (5)-(7) with the staple of Eq. (6);
+ *           a sweep runs mu = 0..3 on the odd sites, then mu = 0..3 on the even
+ *           sites (Sec. 2.4).  Links are the quaternions (U0, U1, U2, U3) of
+ *           Eq. (4) in FP32.
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), keyed by the 64-bit
+ *   seed and counted by (site, sweep, tag, chain id), so every result is
+ *   reproducible and independent of the launch configuration.
+ *
+ * Conventions
+ *   - Every function returns an mc_status; nothing throws across the ABI.  On a
+ *     non-OK status mc_last_error() returns a message (thread-local).
+ *   - Memory: the caller allocates ONE device workspace of
+ *     mc_workspace_bytes(...) bytes (e.g. a torch uint8 tensor) and keeps it
+ *     alive until mc_destroy; the library carves the lattice, series ring
+ *     buffer, scratch and state out of it and allocates no device memory of its
+ *     own.  The library owns the mc_ctx struct and its CUDA graphs.
+ *   - Streams: all device work of a context is issued on the cudaStream_t given
+ *     at init (passed as void*; NULL = legacy default stream).  Calls marked
+ *     "async" return before the GPU has finished; device-side faults detected by
+ *     the kernels (bad index, wait limit reached) are latched in the context and
+ *     reported by the next synchronising call (mc_sync, mc_measure,
+ *     mc_read_series, mc_get_config) as MC_EDEVICE.
+ *   - Layout-free I/O: configurations cross the ABI in a canonical order that
+ *     does not depend on the internal layout:
+ *       Ising : MC_FMT_INT8 -- int8 s[y][x] = +-1;
+ *               MC_FMT_BITS -- uint32 words, row-major, bit b of word w of row y
+ *                              is site x = 32 w + b, 1 = spin +1 (Lx % 32 == 0).
+ *       SU(2) : float q[s][mu][4], s = x1 + L1 (x2 + L2 (x3 + L3 x0)).
+ *   - Threads: one context must not be used by two host threads at once.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MC_API __attribute__((visibility("default")))
+#else
+#define MC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mc_ctx mc_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    MC_OK = 0,
+    MC_EINVAL = -1,   /* bad argument (reported before any device work) */
+    MC_ENOMEM = -2,   /* workspace too small */
+    MC_ECUDA = -3,    /* a CUDA runtime call failed */
+    MC_ETIMEOUT = -4, /* a device-side wait reached its iteration limit */
+    MC_ESTATE = -5,   /* call not valid in the context's current state */
+    MC_EDEVICE = -6   /* a kernel detected a fault and latched it */
+} mc_status;
+
+enum { MC_COLD = 0, MC_HOT = 1 };              /* initial configuration (Sec. 2.1, 2.4) */
+enum { MC_KIND_ISING = 1, MC_KIND_SU2 = 2 };   /* model */
+enum { MC_LAYOUT_INT8 = 0, MC_LAYOUT_MSC32 = 1 }; /* Ising storage: 1 byte / 1 bit per spin */
+enum { MC_FMT_INT8 = 0, MC_FMT_BITS = 1, MC_FMT_F32 = 2 }; /* canonical config formats */
+enum { MC_MODE_AUTO = 0, MC_MODE_GRID = 1, MC_MODE_RESIDENT = 2 }; /* sweep execution */
+
+/* One Markov chain of a batch. */
+typedef struct {
+    int32_t kind;      /* MC_KIND_ISING or MC_KIND_SU2 */
+    int32_t L[4];      /* Ising: L[0] = Lx, L[1] = Ly (L[2], L[3] ignored); SU(2): L[mu] */
+    double beta;       /* Ising: coupling beta of Eq. (1); SU(2): beta = 4/g^2 of Eq. (2); >= 0 */
+    uint64_t seed;     /* Philox key */
+    uint32_t chain_id; /* Philox counter word 3: distinguishes chains sharing a seed */
+    int32_t start;     /* MC_COLD or MC_HOT */
+} mc_chain_desc;
+
+/* One measurement record (per chain, per measured sweep). */
+typedef struct {
+    int64_t sweep; /* global index of the sweep after which it was taken (0-based) */
+    int64_t E;     /* Ising: H of Eq. (1), exact */
+    int64_t M;     /* Ising: sum of spins, exact */
+    double P;      /* SU(2): plaquette (1/6N) sum_x sum_{mu<nu} (1/2) Tr U_munu(x), Eq. (3); FP64 sum */
+    double Ps;     /* SU(2): spatial plaquettes only (mu, nu in 1..3) */
+    double Pt;     /* SU(2): temporal plaquettes only (one index 0) */
+} mc_record;
+
+/* Sizes.  Each chain needs all extents even (checkerboard / parity split);
+ * MC_LAYOUT_MSC32 additionally needs Lx % 64 == 0.  series_capacity = records
+ * per chain the ring buffer holds between two mc_read_series calls (>= 1).
+ * Returns 0 when the arguments are invalid (see mc_last_error). */
+MC_API size_t mc_workspace_bytes(int32_t n_chains, const mc_chain_desc *chains, int32_t layout,
+                          int64_t series_capacity);
+
+/* Create a context over n_chains chains, all of the same kind, and launch their
+ * initialisation (hot/cold, Sec. 2.1 and Sec. 2.4; async).  `workspace` is a
+ * device pointer to at least mc_workspace_bytes(...) bytes, 256-byte aligned,
+ * borrowed until mc_destroy.  `cuda_stream` is a cudaStream_t or NULL.  The
+ * global sweep counter starts at 0. */
+MC_API mc_status mc_batch_init(mc_ctx **out, int32_t n_chains, const mc_chain_desc *chains, int32_t layout,
+                        int64_t series_capacity, void *workspace, size_t workspace_bytes, void *cuda_stream);
+
+/* Single-chain conveniences (chain_id 0). */
+MC_API mc_status mc_ising_init(mc_ctx **out, const int32_t L[2], double beta, uint64_t seed, int32_t start,
+                        int32_t layout, int64_t series_capacity, void *workspace, size_t workspace_bytes,
+                        void *cuda_stream);
+MC_API mc_status mc_su2_init(mc_ctx **out, const int32_t L[4], double beta, uint64_t seed, int32_t start,
+                      int64_t series_capacity, void *workspace, size_t workspace_bytes, void *cuda_stream);
+
+/* Advance every chain by n_sweeps sweeps (async).  When measure_every > 0 a
+ * record is appended after the k-th sweep of this call (k = 1..n_sweeps) for
+ * every k divisible by measure_every (the measuring kernels of Sec. 2.3/2.4);
+ * MC_EINVAL if that would overrun the unread part of the ring buffer.
+ * Repeated calls with the same (n_sweeps, measure_every) replay one captured
+ * CUDA graph. */
+MC_API mc_status mc_sweep(mc_ctx *ctx, int64_t n_sweeps, int32_t measure_every);
+
+/* Execution mode for later sweeps: MC_MODE_GRID (one launch per half-sweep /
+ * phase over all chains), MC_MODE_RESIDENT (Ising only: one CTA per chain with
+ * its lattice in shared memory, all sweeps of a call in one launch) or
+ * MC_MODE_AUTO.  threads_per_block = 0 keeps the default.  Results are
+ * bit-identical in every mode. */
+MC_API mc_status mc_set_mode(mc_ctx *ctx, int32_t mode, int32_t threads_per_block);
+
+/* Wait for the context's stream; report latched device faults. */
+MC_API mc_status mc_sync(mc_ctx *ctx);
+
+/* Measure chain `chain` now (synchronous) and return the record (sweep field =
+ * number of sweeps done - 1, or -1 before the first sweep). */
+MC_API mc_status mc_measure(mc_ctx *ctx, int32_t chain, mc_record *out);
+
+/* Copy the unread records (oldest first, chain-major: all of chain 0, then
+ * chain 1, ...) into host_dst, which must hold n_chains * max_per_chain
+ * records; *n_per_chain receives how many records each chain returned.  The
+ * copied records are marked read.  Synchronous. */
+MC_API mc_status mc_read_series(mc_ctx *ctx, mc_record *host_dst, int64_t max_per_chain, int64_t *n_per_chain);
+
+/* Canonical configuration of one chain, to/from host or device memory
+ * (dst_is_device / src_is_device).  Ising: MC_FMT_INT8 or MC_FMT_BITS;
+ * SU(2): MC_FMT_F32.  mc_get_config is synchronous; mc_set_config is async but
+ * the source may be reused as soon as it returns when it is host memory. */
+MC_API mc_status mc_get_config(mc_ctx *ctx, int32_t chain, int32_t fmt, void *dst, int32_t dst_is_device);
+MC_API mc_status mc_set_config(mc_ctx *ctx, int32_t chain, int32_t fmt, const void *src, int32_t src_is_device);
+MC_API size_t mc_config_bytes(const mc_ctx *ctx, int32_t chain, int32_t fmt); /* 0 if invalid */
+
+/* Checkpoint: the global sweep counter is the whole RNG state (counter-based
+ * stream); together with the configurations it makes resume bit-exact. */
+MC_API mc_status mc_get_sweep(const mc_ctx *ctx, int64_t *sweeps_done);
+MC_API mc_status mc_set_sweep(mc_ctx *ctx, int64_t sweeps_done);
+
+/* SU(2) debugging: when enabled, every sweep writes, per link, the index of
+ * the heat-bath try whose draw was taken (0..7 Kennedy-Pendleton, 8..71 Creutz,
+ * 255 = all rejected, link unchanged) into a per-chain byte array readable with
+ * mc_su2_get_tries (canonical [s][mu] order, 4 N bytes, host memory). */
+MC_API mc_status mc_su2_record_tries(mc_ctx *ctx, int32_t enable);
+MC_API mc_status mc_su2_get_tries(mc_ctx *ctx, int32_t chain, uint8_t *host_dst);
+
+/* Number of SU(2) link updates, summed over chains and sweeps so far, whose
+ * every heat-bath try was rejected (link kept; still exact).  Synchronous. */
+MC_API mc_status mc_su2_failed_updates(mc_ctx *ctx, int64_t *count);
+
+/* Kernel timing.  While enabled, sweeps are enqueued without CUDA graphs and
+ * every launch of a sweep kernel (Ising half-sweep, SU(2) (parity, mu) phase)
+ * is bracketed by CUDA events recorded on the context stream. */
+MC_API mc_status mc_profile_enable(mc_ctx *ctx, int32_t enable);
+/* Number of bracketed launches and their summed duration in milliseconds since
+ * the previous read (synchronous; resets the counters). */
+MC_API mc_status mc_profile_read(mc_ctx *ctx, int64_t *launches, double *total_ms);
+
+/* Destroy the context (synchronises its stream first; frees graphs). */
+MC_API mc_status mc_destroy(mc_ctx *ctx);
+
+/* Message for the last non-OK status returned on this thread. */
+MC_API const char *mc_last_error(void);
+
+/* Library version string. */
+MC_API const char *mc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

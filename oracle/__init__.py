@@ -69,6 +69,11 @@ def lib() -> ctypes.CDLL:
             L.orc_su2_staple.argtypes = [P, P, c.c_long, c.c_int, P]
             L.orc_su2_sample_a0.argtypes = [c.c_double, c.c_uint64, c.c_long, P, P]
             L.orc_su2_mul.argtypes = [P, P, P]
+            L.orc_ising_check_sites.argtypes = [P, P, c.c_int, c.c_int, c.c_double, c.c_uint64, c.c_uint32,
+                                                c.c_uint32, P, c.c_long, P]
+            L.orc_su2_check_links.argtypes = [P, P, P, c.c_double, c.c_uint64, c.c_uint32, c.c_uint32, P, c.c_long,
+                                              P, c.c_double, P, P, P]
+            L.orc_su2_check_links.restype = c.c_long
             L.orc_su2_nlinks.argtypes = [P]
             L.orc_su2_nlinks.restype = c.c_long
             _lib = L
@@ -197,3 +202,37 @@ def su2_mul(a, b) -> np.ndarray:
     out = np.zeros(4, dtype=np.float64)
     lib().orc_su2_mul(_ptr(a), _ptr(b), _ptr(out))
     return out
+
+
+# --------------------------------------------------------------------------- sampled checks
+def ising_check_sites(pre: np.ndarray, post: np.ndarray, beta: float, seed: int, chain: int, sweep: int,
+                      sites) -> np.ndarray:
+    """Expected post-sweep spins of the listed sites (flat indices y*Lx + x)."""
+    Ly, Lx = pre.shape
+    pre = np.ascontiguousarray(pre, dtype=np.int8)
+    post = np.ascontiguousarray(post, dtype=np.int8)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.zeros(len(sites), dtype=np.int8)
+    lib().orc_ising_check_sites(_ptr(pre), _ptr(post), Lx, Ly, float(beta), seed, chain, sweep, _ptr(sites),
+                                len(sites), _ptr(out))
+    return out
+
+
+def su2_check_links(pre: np.ndarray, post: np.ndarray, L, beta: float, seed: int, chain: int, sweep: int, links,
+                    forced_tries=None, eps: float = 1e-6):
+    """Expected post-sweep links (flat indices 4 s + mu) recomputed in FP64 from
+    the lattice each update saw.  Returns (values[n, 4], failures, near, bad)."""
+    d = _dims(L)
+    pre = np.ascontiguousarray(pre, dtype=np.float64)
+    post = np.ascontiguousarray(post, dtype=np.float64)
+    links = np.ascontiguousarray(links, dtype=np.int64)
+    out = np.zeros((len(links), 4), dtype=np.float64)
+    f = None
+    if forced_tries is not None:
+        forced_tries = np.ascontiguousarray(forced_tries, dtype=np.uint8)
+        f = _ptr(forced_tries)
+    near = ctypes.c_long(0)
+    bad = ctypes.c_long(0)
+    fails = lib().orc_su2_check_links(_ptr(pre), _ptr(post), _ptr(d), float(beta), seed, chain, sweep, _ptr(links),
+                                      len(links), f, float(eps), _ptr(out), ctypes.byref(near), ctypes.byref(bad))
+    return out, int(fails), int(near.value), int(bad.value)

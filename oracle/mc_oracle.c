@@ -633,3 +633,75 @@ ORC_API void orc_su2_mul(const double a[4], const double b[4], double out[4])
 {
     quat_from_mat(mat_mul(mat_from_quat(a), mat_from_quat(b)), out);
 }
+
+/* ========================================================================= */
+/* Sampled checks of one sweep at any lattice size.                           */
+/* ========================================================================= */
+
+/* Expected post-sweep spin of each listed site (index y*Lx + x), given the
+ * configurations before (pre) and after (post) sweep number `sweep`: colour-0
+ * sites are updated against the pre-sweep colour-1 spins, colour-1 sites
+ * against the post-sweep colour-0 spins (Sec. 2.3 checkerboard order). */
+ORC_API void orc_ising_check_sites(const int8_t *pre, const int8_t *post, int Lx, int Ly, double beta,
+                                   uint64_t seed, uint32_t chain, uint32_t sweep, const int64_t *sites, long n,
+                                   int8_t *out)
+{
+    uint32_t thr[2];
+    orc_ising_thresholds(beta, thr);
+    for (long k = 0; k < n; ++k) {
+        int x = (int)(sites[k] % Lx), y = (int)(sites[k] / Lx);
+        int c = (x + y) & 1;
+        const int8_t *nb = c == 0 ? pre : post;
+        int xp = (x + 1) % Lx, xm = (x + Lx - 1) % Lx, yp = (y + 1) % Ly, ym = (y + Ly - 1) % Ly;
+        int h = nb[y * Lx + xp] + nb[y * Lx + xm] + nb[yp * Lx + x] + nb[ym * Lx + x];
+        int v = pre[y * Lx + x];
+        int local = v * h;
+        uint32_t r = site_word(seed, chain, sweep, TAG_ISING_METRO, c, colour_index(x, y, Lx));
+        int flip = local <= 0 || (local == 2 ? r < thr[0] : r < thr[1]);
+        out[k] = (int8_t)(flip ? -v : v);
+    }
+}
+
+/* Position of phase (parity p, direction mu) in the sweep: odd sites first. */
+static int phase_index(int p, int mu) { return (p == 1 ? 0 : 4) + mu; }
+
+/* Expected post-sweep value of each listed link (index 4 s + mu), given the
+ * quaternion configurations before and after sweep number `sweep`: for a link
+ * of phase k, every link of an earlier phase holds its post-sweep value and
+ * every other link its pre-sweep value, which is exactly the lattice the
+ * update saw.  forced_tries (per listed link, or NULL) as in orc_su2_sweep.
+ * Returns the number of listed links whose every try was rejected. */
+ORC_API long orc_su2_check_links(const double *pre, const double *post, const int L[4], double beta, uint64_t seed,
+                                 uint32_t chain, uint32_t sweep, const int64_t *links, long n,
+                                 const uint8_t *forced_tries, double eps, double *out, long *n_near, long *n_bad)
+{
+    su2_lattice lat;
+    load_lattice(&lat, L, pre);
+    long failures = 0, near = 0, bad = 0;
+    for (int ph = 0; ph < 8; ++ph) {
+        int p = ph < 4 ? 1 : 0, mu = ph & 3;
+        /* lattice as seen by phase ph */
+        for (long s = 0; s < lat.nsites; ++s)
+            for (int nu = 0; nu < 4; ++nu) {
+                const double *src = phase_index(site_parity(L, s), nu) < ph ? post : pre;
+                lat.U[s * 4 + nu] = mat_from_quat(&src[(s * 4 + nu) * 4]);
+            }
+        for (long k = 0; k < n; ++k) {
+            long s = (long)(links[k] >> 2);
+            int m = (int)(links[k] & 3);
+            if (m != mu || site_parity(L, s) != p)
+                continue;
+            int forced = forced_tries ? (int)forced_tries[k] : NOT_FORCED;
+            int t = heatbath_link(&lat, s, mu, p, beta, seed, chain, sweep, forced, eps, &near, &bad);
+            if (t == HB_FAILED)
+                ++failures;
+            quat_from_mat(*link(&lat, s, mu), &out[k * 4]);
+        }
+    }
+    free_lattice(&lat);
+    if (n_near)
+        *n_near = near;
+    if (n_bad)
+        *n_bad = bad;
+    return failures;
+}

@@ -1,0 +1,634 @@
+// ising.cu -- 2D Ising Metropolis sweep on the red/black checkerboard
+// (Eq. (1), Sec. 2.3), two storage layouts:
+//
+//   int8  : s[y][x] = +-1, one byte per spin.
+//   MSC32 : multi-spin coding, 32 spins per 32-bit word and one bit per spin
+//           (the paper stores spins as 1-bit variables, Sec. 2.3).  Each
+//           colour c has its own plane of Ly rows x W = Lx/64 words; bit b of
+//           word w in row y of plane c is the site of colour c with in-row
+//           index j = 32 w + b, i.e. x = 2 j + ((y + c) & 1).  With that packing
+//           the four neighbours of a whole word are: the same word of the other
+//           plane in rows y-1, y and y+1, and the row-y word of the other plane
+//           shifted by one bit (towards w-1 or w+1 depending on the row parity).
+//           Anti-aligned neighbours are counted bit-sliced for 32 spins at once.
+//
+// Random numbers: site i = y*(Lx/2) + j of colour c uses word (i & 3) of the
+// Philox block with counter (i >> 2, sweep, TAG_METRO | c, chain_id), so the
+// stream does not depend on layout, tiling or launch shape.  A spin flips when
+// dE = 2 s h <= 0, or when its word is below T[dE] = floor(e^{-beta dE} 2^32)
+// (integer thresholds, no floating point on the path).
+//
+// Execution modes:
+//   grid     : one launch per colour over every chain of the batch; chain of a
+//              block found by binary search over per-chain block offsets.
+//   resident : one CTA per chain holding its whole lattice in shared memory and
+//              running all sweeps of a call in one launch (small lattices).
+// The energy/magnetisation measurement (the paper's sweep+measure kernels) is
+// fused into the colour-1 half-sweep: each colour-1 site counts its
+// anti-aligned bonds (every bond joins exactly one colour-1 site) and pairs
+// itself with one colour-0 site for the magnetisation; exact integer sums via
+// warp reductions and one 64-bit atomic per CTA.
+#include "mc_internal.cuh"
+
+namespace mc {
+namespace {
+
+__device__ __forceinline__ uint32_t inc_wrap(uint32_t v, uint32_t n) { return v + 1 == n ? 0u : v + 1; }
+__device__ __forceinline__ uint32_t dec_wrap(uint32_t v, uint32_t n) { return v == 0 ? n - 1 : v - 1; }
+
+// Sum two per-thread counters over the CTA; thread 0 receives the totals.
+// Every thread of the CTA must call it.
+__device__ __forceinline__ void block_sum2(uint32_t &a, uint32_t &b)
+{
+    __shared__ uint32_t sa[32], sb[32];
+    a = __reduce_add_sync(0xffffffffu, a);
+    b = __reduce_add_sync(0xffffffffu, b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[warp] = a;
+        sb[warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ta = 0, tb = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            ta += sa[w];
+            tb += sb[w];
+        }
+        a = ta;
+        b = tb;
+    }
+}
+
+// ------------------------------------------------------------------ int8 layout
+// Update the (up to four) sites of colour C that share Philox block g.
+template <int C, bool MEASURE>
+__device__ __forceinline__ void int8_group(int8_t *s, const IsingChain &ch, uint32_t g, uint32_t sweep,
+                                           uint32_t &anti, uint32_t &up)
+{
+    const uint32_t Lx = ch.Lx, Ly = ch.Ly, half = Lx >> 1, nc = (Lx * Ly) >> 1;
+    const uint4 r4 = philox4x32_10(make_uint4(g, sweep, kTagIsingMetro | (uint32_t)C, ch.chain_id), ch.key);
+    const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t i = 4 * g + q;
+        if (i >= nc)
+            break;
+        const uint32_t y = i / half, j = i - y * half;
+        const uint32_t x = 2 * j + ((y + C) & 1u);
+        const uint32_t row = y * Lx, rowp = inc_wrap(y, Ly) * Lx, rowm = dec_wrap(y, Ly) * Lx;
+        const int sv = s[row + x];
+        const int ne = s[row + inc_wrap(x, Lx)], nw = s[row + dec_wrap(x, Lx)];
+        const int nn = s[rowm + x], ns = s[rowp + x];
+        const int local = sv * (ne + nw + nn + ns); // dE / 2
+        const bool flip = local <= 0 || rr[q] < (local == 2 ? ch.T2 : ch.T4);
+        const int nv = flip ? -sv : sv;
+        if (flip)
+            s[row + x] = (int8_t)nv;
+        if (MEASURE) {
+            anti += (uint32_t)(ne != nv) + (uint32_t)(nw != nv) + (uint32_t)(nn != nv) + (uint32_t)(ns != nv);
+            const int partner = (x & 1u) ? nw : ne; // colour-0 site (x ^ 1, y)
+            up += (uint32_t)(nv > 0) + (uint32_t)(partner > 0);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ MSC layout
+// New value of one colour-C word given its four neighbour words.
+template <int C>
+__device__ __forceinline__ uint32_t msc_word(uint32_t s, uint32_t nu, uint32_t nd, uint32_t ns, uint32_t side,
+                                             uint32_t blk0, uint32_t sweep, const IsingChain &ch)
+{
+    const uint32_t a1 = s ^ nu, a2 = s ^ nd, a3 = s ^ ns, a4 = s ^ side; // 1 = anti-aligned
+    const uint32_t s12 = a1 ^ a2, c12 = a1 & a2, s34 = a3 ^ a4, c34 = a3 & a4;
+    const uint32_t ge2 = c12 | c34 | (s12 & s34); // >= 2 anti-aligned: dE <= 0, always flip
+    const uint32_t eq0 = ~(a1 | a2 | a3 | a4);    // dE = 8
+    const uint32_t eq1 = ~(ge2 | eq0);            // dE = 4
+    const uint32_t need = eq0 | eq1;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if ((need >> (4 * k)) & 0xFu) {
+            const uint4 r = philox4x32_10(make_uint4(blk0 + k, sweep, kTagIsingMetro | (uint32_t)C, ch.chain_id),
+                                          ch.key);
+            const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int b = 4 * k + q;
+                const uint32_t T = ((eq1 >> b) & 1u) ? ch.T2 : ch.T4;
+                acc |= (uint32_t)(rr[q] < T) << b;
+            }
+        }
+    }
+    return s ^ (ge2 | (acc & need));
+}
+
+// Gather the neighbours of word (y, w) of plane C from the other plane `po`.
+template <int C>
+__device__ __forceinline__ void msc_neighbours(const uint32_t *po, uint32_t y, uint32_t w, uint32_t W, uint32_t Ly,
+                                               uint32_t &nu, uint32_t &nd, uint32_t &ns, uint32_t &side)
+{
+    const uint32_t row = y * W;
+    nu = po[dec_wrap(y, Ly) * W + w];
+    nd = po[inc_wrap(y, Ly) * W + w];
+    ns = po[row + w];
+    if (((y + C) & 1u) == 0) { // x = 2j: other colour at j-1 and j
+        const uint32_t prev = po[row + dec_wrap(w, W)];
+        side = (ns << 1) | (prev >> 31);
+    } else { // x = 2j+1: other colour at j and j+1
+        const uint32_t next = po[row + inc_wrap(w, W)];
+        side = (ns >> 1) | (next << 31);
+    }
+}
+
+// ------------------------------------------------------------------ grid mode
+template <int C, int LAYOUT>
+__global__ void __launch_bounds__(1024) k_half_sweep(SweepArgs a)
+{
+    const int k = find_chain(a.block_start, a.n_chains, blockIdx.x);
+    const IsingChain ch = static_cast<const IsingChain *>(a.chains)[k];
+    const uint32_t t = (blockIdx.x - a.block_start[k]) * blockDim.x + threadIdx.x;
+    const uint32_t sweep = (uint32_t)(a.state->sweep_base + a.k);
+    const bool measure = (C == 1) && a.measure;
+    uint32_t anti = 0, up = 0;
+    if (LAYOUT == MC_LAYOUT_INT8) {
+        int8_t *s = reinterpret_cast<int8_t *>(a.lattice + ch.spin_off);
+        const uint32_t groups = (((ch.Lx * ch.Ly) >> 1) + 3) >> 2;
+        if (t < groups) {
+            if (measure)
+                int8_group<C, true>(s, ch, t, sweep, anti, up);
+            else
+                int8_group<C, false>(s, ch, t, sweep, anti, up);
+        }
+    } else {
+        const uint32_t W = ch.W, Ly = ch.Ly, nw = W * Ly;
+        uint32_t *base = reinterpret_cast<uint32_t *>(a.lattice + ch.spin_off);
+        uint32_t *pc = base + (size_t)C * nw;
+        const uint32_t *po = base + (size_t)(1 - C) * nw;
+        if (t < nw) {
+            const uint32_t y = t / W, w = t - y * W;
+            uint32_t nu, nd, ns, side;
+            msc_neighbours<C>(po, y, w, W, Ly, nu, nd, ns, side);
+            const uint32_t s = pc[t];
+            const uint32_t sn = msc_word<C>(s, nu, nd, ns, side, y * (ch.Lx >> 3) + 8 * w, sweep, ch);
+            if (sn != s)
+                pc[t] = sn;
+            if (measure) {
+                anti = __popc(sn ^ nu) + __popc(sn ^ nd) + __popc(sn ^ ns) + __popc(sn ^ side);
+                up = __popc(sn) + __popc(ns);
+            }
+        }
+    }
+    if (!a.measure)
+        return;
+    const long long slot = (long long)((a.state->rec_head + a.rec_k) % (unsigned long long)a.cap);
+    DevRecord *rec = &a.series[(long long)k * a.cap + slot];
+    if (C == 0) {
+        if (t == 0) { // zero the record before the colour-1 kernel accumulates into it
+            rec->sweep = (long long)(a.state->sweep_base + a.k);
+            rec->a = 0;
+            rec->b = 0;
+            rec->d0 = rec->d1 = rec->d2 = 0.0;
+        }
+        return;
+    }
+    block_sum2(anti, up);
+    if (threadIdx.x == 0) {
+        atomicAdd(&rec->a, (unsigned long long)anti);
+        atomicAdd(&rec->b, (unsigned long long)up);
+    }
+}
+
+// ------------------------------------------------------------------ resident mode
+template <int LAYOUT>
+__global__ void __launch_bounds__(1024) k_resident(SweepArgs a, uint32_t n_sweeps, uint32_t every)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int k = blockIdx.x;
+    const IsingChain ch = static_cast<const IsingChain *>(a.chains)[k];
+    const uint32_t bytes = LAYOUT == MC_LAYOUT_INT8 ? ch.Lx * ch.Ly : 8u * ch.Ly * ch.W;
+    uint32_t *gl = reinterpret_cast<uint32_t *>(a.lattice + ch.spin_off);
+    uint32_t *sl = reinterpret_cast<uint32_t *>(smem);
+    for (uint32_t u = threadIdx.x; u < bytes / 4; u += blockDim.x)
+        sl[u] = gl[u];
+    __syncthreads();
+    const unsigned long long base = a.state->sweep_base;
+    for (uint32_t t = 0; t < n_sweeps; ++t) {
+        const uint32_t sweep = (uint32_t)(base + t);
+        const bool measure = every != 0 && ((t + 1) % every) == 0;
+        uint32_t anti = 0, up = 0;
+        if (LAYOUT == MC_LAYOUT_INT8) {
+            int8_t *s = reinterpret_cast<int8_t *>(smem);
+            const uint32_t groups = (((ch.Lx * ch.Ly) >> 1) + 3) >> 2;
+            for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+                int8_group<0, false>(s, ch, g, sweep, anti, up);
+            __syncthreads();
+            if (measure) {
+                for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+                    int8_group<1, true>(s, ch, g, sweep, anti, up);
+            } else {
+                for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+                    int8_group<1, false>(s, ch, g, sweep, anti, up);
+            }
+        } else {
+            const uint32_t W = ch.W, Ly = ch.Ly, nw = W * Ly;
+            uint32_t *p0 = sl, *p1 = sl + nw;
+            for (uint32_t u = threadIdx.x; u < nw; u += blockDim.x) {
+                const uint32_t y = u / W, w = u - y * W;
+                uint32_t nu, nd, ns, side;
+                msc_neighbours<0>(p1, y, w, W, Ly, nu, nd, ns, side);
+                const uint32_t s = p0[u];
+                p0[u] = msc_word<0>(s, nu, nd, ns, side, y * (ch.Lx >> 3) + 8 * w, sweep, ch);
+            }
+            __syncthreads();
+            for (uint32_t u = threadIdx.x; u < nw; u += blockDim.x) {
+                const uint32_t y = u / W, w = u - y * W;
+                uint32_t nu, nd, ns, side;
+                msc_neighbours<1>(p0, y, w, W, Ly, nu, nd, ns, side);
+                const uint32_t s = p1[u];
+                const uint32_t sn = msc_word<1>(s, nu, nd, ns, side, y * (ch.Lx >> 3) + 8 * w, sweep, ch);
+                p1[u] = sn;
+                if (measure) {
+                    anti += __popc(sn ^ nu) + __popc(sn ^ nd) + __popc(sn ^ ns) + __popc(sn ^ side);
+                    up += __popc(sn) + __popc(ns);
+                }
+            }
+        }
+        if (measure) {
+            block_sum2(anti, up);
+            if (threadIdx.x == 0) {
+                const unsigned long long r = a.state->rec_head + (t + 1) / every - 1;
+                DevRecord *rec = &a.series[(long long)k * a.cap + (long long)(r % (unsigned long long)a.cap)];
+                rec->sweep = (long long)(base + t);
+                rec->a = anti;
+                rec->b = up;
+                rec->d0 = rec->d1 = rec->d2 = 0.0;
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t u = threadIdx.x; u < bytes / 4; u += blockDim.x)
+        gl[u] = sl[u];
+}
+
+// ------------------------------------------------------------------ init
+// Hot start: spin +1 iff the top bit of its random word (sweep field 0, tag
+// INIT | colour) is set; cold start: all +1 (Sec. 2.1).
+__global__ void k_init_int8(IsingChain ch, int8_t *s, int hot)
+{
+    const uint32_t n = ch.Lx * ch.Ly;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t y = p / ch.Lx, x = p - y * ch.Lx;
+        int8_t v = 1;
+        if (hot) {
+            const uint32_t c = (x + y) & 1u, i = y * (ch.Lx >> 1) + (x >> 1);
+            const uint4 r = philox4x32_10(make_uint4(i >> 2, 0u, kTagIsingInit | c, ch.chain_id), ch.key);
+            const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+            v = (rr[i & 3u] >> 31) ? 1 : -1;
+        }
+        s[p] = v;
+    }
+}
+
+__global__ void k_init_msc(IsingChain ch, uint32_t *base, int hot)
+{
+    const uint32_t nw = ch.Ly * ch.W;
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < 2 * nw; u += gridDim.x * blockDim.x) {
+        const uint32_t c = u / nw, t = u - c * nw, y = t / ch.W, w = t - y * ch.W;
+        uint32_t word = 0xFFFFFFFFu;
+        if (hot) {
+            word = 0;
+            const uint32_t blk0 = y * (ch.Lx >> 3) + 8 * w;
+            for (int kk = 0; kk < 8; ++kk) {
+                const uint4 r = philox4x32_10(make_uint4(blk0 + kk, 0u, kTagIsingInit | c, ch.chain_id), ch.key);
+                word |= ((r.x >> 31) << (4 * kk)) | ((r.y >> 31) << (4 * kk + 1)) | ((r.z >> 31) << (4 * kk + 2)) |
+                        ((r.w >> 31) << (4 * kk + 3));
+            }
+        }
+        base[u] = word;
+    }
+}
+
+// ------------------------------------------------------------------ measure (standalone)
+template <int LAYOUT>
+__global__ void k_measure(IsingChain ch, const char *lat, DevRecord *out)
+{
+    uint32_t anti = 0, up = 0;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (LAYOUT == MC_LAYOUT_INT8) {
+        const int8_t *s = reinterpret_cast<const int8_t *>(lat);
+        const uint32_t Lx = ch.Lx, Ly = ch.Ly, half = Lx >> 1, nc = (Lx * Ly) >> 1;
+        if (tid < nc) {
+            const uint32_t y = tid / half, j = tid - y * half, x = 2 * j + ((y + 1) & 1u);
+            const int sv = s[y * Lx + x];
+            const int ne = s[y * Lx + inc_wrap(x, Lx)], nw = s[y * Lx + dec_wrap(x, Lx)];
+            const int nn = s[dec_wrap(y, Ly) * Lx + x], ns = s[inc_wrap(y, Ly) * Lx + x];
+            anti = (ne != sv) + (nw != sv) + (nn != sv) + (ns != sv);
+            up = (sv > 0) + (((x & 1u) ? nw : ne) > 0);
+        }
+    } else {
+        const uint32_t W = ch.W, Ly = ch.Ly, nw = W * Ly;
+        const uint32_t *p0 = reinterpret_cast<const uint32_t *>(lat), *p1 = p0 + nw;
+        if (tid < nw) {
+            const uint32_t y = tid / W, w = tid - y * W;
+            uint32_t nu, nd, ns, side;
+            msc_neighbours<1>(p0, y, w, W, Ly, nu, nd, ns, side);
+            const uint32_t s = p1[tid];
+            anti = __popc(s ^ nu) + __popc(s ^ nd) + __popc(s ^ ns) + __popc(s ^ side);
+            up = __popc(s) + __popc(ns);
+        }
+    }
+    block_sum2(anti, up);
+    if (threadIdx.x == 0) {
+        atomicAdd(&out->a, (unsigned long long)anti);
+        atomicAdd(&out->b, (unsigned long long)up);
+    }
+}
+
+// ------------------------------------------------------------------ config I/O
+// Canonical int8 s[y][x] <-> MSC planes; one thread per MSC word.
+__global__ void k_msc_from_int8(IsingChain ch, const int8_t *src, uint32_t *dst)
+{
+    const uint32_t nw = ch.Ly * ch.W;
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= 2 * nw)
+        return;
+    const uint32_t c = u / nw, t = u - c * nw, y = t / ch.W, w = t - y * ch.W;
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b) {
+        const uint32_t x = 2 * (32 * w + b) + ((y + c) & 1u);
+        word |= (uint32_t)(src[y * ch.Lx + x] > 0) << b;
+    }
+    dst[u] = word;
+}
+
+__global__ void k_msc_to_int8(IsingChain ch, const uint32_t *src, int8_t *dst)
+{
+    const uint32_t nw = ch.Ly * ch.W;
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= 2 * nw)
+        return;
+    const uint32_t c = u / nw, t = u - c * nw, y = t / ch.W, w = t - y * ch.W;
+    const uint32_t word = src[u];
+    for (int b = 0; b < 32; ++b) {
+        const uint32_t x = 2 * (32 * w + b) + ((y + c) & 1u);
+        dst[y * ch.Lx + x] = ((word >> b) & 1u) ? 1 : -1;
+    }
+}
+
+// Canonical bit rows (bit b of word v of row y = site x = 32 v + b) <-> MSC.
+__global__ void k_msc_from_bits(IsingChain ch, const uint32_t *src, uint32_t *dst)
+{
+    const uint32_t nw = ch.Ly * ch.W, rw = ch.Lx >> 5;
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= 2 * nw)
+        return;
+    const uint32_t c = u / nw, t = u - c * nw, y = t / ch.W, w = t - y * ch.W;
+    const uint32_t o = (y + c) & 1u;
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b) {
+        const uint32_t x = 64 * w + 2 * b + o;
+        word |= ((src[y * rw + (x >> 5)] >> (x & 31u)) & 1u) << b;
+    }
+    dst[u] = word;
+}
+
+__global__ void k_msc_to_bits(IsingChain ch, const uint32_t *src, uint32_t *dst)
+{
+    // one thread per canonical word; gathers from both planes
+    const uint32_t rw = ch.Lx >> 5, nw = ch.Ly * ch.W;
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= ch.Ly * rw)
+        return;
+    const uint32_t y = v / rw, vw = v - y * rw;
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b) {
+        const uint32_t x = 32 * vw + b;
+        const uint32_t c = (x + y) & 1u, j = x >> 1;
+        const uint32_t msc = src[c * nw + y * ch.W + (j >> 5)];
+        word |= ((msc >> (j & 31u)) & 1u) << b;
+    }
+    dst[v] = word;
+}
+
+__global__ void k_int8_from_bits(IsingChain ch, const uint32_t *src, int8_t *dst)
+{
+    const uint32_t n = ch.Lx * ch.Ly;
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n)
+        dst[p] = ((src[p >> 5] >> (p & 31u)) & 1u) ? 1 : -1;
+}
+
+__global__ void k_int8_to_bits(IsingChain ch, const int8_t *src, uint32_t *dst)
+{
+    const uint32_t nwords = (ch.Lx * ch.Ly) >> 5;
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nwords)
+        return;
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b)
+        word |= (uint32_t)(src[32 * v + b] > 0) << b;
+    dst[v] = word;
+}
+
+__global__ void k_advance(DevState *st, unsigned long long n, unsigned long long recs)
+{
+    st->sweep_base += n;
+    st->rec_head += recs;
+}
+
+inline unsigned blocks_for(size_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+// =========================================================================== host
+size_t ising_config_bytes(const IsingChain &ch, int fmt)
+{
+    const size_t n = (size_t)ch.Lx * ch.Ly;
+    if (fmt == MC_FMT_INT8)
+        return n;
+    if (fmt == MC_FMT_BITS)
+        return (ch.Lx % 32 == 0) ? n / 8 : 0;
+    return 0;
+}
+
+// Work units per chain for a grid-mode launch: Philox groups (int8) or words (MSC).
+static uint32_t grid_units(const mc_ctx *c, const IsingChain &ch)
+{
+    if (c->layout == MC_LAYOUT_INT8)
+        return (((ch.Lx * ch.Ly) >> 1) + 3) >> 2;
+    return ch.Ly * ch.W;
+}
+
+void ising_plan_grid(mc_ctx *c)
+{
+    c->block_start.assign(c->n_chains + 1, 0);
+    uint32_t acc = 0;
+    for (int k = 0; k < c->n_chains; ++k) {
+        c->block_start[k] = acc;
+        acc += blocks_for(grid_units(c, c->ising[k]), c->threads);
+    }
+    c->block_start[c->n_chains] = acc;
+    c->grid_blocks = acc;
+}
+
+static size_t resident_bytes(const mc_ctx *c, const IsingChain &ch)
+{
+    return c->layout == MC_LAYOUT_INT8 ? (size_t)ch.Lx * ch.Ly : (size_t)8 * ch.Ly * ch.W;
+}
+
+bool ising_resident_fits(const mc_ctx *c, int *smem_bytes)
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    size_t need = 0;
+    for (const auto &ch : c->ising) {
+        const size_t b = resident_bytes(c, ch);
+        if (b % 4 != 0)
+            return false;
+        need = b > need ? b : need;
+    }
+    if (smem_bytes)
+        *smem_bytes = (int)need;
+    return need + 1024 <= (size_t)optin;
+}
+
+// Raise the dynamic shared-memory limit of the resident kernels (outside any
+// graph capture).
+cudaError_t ising_prepare_resident(mc_ctx *c)
+{
+    int smem = 0;
+    if (!ising_resident_fits(c, &smem))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_resident<MC_LAYOUT_INT8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_resident<MC_LAYOUT_MSC32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
+cudaError_t ising_init_launch(mc_ctx *c, const mc_chain_desc *desc)
+{
+    for (int k = 0; k < c->n_chains; ++k) {
+        const IsingChain &ch = c->ising[k];
+        char *p = c->d_lattice + ch.spin_off;
+        if (c->layout == MC_LAYOUT_INT8) {
+            k_init_int8<<<blocks_for((size_t)ch.Lx * ch.Ly, 256), 256, 0, c->ls>>>(
+                ch, reinterpret_cast<int8_t *>(p), desc[k].start == MC_HOT);
+        } else {
+            k_init_msc<<<blocks_for((size_t)2 * ch.Ly * ch.W, 256), 256, 0, c->ls>>>(
+                ch, reinterpret_cast<uint32_t *>(p), desc[k].start == MC_HOT);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t advance_state_launch(mc_ctx *c, long long n, long long recs)
+{
+    k_advance<<<1, 1, 0, c->ls>>>(c->d_state, (unsigned long long)n, (unsigned long long)recs);
+    return cudaGetLastError();
+}
+
+cudaError_t ising_sweep_enqueue(mc_ctx *c, long long n, int every, int mode)
+{
+    SweepArgs a{};
+    a.chains = c->d_chains;
+    a.block_start = c->d_block_start;
+    a.n_chains = c->n_chains;
+    a.lattice = c->d_lattice;
+    a.series = c->d_series;
+    a.state = c->d_state;
+    a.cap = c->cap;
+    a.tries = nullptr;
+    if (mode == MC_MODE_RESIDENT) {
+        int smem = 0;
+        if (!ising_resident_fits(c, &smem))
+            return cudaErrorInvalidValue;
+        const int threads = c->threads;
+        cudaError_t e = prof_begin(c);
+        if (e != cudaSuccess)
+            return e;
+        if (c->layout == MC_LAYOUT_INT8)
+            k_resident<MC_LAYOUT_INT8><<<c->n_chains, threads, smem, c->ls>>>(a, (uint32_t)n, (uint32_t)every);
+        else
+            k_resident<MC_LAYOUT_MSC32><<<c->n_chains, threads, smem, c->ls>>>(a, (uint32_t)n, (uint32_t)every);
+        e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+        return prof_end(c);
+    }
+    for (long long t = 0; t < n; ++t) {
+        a.k = (uint32_t)t;
+        a.measure = every > 0 && ((t + 1) % every) == 0;
+        a.rec_k = a.measure ? (uint32_t)((t + 1) / every - 1) : 0u;
+        for (int colour = 0; colour < 2; ++colour) {
+            cudaError_t e = prof_begin(c);
+            if (e != cudaSuccess)
+                return e;
+            if (c->layout == MC_LAYOUT_INT8) {
+                if (colour == 0)
+                    k_half_sweep<0, MC_LAYOUT_INT8><<<c->grid_blocks, c->threads, 0, c->ls>>>(a);
+                else
+                    k_half_sweep<1, MC_LAYOUT_INT8><<<c->grid_blocks, c->threads, 0, c->ls>>>(a);
+            } else {
+                if (colour == 0)
+                    k_half_sweep<0, MC_LAYOUT_MSC32><<<c->grid_blocks, c->threads, 0, c->ls>>>(a);
+                else
+                    k_half_sweep<1, MC_LAYOUT_MSC32><<<c->grid_blocks, c->threads, 0, c->ls>>>(a);
+            }
+            e = prof_end(c);
+            if (e != cudaSuccess)
+                return e;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ising_measure_launch(mc_ctx *c, int chain, DevRecord *out)
+{
+    const IsingChain &ch = c->ising[chain];
+    const char *lat = c->d_lattice + ch.spin_off;
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(DevRecord), c->ls);
+    if (e != cudaSuccess)
+        return e;
+    if (c->layout == MC_LAYOUT_INT8)
+        k_measure<MC_LAYOUT_INT8><<<blocks_for(((size_t)ch.Lx * ch.Ly) >> 1, 256), 256, 0, c->ls>>>(ch, lat, out);
+    else
+        k_measure<MC_LAYOUT_MSC32><<<blocks_for((size_t)ch.Ly * ch.W, 256), 256, 0, c->ls>>>(ch, lat, out);
+    return cudaGetLastError();
+}
+
+cudaError_t ising_config_io(mc_ctx *c, int chain, int fmt, void *buf, bool to_lattice)
+{
+    const IsingChain &ch = c->ising[chain];
+    char *lat = c->d_lattice + ch.spin_off;
+    const size_t n = (size_t)ch.Lx * ch.Ly;
+    if (c->layout == MC_LAYOUT_INT8) {
+        if (fmt == MC_FMT_INT8)
+            return to_lattice ? cudaMemcpyAsync(lat, buf, n, cudaMemcpyDeviceToDevice, c->ls)
+                              : cudaMemcpyAsync(buf, lat, n, cudaMemcpyDeviceToDevice, c->ls);
+        if (to_lattice)
+            k_int8_from_bits<<<blocks_for(n, 256), 256, 0, c->ls>>>(ch, static_cast<const uint32_t *>(buf),
+                                                                        reinterpret_cast<int8_t *>(lat));
+        else
+            k_int8_to_bits<<<blocks_for(n / 32, 256), 256, 0, c->ls>>>(ch, reinterpret_cast<const int8_t *>(lat),
+                                                                           static_cast<uint32_t *>(buf));
+        return cudaGetLastError();
+    }
+    const size_t words = (size_t)2 * ch.Ly * ch.W;
+    uint32_t *msc = reinterpret_cast<uint32_t *>(lat);
+    if (fmt == MC_FMT_INT8) {
+        if (to_lattice)
+            k_msc_from_int8<<<blocks_for(words, 256), 256, 0, c->ls>>>(ch, static_cast<const int8_t *>(buf), msc);
+        else
+            k_msc_to_int8<<<blocks_for(words, 256), 256, 0, c->ls>>>(ch, msc, static_cast<int8_t *>(buf));
+    } else {
+        if (to_lattice)
+            k_msc_from_bits<<<blocks_for(words, 256), 256, 0, c->ls>>>(ch, static_cast<const uint32_t *>(buf), msc);
+        else
+            k_msc_to_bits<<<blocks_for(n / 32, 256), 256, 0, c->ls>>>(ch, msc, static_cast<uint32_t *>(buf));
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mc

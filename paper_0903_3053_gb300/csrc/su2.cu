@@ -1,0 +1,479 @@
+// su2.cu -- 4D SU(2) pure-gauge heat-bath (Sec. 2.4).
+//
+// Links are the quaternions (U0, U1, U2, U3) of Eq. (4), one float4 per link,
+// stored per chain as [parity][mu][site-within-parity] so that the 32 links a
+// warp reads for one neighbour direction are 512 contiguous bytes.  Canonical
+// site index s = x1 + L1 (x2 + L2 (x3 + L3 x0)) (mu = 0 is time); with L1 even,
+// the index of s within its parity class is s >> 1.
+//
+// One kernel per (parity p, direction mu) phase, in the order of Sec. 2.4
+// (mu = 0..3 on odd sites, then on even sites), one thread per site of parity p:
+//   1. staple W of Eq. (6), summed over the six nu != mu (the paper's separate
+//      staple kernel and its N_vect staple buffer are fused away: W lives in
+//      registers only);
+//   2. k = |W|, V = W / k, alpha = beta k;
+//   3. a0 from Kennedy-Pendleton (up to 8 tries, the "8 attempts per start" of
+//      Sec. 2.4), then Creutz (up to 64 tries); a link whose every try fails is
+//      left unchanged and counted (still exact: the failure probability depends
+//      on alpha only);
+//   4. a uniform direction on S^2 for the remaining components;
+//   5. U = X V (Eq. (5) with w = X/k) and reprojection onto SU(2) (U / |U|).
+// Try t of the link at parity index e uses the Philox block
+// (e, sweep, TAG_HB | p<<12 | mu<<8 | t, chain); the direction uses
+// (e, sweep, TAG_DIR | p<<12 | mu<<8, chain).  Uniforms are ((r>>8)+1) 2^-24.
+// FP32 throughout (logf/cospif/sincospif/expm1f/log1pf, not the fast
+// intrinsics), FP64 only in the plaquette sums.
+#include "mc_internal.cuh"
+
+namespace mc {
+namespace {
+
+// (a0 + i a.sigma)(b0 + i b.sigma) = (a0 b0 - a.b) + i (a0 b + b0 a - a x b).sigma
+__device__ __forceinline__ float4 qmul(float4 a, float4 b)
+{
+    return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
+                       a.x * b.y + b.x * a.y - (a.z * b.w - a.w * b.z),
+                       a.x * b.z + b.x * a.z - (a.w * b.y - a.y * b.w),
+                       a.x * b.w + b.x * a.w - (a.y * b.z - a.z * b.y));
+}
+__device__ __forceinline__ float4 qdag(float4 a) { return make_float4(a.x, -a.y, -a.z, -a.w); }
+__device__ __forceinline__ float4 qadd(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float qdot(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+
+struct Site {
+    int x[4];
+};
+
+__device__ __forceinline__ Site site_from_parity_index(const Su2Chain &ch, int p, uint32_t e)
+{
+    const uint32_t L1h = (uint32_t)ch.L[1] >> 1;
+    uint32_t r = e;
+    const int x1h = (int)(r % L1h);
+    r /= L1h;
+    Site s;
+    s.x[2] = (int)(r % (uint32_t)ch.L[2]);
+    r /= (uint32_t)ch.L[2];
+    s.x[3] = (int)(r % (uint32_t)ch.L[3]);
+    s.x[0] = (int)(r / (uint32_t)ch.L[3]);
+    s.x[1] = 2 * x1h + ((p + s.x[0] + s.x[2] + s.x[3]) & 1);
+    return s;
+}
+
+__device__ __forceinline__ uint32_t canonical(const Su2Chain &ch, const Site &s)
+{
+    return (uint32_t)(s.x[1] + ch.L[1] * (s.x[2] + ch.L[2] * (s.x[3] + ch.L[3] * s.x[0])));
+}
+
+template <int D>
+__device__ __forceinline__ Site step(const Su2Chain &ch, Site s, int dir)
+{
+    s.x[D] += dir;
+    if (s.x[D] == ch.L[D])
+        s.x[D] = 0;
+    else if (s.x[D] < 0)
+        s.x[D] = ch.L[D] - 1;
+    return s;
+}
+
+__device__ __forceinline__ float4 load_link(const float4 *__restrict__ U, uint32_t nh, int par, int dir, uint32_t e)
+{
+    return __ldg(&U[(size_t)(par * 4 + dir) * nh + e]);
+}
+
+template <int MU, int NU, int P>
+__device__ __forceinline__ float4 staple_pair(const float4 *__restrict__ U, const Su2Chain &ch, const Site &x,
+                                              uint32_t e)
+{
+    constexpr int Q = 1 - P;
+    const uint32_t nh = ch.nh;
+    const Site xpn = step<NU>(ch, x, +1);
+    const Site xpm = step<MU>(ch, x, +1);
+    const Site xmn = step<NU>(ch, x, -1);
+    const Site xmnpm = step<MU>(ch, xmn, +1);
+    const float4 a = load_link(U, nh, P, NU, e);
+    const float4 b = load_link(U, nh, Q, MU, canonical(ch, xpn) >> 1);
+    const float4 c = load_link(U, nh, Q, NU, canonical(ch, xpm) >> 1);
+    const uint32_t emn = canonical(ch, xmn) >> 1;
+    const float4 d = load_link(U, nh, Q, NU, emn);
+    const float4 f = load_link(U, nh, Q, MU, emn);
+    const float4 g = load_link(U, nh, P, NU, canonical(ch, xmnpm) >> 1);
+    // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+  +  U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu)
+    return qadd(qmul(qmul(a, b), qdag(c)), qmul(qmul(qdag(d), f), g));
+}
+
+template <int MU, int P>
+__device__ __forceinline__ float4 staple(const float4 *__restrict__ U, const Su2Chain &ch, const Site &x, uint32_t e)
+{
+    float4 W = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (MU != 0) W = qadd(W, staple_pair<MU, 0, P>(U, ch, x, e));
+    if (MU != 1) W = qadd(W, staple_pair<MU, 1, P>(U, ch, x, e));
+    if (MU != 2) W = qadd(W, staple_pair<MU, 2, P>(U, ch, x, e));
+    if (MU != 3) W = qadd(W, staple_pair<MU, 3, P>(U, ch, x, e));
+    return W;
+}
+
+constexpr int kKpTries = 8;
+constexpr int kCreutzTries = 64;
+constexpr uint8_t kFailed = 255;
+
+// Heat-bath draw of a0 ~ sqrt(1-a0^2) exp(alpha a0); returns the try taken.
+__device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, uint32_t sel, const Su2Chain &ch,
+                                       float &a0)
+{
+    if (alpha > 0.f) {
+        const float inv2a = 0.5f / alpha;
+        for (int t = 0; t < kKpTries; ++t) {
+            const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id),
+                                          ch.key);
+            const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
+            const float u3 = uniform_open0(r.z), u4 = uniform_open0(r.w);
+            const float cs = cospif(2.0f * u2);
+            const float lam2 = -(logf(u1) + cs * cs * logf(u3)) * inv2a;
+            if (u4 * u4 <= 1.0f - lam2) {
+                a0 = 1.0f - 2.0f * lam2;
+                return t;
+            }
+        }
+    }
+    const float cexp = alpha > 0.f ? -expm1f(-2.0f * alpha) : 0.f; // 1 - e^{-2 alpha}
+    for (int t = kKpTries; t < kKpTries + kCreutzTries; ++t) {
+        const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ch.key);
+        const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
+        const float c = alpha > 0.f ? 1.0f + log1pf(-(1.0f - u1) * cexp) / alpha : 2.0f * u1 - 1.0f;
+        if (u2 * u2 <= 1.0f - c * c) {
+            a0 = c;
+            return t;
+        }
+    }
+    return kFailed;
+}
+
+template <int P, int MU>
+__global__ void __launch_bounds__(256) k_phase(SweepArgs a)
+{
+    const int k = find_chain(a.block_start, a.n_chains, blockIdx.x);
+    const Su2Chain ch = static_cast<const Su2Chain *>(a.chains)[k];
+    const uint32_t e = (blockIdx.x - a.block_start[k]) * blockDim.x + threadIdx.x;
+    if (e >= ch.nh)
+        return;
+    float4 *U = reinterpret_cast<float4 *>(a.lattice + ch.link_off);
+    const uint32_t sweep = (uint32_t)(a.state->sweep_base + a.k);
+    const Site x = site_from_parity_index(ch, P, e);
+    const float4 W = staple<MU, P>(U, ch, x, e);
+    const float k2 = qdot(W, W);
+    const float kn = sqrtf(k2);
+    float4 V = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (kn > 0.f) {
+        const float inv = 1.0f / kn;
+        V = make_float4(W.x * inv, W.y * inv, W.z * inv, W.w * inv);
+    }
+    const uint32_t sel = ((uint32_t)P << 12) | ((uint32_t)MU << 8);
+    float a0 = 0.f;
+    const int t = draw_a0(ch.beta * kn, e, sweep, sel, ch, a0);
+    if (a.tries)
+        a.tries[ch.tries_off + (size_t)canonical(ch, x) * 4 + MU] = (uint8_t)t;
+    if (t == kFailed) {
+        atomicAdd(&a.state->hb_failures, 1ull);
+        return;
+    }
+    const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ch.key);
+    const float ct = 2.0f * uniform_open0(r.x) - 1.0f;
+    float sphi, cphi;
+    sincospif(2.0f * uniform_open0(r.y), &sphi, &cphi);
+    const float st = sqrtf(fmaxf(0.f, 1.0f - ct * ct));
+    const float rad = sqrtf(fmaxf(0.f, 1.0f - a0 * a0));
+    const float4 X = make_float4(a0, rad * st * cphi, rad * st * sphi, rad * ct);
+    float4 Un = qmul(X, V);
+    const float nrm = rsqrtf(qdot(Un, Un));
+    Un = make_float4(Un.x * nrm, Un.y * nrm, Un.z * nrm, Un.w * nrm);
+    U[(size_t)(P * 4 + MU) * ch.nh + e] = Un;
+}
+
+// ------------------------------------------------------------------ plaquette
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per-block partial sums of (1/2) Tr U_munu(x) of Eq. (3), spatial and temporal
+// separately (the two FP64 values per measuring thread of Sec. 2.4).  Products
+// in FP32, sums in FP64.  One thread per site; partial[2 b], partial[2 b + 1].
+__global__ void __launch_bounds__(256) k_plaquette(const Su2Chain *chains, const uint32_t *meas_start, int n_chains,
+                                                   const char *lattice, double *partial)
+{
+    __shared__ double ss[8], st[8];
+    const int k = find_chain(meas_start, n_chains, blockIdx.x);
+    const Su2Chain ch = chains[k];
+    const uint32_t s = (blockIdx.x - meas_start[k]) * blockDim.x + threadIdx.x;
+    const uint32_t n = 2 * ch.nh;
+    double ps = 0.0, pt = 0.0;
+    if (s < n) {
+        const float4 *U = reinterpret_cast<const float4 *>(lattice + ch.link_off);
+        Site x;
+        uint32_t r = s;
+        x.x[1] = (int)(r % (uint32_t)ch.L[1]);
+        r /= (uint32_t)ch.L[1];
+        x.x[2] = (int)(r % (uint32_t)ch.L[2]);
+        r /= (uint32_t)ch.L[2];
+        x.x[3] = (int)(r % (uint32_t)ch.L[3]);
+        x.x[0] = (int)(r / (uint32_t)ch.L[3]);
+        const int p = (x.x[0] + x.x[1] + x.x[2] + x.x[3]) & 1, q = 1 - p;
+        const uint32_t e = s >> 1;
+        float4 Ux[4], Uf[4][4]; // Uf[mu][nu] = U_nu(x + mu)
+        Site xf[4];
+        xf[0] = step<0>(ch, x, +1);
+        xf[1] = step<1>(ch, x, +1);
+        xf[2] = step<2>(ch, x, +1);
+        xf[3] = step<3>(ch, x, +1);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+            Ux[mu] = load_link(U, ch.nh, p, mu, e);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const uint32_t ef = canonical(ch, xf[mu]) >> 1;
+#pragma unroll
+            for (int nu = 0; nu < 4; ++nu)
+                if (nu != mu)
+                    Uf[mu][nu] = load_link(U, ch.nh, q, nu, ef);
+        }
+        float fs = 0.f, ft = 0.f;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                // (1/2) Tr[U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+] = A . B
+                const float4 A = qmul(Ux[mu], Uf[mu][nu]);
+                const float4 B = qmul(Ux[nu], Uf[nu][mu]);
+                const float h = qdot(A, B);
+                if (mu == 0)
+                    ft += h;
+                else
+                    fs += h;
+            }
+        ps = (double)fs;
+        pt = (double)ft;
+    }
+    ps = warp_sum(ps);
+    pt = warp_sum(pt);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        ss[w] = ps;
+        st[w] = pt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a += ss[i];
+            b += st[i];
+        }
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// One block per chain (blockIdx.x = chain index, or `only` when >= 0): fixed-order
+// sum of the chain's partials, written as P, P_s, P_t.
+__global__ void __launch_bounds__(256) k_plaquette_final(const Su2Chain *chains, const uint32_t *meas_start,
+                                                         const double *partial, DevRecord *series, long long cap,
+                                                         const DevState *state, uint32_t ksweep, uint32_t rec_k,
+                                                         int only, DevRecord *out)
+{
+    __shared__ double ss[8], st[8];
+    const int k = only >= 0 ? only : (int)blockIdx.x;
+    const uint32_t b0 = meas_start[k], b1 = meas_start[k + 1];
+    double a = 0.0, b = 0.0;
+    for (uint32_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        a += partial[2 * i];
+        b += partial[2 * i + 1];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        ss[w] = a;
+        st[w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0)
+        return;
+    double A = 0.0, B = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+        A += ss[i];
+        B += st[i];
+    }
+    const double n = 2.0 * (double)chains[k].nh;
+    DevRecord *rec = out;
+    long long sweep = (long long)(state->sweep_base + ksweep);
+    if (!rec) {
+        const unsigned long long slot = (state->rec_head + rec_k) % (unsigned long long)cap;
+        rec = &series[(long long)k * cap + (long long)slot];
+    } else {
+        sweep = (long long)state->sweep_base - 1;
+    }
+    rec->sweep = sweep;
+    rec->a = rec->b = 0;
+    rec->d0 = (A + B) / (6.0 * n);
+    rec->d1 = A / (3.0 * n);
+    rec->d2 = B / (3.0 * n);
+}
+
+// ------------------------------------------------------------------ init / I/O
+// Hot start: Haar-random link = normalised 4-vector of four Box-Muller normals
+// from the Philox block (s, 0, TAG_INIT | mu, chain); cold start: identity.
+__global__ void k_su2_init(Su2Chain ch, float4 *U, int hot)
+{
+    const uint32_t n = 2 * ch.nh;
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4 * n)
+        return;
+    const uint32_t s = idx >> 2, mu = idx & 3u;
+    float4 v = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (hot) {
+        const uint4 r = philox4x32_10(make_uint4(s, 0u, kTagSu2Init | mu, ch.chain_id), ch.key);
+        const float ra = sqrtf(-2.0f * logf(uniform_open0(r.x)));
+        const float rb = sqrtf(-2.0f * logf(uniform_open0(r.z)));
+        float sa, ca, sb, cb;
+        sincospif(2.0f * uniform_open0(r.y), &sa, &ca);
+        sincospif(2.0f * uniform_open0(r.w), &sb, &cb);
+        v = make_float4(ra * ca, ra * sa, rb * cb, rb * sb);
+        const float inv = rsqrtf(qdot(v, v));
+        v = make_float4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
+    }
+    // parity of s from its coordinates
+    uint32_t r = s;
+    int x1 = (int)(r % (uint32_t)ch.L[1]);
+    r /= (uint32_t)ch.L[1];
+    int x2 = (int)(r % (uint32_t)ch.L[2]);
+    r /= (uint32_t)ch.L[2];
+    int x3 = (int)(r % (uint32_t)ch.L[3]);
+    int x0 = (int)(r / (uint32_t)ch.L[3]);
+    const int p = (x0 + x1 + x2 + x3) & 1;
+    U[(size_t)(p * 4 + mu) * ch.nh + (s >> 1)] = v;
+}
+
+// canonical float q[s][mu][4] <-> internal [parity][mu][s >> 1]
+__global__ void k_su2_io(Su2Chain ch, float4 *U, float4 *canon, int to_lattice)
+{
+    const uint32_t n = 2 * ch.nh;
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4 * n)
+        return;
+    const uint32_t s = idx >> 2, mu = idx & 3u;
+    uint32_t r = s;
+    int x1 = (int)(r % (uint32_t)ch.L[1]);
+    r /= (uint32_t)ch.L[1];
+    int x2 = (int)(r % (uint32_t)ch.L[2]);
+    r /= (uint32_t)ch.L[2];
+    int x3 = (int)(r % (uint32_t)ch.L[3]);
+    int x0 = (int)(r / (uint32_t)ch.L[3]);
+    const int p = (x0 + x1 + x2 + x3) & 1;
+    float4 *in = &U[(size_t)(p * 4 + mu) * ch.nh + (s >> 1)];
+    if (to_lattice)
+        *in = canon[idx];
+    else
+        canon[idx] = *in;
+}
+
+inline unsigned blocks_for(size_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+template <int P>
+void launch_phase(mc_ctx *c, const SweepArgs &a, int mu)
+{
+    if (prof_begin(c) != cudaSuccess)
+        return;
+    switch (mu) {
+    case 0: k_phase<P, 0><<<c->grid_blocks, c->threads, 0, c->ls>>>(a); break;
+    case 1: k_phase<P, 1><<<c->grid_blocks, c->threads, 0, c->ls>>>(a); break;
+    case 2: k_phase<P, 2><<<c->grid_blocks, c->threads, 0, c->ls>>>(a); break;
+    default: k_phase<P, 3><<<c->grid_blocks, c->threads, 0, c->ls>>>(a); break;
+    }
+    prof_end(c);
+}
+
+}  // namespace
+
+// =========================================================================== host
+size_t su2_config_bytes(const Su2Chain &ch) { return (size_t)2 * ch.nh * 4 * sizeof(float4); }
+
+void su2_plan_grid(mc_ctx *c)
+{
+    c->block_start.assign(c->n_chains + 1, 0);
+    c->meas_start.assign(c->n_chains + 1, 0);
+    uint32_t acc = 0, macc = 0;
+    for (int k = 0; k < c->n_chains; ++k) {
+        c->block_start[k] = acc;
+        c->meas_start[k] = macc;
+        acc += blocks_for(c->su2[k].nh, c->threads);
+        macc += blocks_for((size_t)2 * c->su2[k].nh, 256);
+    }
+    c->block_start[c->n_chains] = acc;
+    c->meas_start[c->n_chains] = macc;
+    c->grid_blocks = acc;
+    c->meas_blocks = macc;
+}
+
+cudaError_t su2_init_launch(mc_ctx *c, const mc_chain_desc *desc)
+{
+    for (int k = 0; k < c->n_chains; ++k) {
+        const Su2Chain &ch = c->su2[k];
+        k_su2_init<<<blocks_for((size_t)8 * ch.nh, 256), 256, 0, c->ls>>>(
+            ch, reinterpret_cast<float4 *>(c->d_lattice + ch.link_off), desc[k].start == MC_HOT);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t plaquette_launch(mc_ctx *c, uint32_t ksweep, uint32_t rec_k, int only, DevRecord *out)
+{
+    k_plaquette<<<c->meas_blocks, 256, 0, c->ls>>>(static_cast<const Su2Chain *>(c->d_chains), c->d_meas_start,
+                                                       c->n_chains, c->d_lattice, c->d_partials);
+    const unsigned nb = only >= 0 ? 1u : (unsigned)c->n_chains;
+    k_plaquette_final<<<nb, 256, 0, c->ls>>>(static_cast<const Su2Chain *>(c->d_chains), c->d_meas_start,
+                                                 c->d_partials, c->d_series, c->cap, c->d_state, ksweep, rec_k, only,
+                                                 out);
+    return cudaGetLastError();
+}
+
+cudaError_t su2_sweep_enqueue(mc_ctx *c, long long n, int every)
+{
+    SweepArgs a{};
+    a.chains = c->d_chains;
+    a.block_start = c->d_block_start;
+    a.n_chains = c->n_chains;
+    a.lattice = c->d_lattice;
+    a.series = c->d_series;
+    a.state = c->d_state;
+    a.cap = c->cap;
+    a.tries = c->record_tries ? c->d_tries : nullptr;
+    for (long long t = 0; t < n; ++t) {
+        a.k = (uint32_t)t;
+        for (int mu = 0; mu < 4; ++mu)
+            launch_phase<1>(c, a, mu); // odd sites first (Sec. 2.4)
+        for (int mu = 0; mu < 4; ++mu)
+            launch_phase<0>(c, a, mu);
+        if (every > 0 && ((t + 1) % every) == 0) {
+            cudaError_t e = plaquette_launch(c, (uint32_t)t, (uint32_t)((t + 1) / every - 1), -1, nullptr);
+            if (e != cudaSuccess)
+                return e;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t su2_measure_launch(mc_ctx *c, int chain, DevRecord *out)
+{
+    return plaquette_launch(c, 0, 0, chain, out);
+}
+
+cudaError_t su2_config_io(mc_ctx *c, int chain, void *dev_buf, bool to_lattice)
+{
+    const Su2Chain &ch = c->su2[chain];
+    k_su2_io<<<blocks_for((size_t)8 * ch.nh, 256), 256, 0, c->ls>>>(
+        ch, reinterpret_cast<float4 *>(c->d_lattice + ch.link_off), static_cast<float4 *>(dev_buf), to_lattice);
+    return cudaGetLastError();
+}
+
+}  // namespace mc

@@ -1,0 +1,302 @@
+"""Thin ctypes binding of libmc.so (include/mc.h).
+
+Argument marshalling only: every step of the sweep runs in the library's CUDA
+kernels.  PyTorch supplies device memory (the workspace tensor) and the CUDA
+stream.  There is no CPU fallback: if libmc.so cannot be loaded or no GPU is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_ESTATE, MC_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+MC_COLD, MC_HOT = 0, 1
+MC_KIND_ISING, MC_KIND_SU2 = 1, 2
+MC_LAYOUT_INT8, MC_LAYOUT_MSC32 = 0, 1
+MC_FMT_INT8, MC_FMT_BITS, MC_FMT_F32 = 0, 1, 2
+MC_MODE_AUTO, MC_MODE_GRID, MC_MODE_RESIDENT = 0, 1, 2
+
+#: every symbol include/mc.h declares (checked by the ABI test)
+EXPORTS = [
+    "mc_workspace_bytes", "mc_batch_init", "mc_ising_init", "mc_su2_init", "mc_sweep", "mc_set_mode", "mc_sync",
+    "mc_measure", "mc_read_series", "mc_get_config", "mc_set_config", "mc_config_bytes", "mc_get_sweep",
+    "mc_set_sweep", "mc_su2_record_tries", "mc_su2_get_tries", "mc_su2_failed_updates", "mc_destroy",
+    "mc_last_error", "mc_version", "mc_profile_enable", "mc_profile_read",
+]
+
+
+class mc_chain_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("L", ctypes.c_int32 * 4), ("beta", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("chain_id", ctypes.c_uint32), ("start", ctypes.c_int32)]
+
+
+class mc_record(ctypes.Structure):
+    _fields_ = [("sweep", ctypes.c_int64), ("E", ctypes.c_int64), ("M", ctypes.c_int64), ("P", ctypes.c_double),
+                ("Ps", ctypes.c_double), ("Pt", ctypes.c_double)]
+
+
+RECORD_DTYPE = np.dtype([("sweep", "<i8"), ("E", "<i8"), ("M", "<i8"), ("P", "<f8"), ("Ps", "<f8"), ("Pt", "<f8")])
+assert ctypes.sizeof(mc_chain_desc) == 48 and ctypes.sizeof(mc_record) == 48 == RECORD_DTYPE.itemsize
+
+
+class MCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libmc status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libmc.so (building it with nvcc first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libmc.so not found at {_build.LIB}; run paper_0903_3053_gb300.build.build()")
+    L = ctypes.CDLL(_build.LIB)
+    c, P = ctypes, ctypes.c_void_p
+    st = c.c_int
+    sig = {
+        "mc_workspace_bytes": (c.c_size_t, [c.c_int32, P, c.c_int32, c.c_int64]),
+        "mc_batch_init": (st, [P, c.c_int32, P, c.c_int32, c.c_int64, P, c.c_size_t, P]),
+        "mc_ising_init": (st, [P, P, c.c_double, c.c_uint64, c.c_int32, c.c_int32, c.c_int64, P, c.c_size_t, P]),
+        "mc_su2_init": (st, [P, P, c.c_double, c.c_uint64, c.c_int32, c.c_int64, P, c.c_size_t, P]),
+        "mc_sweep": (st, [P, c.c_int64, c.c_int32]),
+        "mc_set_mode": (st, [P, c.c_int32, c.c_int32]),
+        "mc_sync": (st, [P]),
+        "mc_measure": (st, [P, c.c_int32, P]),
+        "mc_read_series": (st, [P, P, c.c_int64, P]),
+        "mc_get_config": (st, [P, c.c_int32, c.c_int32, P, c.c_int32]),
+        "mc_set_config": (st, [P, c.c_int32, c.c_int32, P, c.c_int32]),
+        "mc_config_bytes": (c.c_size_t, [P, c.c_int32, c.c_int32]),
+        "mc_get_sweep": (st, [P, P]),
+        "mc_set_sweep": (st, [P, c.c_int64]),
+        "mc_su2_record_tries": (st, [P, c.c_int32]),
+        "mc_su2_get_tries": (st, [P, c.c_int32, P]),
+        "mc_su2_failed_updates": (st, [P, P]),
+        "mc_destroy": (st, [P]),
+        "mc_profile_enable": (st, [P, c.c_int32]),
+        "mc_profile_read": (st, [P, P, P]),
+        "mc_last_error": (c.c_char_p, []),
+        "mc_version": (c.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != MC_OK:
+        raise MCError(status, load().mc_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libmc needs a CUDA GPU; no CPU fallback exists")
+    return torch
+
+
+@dataclass
+class Chain:
+    """One Markov chain.  Ising: L = (Lx, Ly); SU(2): L = (L0, L1, L2, L3), mu = 0 time."""
+    kind: int
+    L: tuple
+    beta: float
+    seed: int
+    chain_id: int = 0
+    start: int = MC_HOT
+
+    def desc(self) -> mc_chain_desc:
+        d = mc_chain_desc()
+        d.kind = self.kind
+        L = list(self.L) + [1] * (4 - len(self.L))
+        for i in range(4):
+            d.L[i] = int(L[i])
+        d.beta = float(self.beta)
+        d.seed = int(self.seed) & 0xFFFFFFFFFFFFFFFF
+        d.chain_id = int(self.chain_id) & 0xFFFFFFFF
+        d.start = int(self.start)
+        return d
+
+
+def ising(L, beta, seed, chain_id=0, hot=True) -> Chain:
+    L = (L, L) if np.isscalar(L) else tuple(L)
+    return Chain(MC_KIND_ISING, L, beta, seed, chain_id, MC_HOT if hot else MC_COLD)
+
+
+def su2(L, beta, seed, chain_id=0, hot=True) -> Chain:
+    L = (L,) * 4 if np.isscalar(L) else tuple(L)
+    return Chain(MC_KIND_SU2, L, beta, seed, chain_id, MC_HOT if hot else MC_COLD)
+
+
+def mc_workspace_bytes(chains, layout=MC_LAYOUT_INT8, series_capacity=1024) -> int:
+    arr = (mc_chain_desc * len(chains))(*[c.desc() for c in chains])
+    n = load().mc_workspace_bytes(len(chains), arr, layout, series_capacity)
+    if n == 0:
+        raise MCError(MC_EINVAL, load().mc_last_error().decode())
+    return int(n)
+
+
+class Batch:
+    """A batch of chains of one kind, advanced together on one CUDA stream."""
+
+    def __init__(self, chains, layout=MC_LAYOUT_INT8, series_capacity=1024, stream=None, device=None):
+        torch = _torch()
+        L = load()
+        self.chains = list(chains)
+        self.kind = self.chains[0].kind
+        self.layout = layout
+        self.cap = int(series_capacity)
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        arr = (mc_chain_desc * len(self.chains))(*[c.desc() for c in self.chains])
+        nbytes = L.mc_workspace_bytes(len(self.chains), arr, layout, self.cap)
+        if nbytes == 0:
+            raise MCError(MC_EINVAL, L.mc_last_error().decode())
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        if self.workspace.data_ptr() % 256:
+            raise RuntimeError("workspace tensor is not 256-byte aligned")
+        self._ctx = ctypes.c_void_p()
+        _check(L.mc_batch_init(ctypes.byref(self._ctx), len(self.chains), arr, layout, self.cap,
+                               ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                               ctypes.c_void_p(self.stream.cuda_stream)))
+
+    # -- sweeping ---------------------------------------------------------------
+    def sweep(self, n: int, measure_every: int = 0):
+        _check(load().mc_sweep(self._ctx, int(n), int(measure_every)))
+
+    def set_mode(self, mode: int, threads_per_block: int = 0):
+        _check(load().mc_set_mode(self._ctx, int(mode), int(threads_per_block)))
+
+    def sync(self):
+        _check(load().mc_sync(self._ctx))
+
+    @property
+    def sweeps_done(self) -> int:
+        v = ctypes.c_int64()
+        _check(load().mc_get_sweep(self._ctx, ctypes.byref(v)))
+        return int(v.value)
+
+    @sweeps_done.setter
+    def sweeps_done(self, value: int):
+        _check(load().mc_set_sweep(self._ctx, int(value)))
+
+    # -- observables --------------------------------------------------------------
+    def measure(self, chain: int = 0) -> dict:
+        r = mc_record()
+        _check(load().mc_measure(self._ctx, int(chain), ctypes.byref(r)))
+        return {"sweep": r.sweep, "E": r.E, "M": r.M, "P": r.P, "Ps": r.Ps, "Pt": r.Pt}
+
+    def read_series(self, max_per_chain: int | None = None) -> np.ndarray:
+        """Unread records as a structured array of shape (n_chains, n)."""
+        m = self.cap if max_per_chain is None else int(max_per_chain)
+        out = np.zeros((len(self.chains), m), dtype=RECORD_DTYPE)
+        n = ctypes.c_int64()
+        _check(load().mc_read_series(self._ctx, ctypes.c_void_p(out.ctypes.data), m, ctypes.byref(n)))
+        return out[:, : n.value].copy()
+
+    # -- configurations ---------------------------------------------------------------
+    def config_bytes(self, chain: int, fmt: int) -> int:
+        return int(load().mc_config_bytes(self._ctx, int(chain), int(fmt)))
+
+    def _shape(self, chain: int, fmt: int):
+        c = self.chains[chain]
+        if self.kind == MC_KIND_ISING:
+            Lx, Ly = c.L[0], c.L[1]
+            return ((Ly, Lx), np.int8) if fmt == MC_FMT_INT8 else ((Ly, Lx // 32), np.uint32)
+        n = int(np.prod(c.L))
+        return (n, 4, 4), np.float32
+
+    def get_config(self, chain: int = 0, fmt: int | None = None) -> np.ndarray:
+        fmt = self._default_fmt() if fmt is None else fmt
+        shape, dt = self._shape(chain, fmt)
+        out = np.zeros(shape, dtype=dt)
+        _check(load().mc_get_config(self._ctx, int(chain), int(fmt), ctypes.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def set_config(self, chain: int, data: np.ndarray, fmt: int | None = None):
+        fmt = self._default_fmt() if fmt is None else fmt
+        shape, dt = self._shape(chain, fmt)
+        a = np.ascontiguousarray(data, dtype=dt).reshape(shape)
+        _check(load().mc_set_config(self._ctx, int(chain), int(fmt), ctypes.c_void_p(a.ctypes.data), 0))
+        self.sync()  # the host buffer `a` is released when this returns
+
+    def get_config_device(self, chain: int, out_tensor, fmt: int | None = None):
+        fmt = self._default_fmt() if fmt is None else fmt
+        _check(load().mc_get_config(self._ctx, int(chain), int(fmt), ctypes.c_void_p(out_tensor.data_ptr()), 1))
+
+    def set_config_device(self, chain: int, tensor, fmt: int | None = None):
+        fmt = self._default_fmt() if fmt is None else fmt
+        _check(load().mc_set_config(self._ctx, int(chain), int(fmt), ctypes.c_void_p(tensor.data_ptr()), 1))
+
+    def set_config_host_async(self, chain: int, host_tensor, fmt: int | None = None):
+        """Asynchronous upload from a page-locked host tensor (keep it unchanged
+        until the next synchronising call)."""
+        fmt = self._default_fmt() if fmt is None else fmt
+        _check(load().mc_set_config(self._ctx, int(chain), int(fmt), ctypes.c_void_p(host_tensor.data_ptr()), 0))
+
+    def _default_fmt(self):
+        return MC_FMT_INT8 if self.kind == MC_KIND_ISING else MC_FMT_F32
+
+    # -- SU(2) diagnostics --------------------------------------------------------------
+    def record_tries(self, enable: bool = True):
+        _check(load().mc_su2_record_tries(self._ctx, int(bool(enable))))
+
+    def get_tries(self, chain: int = 0) -> np.ndarray:
+        n = int(np.prod(self.chains[chain].L))
+        out = np.zeros((n, 4), dtype=np.uint8)
+        _check(load().mc_su2_get_tries(self._ctx, int(chain), ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def failed_updates(self) -> int:
+        v = ctypes.c_int64()
+        _check(load().mc_su2_failed_updates(self._ctx, ctypes.byref(v)))
+        return int(v.value)
+
+    # -- kernel timing --------------------------------------------------------------
+    def profile(self, enable: bool = True):
+        _check(load().mc_profile_enable(self._ctx, int(bool(enable))))
+
+    def profile_read(self):
+        """(launches, summed duration in ms) of the sweep kernels since the last read."""
+        n = ctypes.c_int64()
+        t = ctypes.c_double()
+        _check(load().mc_profile_read(self._ctx, ctypes.byref(n), ctypes.byref(t)))
+        return int(n.value), float(t.value)
+
+    # -- lifetime -----------------------------------------------------------------
+    def close(self):
+        if self._ctx:
+            st = load().mc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+            _check(st)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

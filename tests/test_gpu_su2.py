@@ -1,0 +1,168 @@
+"""GPU parity of the SU(2) heat-bath (Eqs. (2)-(7), Sec. 2.4) through the C ABI.
+
+FP32 quaternion links on the GPU against the FP64 2x2-matrix oracle: every link
+within 1e-5 after a sweep; an accept decision that FP32 and FP64 take
+differently is allowed only when it lies within 1e-6 of its threshold, and such
+events are counted and reported."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_0903_3053_gb300 as mc
+from conftest import binned_mean_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+EPS = 1e-6
+
+
+def f32_roundtrip(q):
+    return q.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (6, 4, 8, 2), (8, 8, 8, 8)])
+def test_init_matches_oracle(L):
+    for hot in (True, False):
+        b = mc.Batch([mc.su2(L, 2.3, seed=17, chain_id=4, hot=hot)])
+        g = b.get_config(0).astype(np.float64)
+        o = oracle.su2_init(L, 17, 4, hot)
+        assert np.abs(g - o).max() < 1e-6
+        b.close()
+
+
+@pytest.mark.parametrize("beta", [1.5, 2.0, 2.3, 2.6])
+@pytest.mark.parametrize("L,hot", [((4, 4, 4, 4), True), ((6, 4, 8, 2), True), ((8, 8, 8, 8), True),
+                                   ((8, 8, 8, 8), False)])
+def test_one_sweep_per_link(beta, L, hot):
+    """Same starting links on both sides (the oracle's start rounded to FP32),
+    one sweep; the oracle follows the GPU's try indices only where its own FP64
+    decision differs within EPS of the threshold."""
+    q0 = f32_roundtrip(oracle.su2_init(L, 5, 0, hot))
+    b = mc.Batch([mc.su2(L, beta, seed=5, chain_id=0, hot=hot)])
+    b.set_config(0, q0.astype(np.float32))
+    b.record_tries(True)
+    b.sweep(1)
+    g = b.get_config(0).astype(np.float64)
+    tries = b.get_tries(0)
+    q = q0.copy()
+    _, fails, near, bad = oracle.su2_sweep(q, L, beta, 5, 0, 0, forced_tries=tries, eps=EPS)
+    assert bad == 0, f"{bad} decisions differ by more than {EPS} from their thresholds"
+    err = np.abs(g - q).max()
+    assert err < TOL, err
+    assert b.failed_updates() == fails
+    print(f"near-threshold decisions: {near} of {tries.size}")
+    b.close()
+
+
+def test_multi_sweep_trajectory_follows_oracle():
+    """Five sweeps re-synchronised per sweep: the per-link error stays at FP32
+    round-off (no drift in the quaternion algebra)."""
+    L = (4, 6, 4, 4)
+    beta = 2.3
+    q = f32_roundtrip(oracle.su2_init(L, 8, 2, True))
+    b = mc.Batch([mc.su2(L, beta, seed=8, chain_id=2)])
+    b.set_config(0, q.astype(np.float32))
+    b.record_tries(True)
+    for k in range(5):
+        b.sweep(1)
+        tries = b.get_tries(0)
+        _, _, _, bad = oracle.su2_sweep(q, L, beta, 8, 2, k, forced_tries=tries, eps=EPS)
+        assert bad == 0
+        g = b.get_config(0).astype(np.float64)
+        assert np.abs(g - q).max() < TOL
+        q = g.copy()  # continue from the GPU's own FP32 state
+
+
+def test_plaquette_on_fixed_configuration():
+    L = (8, 6, 4, 6)
+    rng = np.random.default_rng(1)
+    q = rng.normal(size=(int(np.prod(L)), 4, 4))
+    q /= np.linalg.norm(q, axis=2, keepdims=True)
+    q = f32_roundtrip(q)
+    b = mc.Batch([mc.su2(L, 2.0, seed=1)])
+    b.set_config(0, q.astype(np.float32))
+    m = b.measure(0)
+    want = oracle.su2_plaquette(q, L)
+    assert abs(m["P"] - want[0]) < 1e-6
+    assert abs(m["Ps"] - want[1]) < 1e-6
+    assert abs(m["Pt"] - want[2]) < 1e-6
+    b.close()
+
+
+def test_unit_norm_and_series():
+    L = (8, 8, 8, 8)
+    b = mc.Batch([mc.su2(L, 2.3, seed=3)], series_capacity=64)
+    b.sweep(40, 4)
+    rec = b.read_series()
+    assert rec.shape == (1, 10)
+    np.testing.assert_array_equal(rec["sweep"][0], np.arange(3, 40, 4))
+    g = b.get_config(0).astype(np.float64).reshape(-1, 4)
+    assert np.abs(np.linalg.norm(g, axis=1) - 1).max() < 1e-6
+    # the recorded P of the last sweep equals a fresh measurement of the state
+    m = b.measure(0)
+    assert abs(m["P"] - rec["P"][0, -1]) < 1e-12
+    assert abs(m["P"] - (m["Ps"] + m["Pt"]) / 2) < 1e-12
+    b.close()
+
+
+def test_batch_of_uneven_chains():
+    rng = np.random.default_rng(0)
+    shapes = [(4, 4, 4, 4), (6, 6, 6, 6), (8, 8, 8, 8), (4, 6, 8, 4)]
+    chains = [mc.su2(s, float(rng.uniform(1.8, 2.6)), seed=1000 + k, chain_id=k, hot=bool(k % 2 == 0))
+              for k, s in enumerate(shapes)]
+    b = mc.Batch(chains)
+    b.record_tries(True)
+    starts = [b.get_config(k).astype(np.float64) for k in range(len(chains))]
+    b.sweep(1)
+    for k, c in enumerate(chains):
+        q = starts[k].copy()
+        tries = b.get_tries(k)
+        _, _, _, bad = oracle.su2_sweep(q, c.L, c.beta, c.seed, c.chain_id, 0, forced_tries=tries, eps=EPS)
+        assert bad == 0
+        assert np.abs(b.get_config(k).astype(np.float64) - q).max() < TOL
+    b.close()
+
+
+@pytest.mark.parametrize("L", [(32, 32, 32, 32), (8, 32, 32, 32)])
+def test_full_size_sampled_links(L):
+    """Full-size lattice, benchmark launch configuration: 20k sampled links of
+    one sweep recomputed in FP64 from the lattice each update saw."""
+    beta = 2.3
+    b = mc.Batch([mc.su2(L, beta, seed=1, chain_id=0)])
+    b.sweep(2)
+    pre = b.get_config(0).astype(np.float64)
+    b.record_tries(True)
+    b.sweep(1)
+    post = b.get_config(0).astype(np.float64)
+    tries = b.get_tries(0).reshape(-1)
+    rng = np.random.default_rng(7)
+    links = rng.choice(pre.shape[0] * 4, size=20_000, replace=False)
+    want, _, near, bad = oracle.su2_check_links(pre, post, L, beta, 1, 0, 2, links, tries[links], eps=EPS)
+    assert bad == 0
+    got = post.reshape(-1, 4)[links]
+    assert np.abs(got - want).max() < TOL
+    assert np.abs(np.linalg.norm(post.reshape(-1, 4), axis=1) - 1).max() < 1e-6
+    b.close()
+
+
+@pytest.mark.slow
+def test_plaquette_average_8x4_long_run():
+    """10^4 sweeps of 8^4 at beta = 2.3 on the GPU (FP64 plaquette sums) against
+    an independent, shorter oracle run: averages within 3 combined binned sigma."""
+    L = (8, 8, 8, 8)
+    beta = 2.3
+    b = mc.Batch([mc.su2(L, beta, seed=21)], series_capacity=10_000)
+    b.sweep(1000)
+    b.read_series()
+    b.sweep(10_000, 1)
+    P = b.read_series()["P"][0]
+    gm, ge = binned_mean_err(P, 20)
+    q = oracle.su2_init(L, 33, 0, True)
+    Po = []
+    for k in range(1300):
+        oracle.su2_sweep(q, L, beta, 33, 0, k)
+        if k >= 300:
+            Po.append(oracle.su2_plaquette(q, L)[0])
+    om, oe = binned_mean_err(Po, 10)
+    assert abs(gm - om) < 3 * np.hypot(ge, oe) + 1e-4, (gm, ge, om, oe)
+    print(f"<P> GPU {gm:.6f} +- {ge:.6f}  oracle {om:.6f} +- {oe:.6f}")

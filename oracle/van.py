@@ -1,0 +1,157 @@
+"""FP64 oracle of the learned global proposal (test infrastructure; see the
+package docstring for who may import it).
+
+The paper has no learned component; this follows the published method of
+variational autoregressive networks (D. Wu, L. Wang, P. Zhang, Phys. Rev. Lett.
+122 (2019) 080602) used as an independence proposal corrected by a
+Metropolis-Hastings step, so the stationary distribution stays the Boltzmann
+distribution of Eq. (1) whatever the network has learned.
+
+Network (raster order k = y L + x, zero padding -- an autoregressive mask is
+not compatible with periodic padding):
+  layer 1 : 5x5 convolution, 1 -> C channels, mask A (taps strictly before the
+            centre: dy < 0, or dy = 0 and dx < 0), bias, ReLU;
+  layers 2..D-1 : 5x5, C -> C, mask B (mask A plus the centre), bias, ReLU;
+  layer D : 5x5, C -> 1, mask B, bias -> logit f_k.
+p(s_k = +1 | s_<k) = sigmoid(f_k); log q(s) = sum_k log sigmoid(s_k f_k).
+Parameters are (W, b) per layer with W[c_out, c_in, 5, 5] (masked taps unused).
+Convolution is correlation: out[y, x] = sum_{dy,dx} W[., ., dy+2, dx+2] in[y+dy, x+dx].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+K = 5
+R = K // 2
+
+
+def taps(mask: str):
+    """(dy, dx) offsets of a mask, in raster order."""
+    out = []
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            if dy < 0 or (dy == 0 and (dx < 0 or (mask == "B" and dx == 0))):
+                out.append((dy, dx))
+    return out
+
+
+def shift(x: np.ndarray, dy: int, dx: int) -> np.ndarray:
+    """y[..., i, j] = x[..., i + dy, j + dx], zero outside the lattice."""
+    out = np.zeros_like(x)
+    H, W = x.shape[-2:]
+    ys, ye = max(0, -dy), min(H, H - dy)
+    xs, xe = max(0, -dx), min(W, W - dx)
+    out[..., ys:ye, xs:xe] = x[..., ys + dy:ye + dy, xs + dx:xe + dx]
+    return out
+
+
+def init_params(depth: int = 6, channels: int = 32, seed: int = 0, scale: float = 1.0):
+    rng = np.random.default_rng(seed)
+    params = []
+    for l in range(depth):
+        cin = 1 if l == 0 else channels
+        cout = 1 if l == depth - 1 else channels
+        ntap = len(taps("A" if l == 0 else "B"))
+        std = scale * np.sqrt(2.0 / (cin * ntap))
+        W = rng.normal(0.0, std, size=(cout, cin, K, K))
+        b = np.zeros(cout)
+        params.append((W, b))
+    return params
+
+
+def masked(params):
+    """Zero the taps outside each layer's mask."""
+    out = []
+    for l, (W, b) in enumerate(params):
+        m = np.zeros((K, K))
+        for dy, dx in taps("A" if l == 0 else "B"):
+            m[dy + R, dx + R] = 1.0
+        out.append((W * m, b))
+    return out
+
+
+def forward(params, s: np.ndarray):
+    """s: (B, L, L) of +-1.  Returns logits f (B, L, L) and the per-layer cache
+    [(input, pre-activation)] for the backward pass."""
+    x = s[:, None, :, :].astype(np.float64)
+    cache = []
+    D = len(params)
+    for l, (W, b) in enumerate(params):
+        mask = "A" if l == 0 else "B"
+        z = np.zeros((x.shape[0], W.shape[0]) + x.shape[2:])
+        for dy, dx in taps(mask):
+            xs = shift(x, dy, dx)  # (B, cin, L, L)
+            z += np.einsum("oi,bixy->boxy", W[:, :, dy + R, dx + R], xs)
+        z += b[None, :, None, None]
+        cache.append((x, z))
+        x = np.maximum(z, 0.0) if l < D - 1 else z
+    return x[:, 0], cache
+
+
+def log_sigmoid(t):
+    return -np.logaddexp(0.0, -t)
+
+
+def log_prob(params, s: np.ndarray) -> np.ndarray:
+    """log q(s) per configuration (FP64 accumulation)."""
+    f, _ = forward(params, s)
+    return log_sigmoid(s * f).reshape(len(s), -1).sum(axis=1)
+
+
+def log_prob_sym(params, s: np.ndarray) -> np.ndarray:
+    """log q_sym(s), q_sym(s) = (q(s) + q(-s)) / 2 (symmetry under the global
+    spin flip, Wu-Wang-Zhang)."""
+    return np.logaddexp(log_prob(params, s), log_prob(params, -s)) - np.log(2.0)
+
+
+def loss_and_grad(params, s: np.ndarray):
+    """Negative mean log-likelihood -mean_b log q(s_b) and its gradient."""
+    B = len(s)
+    f, cache = forward(params, s)
+    loss = -log_sigmoid(s * f).reshape(B, -1).sum(axis=1).mean()
+    # d loss / d f = -(1/B) s sigmoid(-s f)
+    g = -(s * (1.0 / (1.0 + np.exp(s * f)))) / B
+    grad_out = g[:, None, :, :]
+    grads = [None] * len(params)
+    D = len(params)
+    for l in range(D - 1, -1, -1):
+        W, b = params[l]
+        x, z = cache[l]
+        dz = grad_out if l == D - 1 else grad_out * (z > 0)
+        mask = "A" if l == 0 else "B"
+        dW = np.zeros_like(W)
+        dx_in = np.zeros_like(x)
+        for dy, dx in taps(mask):
+            xs = shift(x, dy, dx)
+            dW[:, :, dy + R, dx + R] = np.einsum("boxy,bixy->oi", dz, xs)
+            # x enters z at (y, x) via x[y+dy, x+dx]: scatter back with the opposite shift
+            dx_in += shift(np.einsum("oi,boxy->bixy", W[:, :, dy + R, dx + R], dz), -dy, -dx)
+        db = dz.sum(axis=(0, 2, 3))
+        grads[l] = (dW, db)
+        grad_out = dx_in
+    return float(loss), grads
+
+
+def sample(params, n: int, L: int, uniforms: np.ndarray) -> np.ndarray:
+    """Autoregressive sampling, one position at a time in raster order:
+    s_k = +1 iff u_k < sigmoid(f_k(s_<k)).  uniforms: (n, L*L) in (0, 1).
+    Slow (L^2 full forward passes): for small lattices only."""
+    s = np.zeros((n, L, L))
+    for k in range(L * L):
+        y, x = divmod(k, L)
+        f, _ = forward(params, s)
+        p = 1.0 / (1.0 + np.exp(-f[:, y, x]))
+        s[:, y, x] = np.where(uniforms[:, k] < p, 1.0, -1.0)
+    return s
+
+
+def ising_energy(s: np.ndarray) -> np.ndarray:
+    """H of Eq. (1) on the periodic torus, per configuration."""
+    return -(s * np.roll(s, -1, axis=-1)).sum(axis=(-2, -1)) - (s * np.roll(s, -1, axis=-2)).sum(axis=(-2, -1))
+
+
+def mh_accept_logratio(params, beta: float, s_cur: np.ndarray, s_prop: np.ndarray) -> np.ndarray:
+    """log of the Metropolis-Hastings ratio for an independence proposal from
+    q_sym: -beta (E' - E) + log q_sym(s) - log q_sym(s')."""
+    return (-beta * (ising_energy(s_prop) - ising_energy(s_cur)) + log_prob_sym(params, s_cur)
+            - log_prob_sym(params, s_prop))

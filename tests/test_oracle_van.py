@@ -1,0 +1,148 @@
+"""Pins of the learned-proposal oracle (oracle/van.py): exact normalisation of
+the autoregressive distribution, the autoregressive mask, the backward pass
+against finite differences, the sampler against q itself, and exactness of the
+Metropolis-Hastings correction against the Boltzmann distribution of Eq. (1)."""
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import exact, van
+
+
+def all_states(Lx, Ly):
+    idx = np.arange(1 << (Lx * Ly))
+    return (((idx[:, None] >> np.arange(Lx * Ly)) & 1) * 2 - 1).reshape(-1, Ly, Lx).astype(np.float64)
+
+
+def _merge_small(counts, expected, floor=5.0):
+    """Pool the cells with expected count < floor into one (if there are any)."""
+    big = expected >= floor
+    obs, e = counts[big].astype(np.float64), expected[big]
+    if (~big).any():
+        obs = np.append(obs, counts[~big].sum())
+        e = np.append(e, expected[~big].sum())
+    return obs, e
+
+
+def test_taps():
+    assert len(van.taps("A")) == 12 and len(van.taps("B")) == 13
+    assert (0, 0) not in van.taps("A") and (0, 0) in van.taps("B")
+    assert all(dy < 0 or (dy == 0 and dx <= 0) for dy, dx in van.taps("B"))
+
+
+def test_normalisation_by_enumeration():
+    """sum_s q(s) = 1 exactly over all 2^16 states of a 4x4 lattice (any weights)."""
+    p = van.masked(van.init_params(depth=4, channels=4, seed=3, scale=2.0))
+    for a in range(2):
+        p[1] = (p[1][0], p[1][1] + a)  # non-zero biases too
+    q = np.exp(van.log_prob(p, all_states(4, 4)))
+    assert abs(q.sum() - 1.0) < 1e-10
+
+
+def test_autoregressive_mask():
+    """f_k depends only on s_j for j < k in raster order."""
+    rng = np.random.default_rng(1)
+    p = van.masked(van.init_params(depth=6, channels=6, seed=1))
+    L = 6
+    s = np.where(rng.random((1, L, L)) < 0.5, 1.0, -1.0)
+    f0, _ = van.forward(p, s)
+    for j in [0, 7, 14, 20, 35]:
+        s2 = s.copy()
+        s2[0, j // L, j % L] *= -1
+        f1, _ = van.forward(p, s2)
+        d = np.abs(f1 - f0).reshape(-1)
+        assert np.all(d[: j + 1] == 0.0), j
+        if j < L * L - 1:
+            assert d[j + 1:].max() > 0.0
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    p = van.masked(van.init_params(depth=6, channels=5, seed=2))
+    p = [(W, b + 0.1 * rng.normal(size=b.shape)) for W, b in p]
+    s = np.where(rng.random((3, 6, 6)) < 0.5, 1.0, -1.0)
+    _, g = van.loss_and_grad(p, s)
+    h = 1e-6
+    for l in range(6):
+        W, b = p[l]
+        mask = "A" if l == 0 else "B"
+        for _ in range(3):
+            o = rng.integers(W.shape[0]); i = rng.integers(W.shape[1])
+            dy, dx = van.taps(mask)[rng.integers(len(van.taps(mask)))]
+            ix = (o, i, dy + 2, dx + 2)
+            pp = [(w.copy(), bb.copy()) for w, bb in p]; pp[l][0][ix] += h
+            pm = [(w.copy(), bb.copy()) for w, bb in p]; pm[l][0][ix] -= h
+            fd = (van.loss_and_grad(pp, s)[0] - van.loss_and_grad(pm, s)[0]) / (2 * h)
+            assert abs(g[l][0][ix] - fd) <= 1e-6 * max(1.0, abs(fd)), (l, ix, g[l][0][ix], fd)
+        o = rng.integers(b.shape[0])
+        pp = [(w.copy(), bb.copy()) for w, bb in p]; pp[l][1][o] += h
+        pm = [(w.copy(), bb.copy()) for w, bb in p]; pm[l][1][o] -= h
+        fd = (van.loss_and_grad(pp, s)[0] - van.loss_and_grad(pm, s)[0]) / (2 * h)
+        assert abs(g[l][1][o] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_sampler_follows_q():
+    """Chi-square of 20000 autoregressive samples on a 3x3 lattice against q."""
+    p = van.masked(van.init_params(depth=4, channels=4, seed=5, scale=1.5))
+    n = 20000
+    u = np.random.default_rng(6).random((n, 9))
+    s = van.sample(p, n, 3, u)
+    states = all_states(3, 3)
+    q = np.exp(van.log_prob(p, states))
+    code = ((s.reshape(n, -1) > 0).astype(np.int64) << np.arange(9)).sum(axis=1)
+    counts = np.bincount(code, minlength=512)
+    obs, e = _merge_small(counts, q * n)
+    chi2 = ((obs - e) ** 2 / e).sum()
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-4
+
+
+def _mh_chain_histogram(correct: bool, n_chains=6000, steps=30, beta=0.4):
+    """Independence-sampler chains on a 4x2 torus using only MH proposals from a
+    deliberately poor (random) network, started in the exact Boltzmann
+    distribution: an exact MH step keeps them there (stationarity), a wrong
+    ratio drifts away."""
+    Lx, Ly = 4, 2
+    p = van.masked(van.init_params(depth=3, channels=4, seed=9, scale=2.0))
+    rng = np.random.default_rng(10)
+    en = exact.ising_enumerate(Lx, Ly, beta)
+    code = rng.choice(len(en["p"]), size=n_chains, p=en["p"])
+    s = (((code[:, None] >> np.arange(Lx * Ly)) & 1) * 2 - 1).reshape(-1, Ly, Lx).astype(np.float64)
+    for _ in range(steps):
+        # proposals from q_sym: sample from q, then flip globally with probability 1/2
+        prop = _sample_rect(p, n_chains, Lx, Ly, rng)
+        flip = rng.random(n_chains) < 0.5
+        prop[flip] *= -1
+        if correct:
+            lr = (-beta * (van.ising_energy(prop) - van.ising_energy(s)) + van.log_prob_sym(p, s)
+                  - van.log_prob_sym(p, prop))
+        else:  # planted mistake: the proposal density left out of the ratio
+            lr = -beta * (van.ising_energy(prop) - van.ising_energy(s))
+        acc = np.log(rng.random(n_chains)) < lr
+        s[acc] = prop[acc]
+    return s
+
+
+def _sample_rect(p, n, Lx, Ly, rng):
+    s = np.zeros((n, Ly, Lx))
+    for k in range(Lx * Ly):
+        y, x = divmod(k, Lx)
+        f, _ = van.forward(p, s)
+        pr = 1.0 / (1.0 + np.exp(-f[:, y, x]))
+        s[:, y, x] = np.where(rng.random(n) < pr, 1.0, -1.0)
+    return s
+
+
+@pytest.mark.parametrize("correct", [True, False])
+def test_mh_correction_is_exact(correct):
+    beta = 0.4
+    s = _mh_chain_histogram(correct, beta=beta)
+    en = exact.ising_enumerate(4, 2, beta)
+    code = ((s.reshape(len(s), -1) > 0).astype(np.int64) << np.arange(8)).sum(axis=1)
+    counts = np.bincount(code, minlength=256)
+    obs, ex = _merge_small(counts, en["p"] * len(s))
+    chi2 = ((obs - ex) ** 2 / ex).sum()
+    pval = stats.chi2.sf(chi2, len(obs) - 1)
+    if correct:
+        assert pval > 1e-4, pval
+    else:
+        assert pval < 1e-6, pval  # the test has the power to see a wrong ratio

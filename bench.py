@@ -311,7 +311,7 @@ def run_su2(mc, torch, rank, K, world):
     batch.close()
     updates = len(chains) * 4 * SU2_L ** 4 * K * world
     phase_ms = kernel_ms / max(launches, 1)
-    per_launch_updates = len(chains) * SU2_L ** 4 / 2
+    per_launch_updates = len(chains) * 4 * SU2_L ** 4 * K / max(launches, 1)
     hbm = 6777.3e9
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] * 1e9

@@ -63,11 +63,11 @@ __device__ __forceinline__ void block_sum2(uint32_t &a, uint32_t &b)
 // ------------------------------------------------------------------ int8 layout
 // Update the (up to four) sites of colour C that share Philox block g.
 template <int C, bool MEASURE>
-__device__ __forceinline__ void int8_group(int8_t *s, const IsingChain &ch, uint32_t g, uint32_t sweep,
-                                           uint32_t &anti, uint32_t &up)
+__device__ __forceinline__ void int8_group(int8_t *s, const IsingChain &ch, const PhiloxSchedule &ks, uint32_t g,
+                                           uint32_t sweep, uint32_t &anti, uint32_t &up)
 {
     const uint32_t Lx = ch.Lx, Ly = ch.Ly, half = Lx >> 1, nc = (Lx * Ly) >> 1;
-    const uint4 r4 = philox4x32_10(make_uint4(g, sweep, kTagIsingMetro | (uint32_t)C, ch.chain_id), ch.key);
+    const uint4 r4 = philox4x32_10(make_uint4(g, sweep, kTagIsingMetro | (uint32_t)C, ch.chain_id), ks);
     const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -94,33 +94,70 @@ __device__ __forceinline__ void int8_group(int8_t *s, const IsingChain &ch, uint
 }
 
 // ------------------------------------------------------------------ MSC layout
-// New value of one colour-C word given its four neighbour words.
+// New value of one colour-C word given its four neighbour words.  Every 4-site
+// Philox block is drawn (a per-block skip branch costs more than it saves);
+// each site compares its word with the threshold of its own dE.
 template <int C>
 __device__ __forceinline__ uint32_t msc_word(uint32_t s, uint32_t nu, uint32_t nd, uint32_t ns, uint32_t side,
-                                             uint32_t blk0, uint32_t sweep, const IsingChain &ch)
+                                             uint32_t blk0, uint32_t sweep, const IsingChain &ch,
+                                             const PhiloxSchedule &ks)
 {
     const uint32_t a1 = s ^ nu, a2 = s ^ nd, a3 = s ^ ns, a4 = s ^ side; // 1 = anti-aligned
     const uint32_t s12 = a1 ^ a2, c12 = a1 & a2, s34 = a3 ^ a4, c34 = a3 & a4;
     const uint32_t ge2 = c12 | c34 | (s12 & s34); // >= 2 anti-aligned: dE <= 0, always flip
     const uint32_t eq0 = ~(a1 | a2 | a3 | a4);    // dE = 8
     const uint32_t eq1 = ~(ge2 | eq0);            // dE = 4
-    const uint32_t need = eq0 | eq1;
     uint32_t acc = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        if ((need >> (4 * k)) & 0xFu) {
-            const uint4 r = philox4x32_10(make_uint4(blk0 + k, sweep, kTagIsingMetro | (uint32_t)C, ch.chain_id),
-                                          ch.key);
-            const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+        const uint4 r = philox4x32_10(make_uint4(blk0 + k, sweep, kTagIsingMetro | (uint32_t)C, ch.chain_id), ks);
+        const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int b = 4 * k + q;
-                const uint32_t T = ((eq1 >> b) & 1u) ? ch.T2 : ch.T4;
-                acc |= (uint32_t)(rr[q] < T) << b;
-            }
+        for (int q = 0; q < 4; ++q) {
+            const int b = 4 * k + q;
+            const uint32_t T = ((eq1 >> b) & 1u) ? ch.T2 : ch.T4;
+            if (rr[q] < T)
+                acc |= 1u << b;
         }
     }
-    return s ^ (ge2 | (acc & need));
+    return s ^ (ge2 | (acc & ~ge2));
+}
+
+// Update words (2 yy, w) and (2 yy + 1, w) of plane C.  The two rows share the
+// other plane's rows 2 yy and 2 yy + 1 as neighbours, so six loads serve both
+// words.  Row y holds sites x = 2 j + ((y + C) & 1): offset C on the even row,
+// 1 - C on the odd one, which decides the side (j - 1 or j + 1) neighbour.
+template <int C, bool MEASURE>
+__device__ __forceinline__ void msc_row_pair(uint32_t *pc, const uint32_t *po, uint32_t yy, uint32_t w,
+                                             const IsingChain &ch, const PhiloxSchedule &ks, uint32_t sweep,
+                                             uint32_t &anti, uint32_t &up)
+{
+    const uint32_t W = ch.W, Ly = ch.Ly, y0 = 2 * yy, y1 = y0 + 1;
+    const uint32_t om = po[dec_wrap(y0, Ly) * W + w];
+    const uint32_t o0 = po[y0 * W + w];
+    const uint32_t o1 = po[y1 * W + w];
+    const uint32_t op = po[inc_wrap(y1, Ly) * W + w];
+    uint32_t side0, side1;
+    if (C == 0) {
+        side0 = (o0 << 1) | (po[y0 * W + dec_wrap(w, W)] >> 31);
+        side1 = (o1 >> 1) | (po[y1 * W + inc_wrap(w, W)] << 31);
+    } else {
+        side0 = (o0 >> 1) | (po[y0 * W + inc_wrap(w, W)] << 31);
+        side1 = (o1 << 1) | (po[y1 * W + dec_wrap(w, W)] >> 31);
+    }
+    const uint32_t s0 = pc[y0 * W + w], s1 = pc[y1 * W + w];
+    const uint32_t bpr = ch.Lx >> 3; // Philox blocks per row of one colour
+    const uint32_t n0 = msc_word<C>(s0, om, o1, o0, side0, y0 * bpr + 8 * w, sweep, ch, ks);
+    const uint32_t n1 = msc_word<C>(s1, o0, op, o1, side1, y1 * bpr + 8 * w, sweep, ch, ks);
+    if (n0 != s0)
+        pc[y0 * W + w] = n0;
+    if (n1 != s1)
+        pc[y1 * W + w] = n1;
+    if (MEASURE) {
+        anti += __popc(n0 ^ om) + __popc(n0 ^ o1) + __popc(n0 ^ o0) + __popc(n0 ^ side0) + __popc(n1 ^ o0) +
+                __popc(n1 ^ op) + __popc(n1 ^ o1) + __popc(n1 ^ side1);
+        up += __popc(n0) + __popc(o0) + __popc(n1) + __popc(o1);
+    }
 }
 
 // Gather the neighbours of word (y, w) of plane C from the other plane `po`.
@@ -155,28 +192,24 @@ __global__ void __launch_bounds__(1024) k_half_sweep(SweepArgs a)
         int8_t *s = reinterpret_cast<int8_t *>(a.lattice + ch.spin_off);
         const uint32_t groups = (((ch.Lx * ch.Ly) >> 1) + 3) >> 2;
         if (t < groups) {
+            const PhiloxSchedule ks = philox_schedule(ch.key);
             if (measure)
-                int8_group<C, true>(s, ch, t, sweep, anti, up);
+                int8_group<C, true>(s, ch, ks, t, sweep, anti, up);
             else
-                int8_group<C, false>(s, ch, t, sweep, anti, up);
+                int8_group<C, false>(s, ch, ks, t, sweep, anti, up);
         }
     } else {
-        const uint32_t W = ch.W, Ly = ch.Ly, nw = W * Ly;
+        const uint32_t W = ch.W, nw = W * ch.Ly;
         uint32_t *base = reinterpret_cast<uint32_t *>(a.lattice + ch.spin_off);
         uint32_t *pc = base + (size_t)C * nw;
         const uint32_t *po = base + (size_t)(1 - C) * nw;
-        if (t < nw) {
-            const uint32_t y = t / W, w = t - y * W;
-            uint32_t nu, nd, ns, side;
-            msc_neighbours<C>(po, y, w, W, Ly, nu, nd, ns, side);
-            const uint32_t s = pc[t];
-            const uint32_t sn = msc_word<C>(s, nu, nd, ns, side, y * (ch.Lx >> 3) + 8 * w, sweep, ch);
-            if (sn != s)
-                pc[t] = sn;
-            if (measure) {
-                anti = __popc(sn ^ nu) + __popc(sn ^ nd) + __popc(sn ^ ns) + __popc(sn ^ side);
-                up = __popc(sn) + __popc(ns);
-            }
+        if (t < W * (ch.Ly >> 1)) { // one thread per row pair and word column
+            const PhiloxSchedule ks = philox_schedule(ch.key);
+            const uint32_t yy = t / W, w = t - yy * W;
+            if (measure)
+                msc_row_pair<C, true>(pc, po, yy, w, ch, ks, sweep, anti, up);
+            else
+                msc_row_pair<C, false>(pc, po, yy, w, ch, ks, sweep, anti, up);
         }
     }
     if (!a.measure)
@@ -212,6 +245,7 @@ __global__ void __launch_bounds__(1024) k_resident(SweepArgs a, uint32_t n_sweep
     for (uint32_t u = threadIdx.x; u < bytes / 4; u += blockDim.x)
         sl[u] = gl[u];
     __syncthreads();
+    const PhiloxSchedule ks = philox_schedule(ch.key);
     const unsigned long long base = a.state->sweep_base;
     for (uint32_t t = 0; t < n_sweeps; ++t) {
         const uint32_t sweep = (uint32_t)(base + t);
@@ -221,36 +255,32 @@ __global__ void __launch_bounds__(1024) k_resident(SweepArgs a, uint32_t n_sweep
             int8_t *s = reinterpret_cast<int8_t *>(smem);
             const uint32_t groups = (((ch.Lx * ch.Ly) >> 1) + 3) >> 2;
             for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-                int8_group<0, false>(s, ch, g, sweep, anti, up);
+                int8_group<0, false>(s, ch, ks, g, sweep, anti, up);
             __syncthreads();
             if (measure) {
                 for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-                    int8_group<1, true>(s, ch, g, sweep, anti, up);
+                    int8_group<1, true>(s, ch, ks, g, sweep, anti, up);
             } else {
                 for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-                    int8_group<1, false>(s, ch, g, sweep, anti, up);
+                    int8_group<1, false>(s, ch, ks, g, sweep, anti, up);
             }
         } else {
-            const uint32_t W = ch.W, Ly = ch.Ly, nw = W * Ly;
+            const uint32_t W = ch.W, nw = W * ch.Ly, pairs = W * (ch.Ly >> 1);
             uint32_t *p0 = sl, *p1 = sl + nw;
-            for (uint32_t u = threadIdx.x; u < nw; u += blockDim.x) {
-                const uint32_t y = u / W, w = u - y * W;
-                uint32_t nu, nd, ns, side;
-                msc_neighbours<0>(p1, y, w, W, Ly, nu, nd, ns, side);
-                const uint32_t s = p0[u];
-                p0[u] = msc_word<0>(s, nu, nd, ns, side, y * (ch.Lx >> 3) + 8 * w, sweep, ch);
+            for (uint32_t u = threadIdx.x; u < pairs; u += blockDim.x) {
+                const uint32_t yy = u / W, w = u - yy * W;
+                msc_row_pair<0, false>(p0, p1, yy, w, ch, ks, sweep, anti, up);
             }
             __syncthreads();
-            for (uint32_t u = threadIdx.x; u < nw; u += blockDim.x) {
-                const uint32_t y = u / W, w = u - y * W;
-                uint32_t nu, nd, ns, side;
-                msc_neighbours<1>(p0, y, w, W, Ly, nu, nd, ns, side);
-                const uint32_t s = p1[u];
-                const uint32_t sn = msc_word<1>(s, nu, nd, ns, side, y * (ch.Lx >> 3) + 8 * w, sweep, ch);
-                p1[u] = sn;
-                if (measure) {
-                    anti += __popc(sn ^ nu) + __popc(sn ^ nd) + __popc(sn ^ ns) + __popc(sn ^ side);
-                    up += __popc(sn) + __popc(ns);
+            if (measure) {
+                for (uint32_t u = threadIdx.x; u < pairs; u += blockDim.x) {
+                    const uint32_t yy = u / W, w = u - yy * W;
+                    msc_row_pair<1, true>(p1, p0, yy, w, ch, ks, sweep, anti, up);
+                }
+            } else {
+                for (uint32_t u = threadIdx.x; u < pairs; u += blockDim.x) {
+                    const uint32_t yy = u / W, w = u - yy * W;
+                    msc_row_pair<1, false>(p1, p0, yy, w, ch, ks, sweep, anti, up);
                 }
             }
         }
@@ -452,12 +482,12 @@ size_t ising_config_bytes(const IsingChain &ch, int fmt)
     return 0;
 }
 
-// Work units per chain for a grid-mode launch: Philox groups (int8) or words (MSC).
+// Work units per chain for a grid-mode launch: Philox groups (int8) or row pairs (MSC).
 static uint32_t grid_units(const mc_ctx *c, const IsingChain &ch)
 {
     if (c->layout == MC_LAYOUT_INT8)
         return (((ch.Lx * ch.Ly) >> 1) + 3) >> 2;
-    return ch.Ly * ch.W;
+    return (ch.Ly >> 1) * ch.W; // row pairs x words
 }
 
 void ising_plan_grid(mc_ctx *c)

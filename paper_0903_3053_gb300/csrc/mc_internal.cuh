@@ -7,6 +7,7 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/mc.h"
@@ -97,6 +98,7 @@ struct SweepArgs {
     int measure;                 // 1: this sweep is measured
     uint32_t rec_k;              // index of this record within the running call
     uint8_t *tries;              // SU(2) try record base, or nullptr
+    uint32_t block_base;         // first block of this launch in the block table
 };
 
 }  // namespace mc
@@ -133,6 +135,7 @@ struct mc_ctx {
     std::vector<mc::Su2Chain> su2;
     std::vector<mc_chain_desc> desc;
     std::vector<uint32_t> block_start, meas_start;
+    std::vector<std::pair<int, int>> groups; // SU(2) launch groups of chains [first, last)
     uint32_t grid_blocks = 0, meas_blocks = 0;
     // run bookkeeping
     long long sweeps_done = 0;
@@ -164,7 +167,6 @@ cudaError_t su2_measure_launch(mc_ctx *c, int chain, DevRecord *out);
 cudaError_t su2_config_io(mc_ctx *c, int chain, void *dev_buf, bool to_lattice);
 size_t su2_config_bytes(const Su2Chain &ch);
 void su2_plan_grid(mc_ctx *c);
-cudaError_t su2_tries_to_canonical(mc_ctx *c, int chain, uint8_t *dev_dst);
 
 cudaError_t advance_state_launch(mc_ctx *c, long long n, long long recs);
 

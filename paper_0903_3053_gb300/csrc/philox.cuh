@@ -41,6 +41,36 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, PhiloxKey key)
     return x;
 }
 
+// The ten round keys of one 64-bit key.  A thread that draws many blocks under
+// the same key computes them once: the Weyl increments then cost nothing per
+// block, and each round is two 32x32->64 multiplies and two three-input xors.
+struct PhiloxSchedule {
+    uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ PhiloxSchedule philox_schedule(PhiloxKey key)
+{
+    PhiloxSchedule s;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        s.k0[r] = key.k0 + (uint32_t)r * 0x9E3779B9u;
+        s.k1[r] = key.k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    return s;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, const PhiloxSchedule &ks)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * x.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * x.z;
+        x = make_uint4((uint32_t)(p1 >> 32) ^ x.y ^ ks.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ x.w ^ ks.k1[r],
+                       (uint32_t)p0);
+    }
+    return x;
+}
+
 // 32-bit random word -> float in (0, 1] with 24-bit resolution.  Exact in FP32:
 // ((r >> 8) + 1) <= 2^24 is representable and the scale is a power of two.
 __device__ __forceinline__ float uniform_open0(uint32_t r)

@@ -80,35 +80,65 @@ __device__ __forceinline__ float4 load_link(const float4 *__restrict__ U, uint32
     return __ldg(&U[(size_t)(par * 4 + dir) * nh + e]);
 }
 
+// Canonical index strides: direction mu moves the canonical index by st[mu].
+struct Strides {
+    uint32_t st[4];
+};
+
+__device__ __forceinline__ Strides strides_of(const Su2Chain &ch)
+{
+    Strides g;
+    g.st[1] = 1u;
+    g.st[2] = (uint32_t)ch.L[1];
+    g.st[3] = (uint32_t)(ch.L[1] * ch.L[2]);
+    g.st[0] = (uint32_t)(ch.L[1] * ch.L[2] * ch.L[3]);
+    return g;
+}
+
+// Canonical index of x + e_D / x - e_D, given x's coordinate along D.
+template <int D>
+__device__ __forceinline__ uint32_t fwd(const Su2Chain &ch, const Strides &g, int xd, uint32_t s)
+{
+    return xd + 1 == ch.L[D] ? s - (uint32_t)(ch.L[D] - 1) * g.st[D] : s + g.st[D];
+}
+template <int D>
+__device__ __forceinline__ uint32_t bwd(const Su2Chain &ch, const Strides &g, int xd, uint32_t s)
+{
+    return xd == 0 ? s + (uint32_t)(ch.L[D] - 1) * g.st[D] : s - g.st[D];
+}
+
+// The two staples of Eq. (6) in the (MU, NU) plane:
+//   U_nu(x) U_mu(x+nu) U_nu(x+mu)^+  +  U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu).
+// x + nu, x + mu and x - nu have parity 1 - P; x - nu + mu has parity P.
 template <int MU, int NU, int P>
-__device__ __forceinline__ float4 staple_pair(const float4 *__restrict__ U, const Su2Chain &ch, const Site &x,
-                                              uint32_t e)
+__device__ __forceinline__ float4 staple_pair(const float4 *__restrict__ U, const Su2Chain &ch, const Strides &g,
+                                              const Site &x, uint32_t s, uint32_t spm, uint32_t e)
 {
     constexpr int Q = 1 - P;
     const uint32_t nh = ch.nh;
-    const Site xpn = step<NU>(ch, x, +1);
-    const Site xpm = step<MU>(ch, x, +1);
-    const Site xmn = step<NU>(ch, x, -1);
-    const Site xmnpm = step<MU>(ch, xmn, +1);
+    const uint32_t spn = fwd<NU>(ch, g, x.x[NU], s);
+    const uint32_t smn = bwd<NU>(ch, g, x.x[NU], s);
+    const uint32_t smnpm = fwd<MU>(ch, g, x.x[MU], smn); // x - nu has the same MU coordinate as x
     const float4 a = load_link(U, nh, P, NU, e);
-    const float4 b = load_link(U, nh, Q, MU, canonical(ch, xpn) >> 1);
-    const float4 c = load_link(U, nh, Q, NU, canonical(ch, xpm) >> 1);
-    const uint32_t emn = canonical(ch, xmn) >> 1;
-    const float4 d = load_link(U, nh, Q, NU, emn);
-    const float4 f = load_link(U, nh, Q, MU, emn);
-    const float4 g = load_link(U, nh, P, NU, canonical(ch, xmnpm) >> 1);
-    // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+  +  U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu)
-    return qadd(qmul(qmul(a, b), qdag(c)), qmul(qmul(qdag(d), f), g));
+    const float4 b = load_link(U, nh, Q, MU, spn >> 1);
+    const float4 c = load_link(U, nh, Q, NU, spm >> 1);
+    const float4 d = load_link(U, nh, Q, NU, smn >> 1);
+    const float4 f = load_link(U, nh, Q, MU, smn >> 1);
+    const float4 h = load_link(U, nh, P, NU, smnpm >> 1);
+    return qadd(qmul(qmul(a, b), qdag(c)), qmul(qmul(qdag(d), f), h));
 }
 
 template <int MU, int P>
-__device__ __forceinline__ float4 staple(const float4 *__restrict__ U, const Su2Chain &ch, const Site &x, uint32_t e)
+__device__ __forceinline__ float4 staple(const float4 *__restrict__ U, const Su2Chain &ch, const Site &x, uint32_t s,
+                                         uint32_t e)
 {
+    const Strides g = strides_of(ch);
+    const uint32_t spm = fwd<MU>(ch, g, x.x[MU], s);
     float4 W = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (MU != 0) W = qadd(W, staple_pair<MU, 0, P>(U, ch, x, e));
-    if (MU != 1) W = qadd(W, staple_pair<MU, 1, P>(U, ch, x, e));
-    if (MU != 2) W = qadd(W, staple_pair<MU, 2, P>(U, ch, x, e));
-    if (MU != 3) W = qadd(W, staple_pair<MU, 3, P>(U, ch, x, e));
+    if (MU != 0) W = qadd(W, staple_pair<MU, 0, P>(U, ch, g, x, s, spm, e));
+    if (MU != 1) W = qadd(W, staple_pair<MU, 1, P>(U, ch, g, x, s, spm, e));
+    if (MU != 2) W = qadd(W, staple_pair<MU, 2, P>(U, ch, g, x, s, spm, e));
+    if (MU != 3) W = qadd(W, staple_pair<MU, 3, P>(U, ch, g, x, s, spm, e));
     return W;
 }
 
@@ -118,13 +148,12 @@ constexpr uint8_t kFailed = 255;
 
 // Heat-bath draw of a0 ~ sqrt(1-a0^2) exp(alpha a0); returns the try taken.
 __device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, uint32_t sel, const Su2Chain &ch,
-                                       float &a0)
+                                       const PhiloxSchedule &ks, float &a0)
 {
     if (alpha > 0.f) {
         const float inv2a = 0.5f / alpha;
         for (int t = 0; t < kKpTries; ++t) {
-            const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id),
-                                          ch.key);
+            const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ks);
             const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
             const float u3 = uniform_open0(r.z), u4 = uniform_open0(r.w);
             const float cs = cospif(2.0f * u2);
@@ -137,7 +166,7 @@ __device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, 
     }
     const float cexp = alpha > 0.f ? -expm1f(-2.0f * alpha) : 0.f; // 1 - e^{-2 alpha}
     for (int t = kKpTries; t < kKpTries + kCreutzTries; ++t) {
-        const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ch.key);
+        const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ks);
         const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
         const float c = alpha > 0.f ? 1.0f + log1pf(-(1.0f - u1) * cexp) / alpha : 2.0f * u1 - 1.0f;
         if (u2 * u2 <= 1.0f - c * c) {
@@ -151,15 +180,17 @@ __device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, 
 template <int P, int MU>
 __global__ void __launch_bounds__(256) k_phase(SweepArgs a)
 {
-    const int k = find_chain(a.block_start, a.n_chains, blockIdx.x);
+    const uint32_t b = blockIdx.x + a.block_base;
+    const int k = find_chain(a.block_start, a.n_chains, b);
     const Su2Chain ch = static_cast<const Su2Chain *>(a.chains)[k];
-    const uint32_t e = (blockIdx.x - a.block_start[k]) * blockDim.x + threadIdx.x;
+    const uint32_t e = (b - a.block_start[k]) * blockDim.x + threadIdx.x;
     if (e >= ch.nh)
         return;
     float4 *U = reinterpret_cast<float4 *>(a.lattice + ch.link_off);
     const uint32_t sweep = (uint32_t)(a.state->sweep_base + a.k);
     const Site x = site_from_parity_index(ch, P, e);
-    const float4 W = staple<MU, P>(U, ch, x, e);
+    const uint32_t s = canonical(ch, x);
+    const float4 W = staple<MU, P>(U, ch, x, s, e);
     const float k2 = qdot(W, W);
     const float kn = sqrtf(k2);
     float4 V = make_float4(1.f, 0.f, 0.f, 0.f);
@@ -169,14 +200,15 @@ __global__ void __launch_bounds__(256) k_phase(SweepArgs a)
     }
     const uint32_t sel = ((uint32_t)P << 12) | ((uint32_t)MU << 8);
     float a0 = 0.f;
-    const int t = draw_a0(ch.beta * kn, e, sweep, sel, ch, a0);
+    const PhiloxSchedule ks = philox_schedule(ch.key);
+    const int t = draw_a0(ch.beta * kn, e, sweep, sel, ch, ks, a0);
     if (a.tries)
-        a.tries[ch.tries_off + (size_t)canonical(ch, x) * 4 + MU] = (uint8_t)t;
+        a.tries[ch.tries_off + (size_t)s * 4 + MU] = (uint8_t)t;
     if (t == kFailed) {
         atomicAdd(&a.state->hb_failures, 1ull);
         return;
     }
-    const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ch.key);
+    const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ks);
     const float ct = 2.0f * uniform_open0(r.x) - 1.0f;
     float sphi, cphi;
     sincospif(2.0f * uniform_open0(r.y), &sphi, &cphi);
@@ -202,12 +234,13 @@ __device__ __forceinline__ double warp_sum(double v)
 // separately (the two FP64 values per measuring thread of Sec. 2.4).  Products
 // in FP32, sums in FP64.  One thread per site; partial[2 b], partial[2 b + 1].
 __global__ void __launch_bounds__(256) k_plaquette(const Su2Chain *chains, const uint32_t *meas_start, int n_chains,
-                                                   const char *lattice, double *partial)
+                                                   const char *lattice, double *partial, uint32_t block_base)
 {
     __shared__ double ss[8], st[8];
-    const int k = find_chain(meas_start, n_chains, blockIdx.x);
+    const uint32_t blk = blockIdx.x + block_base;
+    const int k = find_chain(meas_start, n_chains, blk);
     const Su2Chain ch = chains[k];
-    const uint32_t s = (blockIdx.x - meas_start[k]) * blockDim.x + threadIdx.x;
+    const uint32_t s = (blk - meas_start[k]) * blockDim.x + threadIdx.x;
     const uint32_t n = 2 * ch.nh;
     double ps = 0.0, pt = 0.0;
     if (s < n) {
@@ -270,8 +303,8 @@ __global__ void __launch_bounds__(256) k_plaquette(const Su2Chain *chains, const
             a += ss[i];
             b += st[i];
         }
-        partial[2 * blockIdx.x] = a;
-        partial[2 * blockIdx.x + 1] = b;
+        partial[2 * blk] = a;
+        partial[2 * blk + 1] = b;
     }
 }
 
@@ -381,15 +414,15 @@ __global__ void k_su2_io(Su2Chain ch, float4 *U, float4 *canon, int to_lattice)
 inline unsigned blocks_for(size_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 template <int P>
-void launch_phase(mc_ctx *c, const SweepArgs &a, int mu)
+void launch_phase(mc_ctx *c, const SweepArgs &a, int mu, unsigned nblocks)
 {
     if (prof_begin(c) != cudaSuccess)
         return;
     switch (mu) {
-    case 0: k_phase<P, 0><<<c->grid_blocks, c->threads, 0, c->ls>>>(a); break;
-    case 1: k_phase<P, 1><<<c->grid_blocks, c->threads, 0, c->ls>>>(a); break;
-    case 2: k_phase<P, 2><<<c->grid_blocks, c->threads, 0, c->ls>>>(a); break;
-    default: k_phase<P, 3><<<c->grid_blocks, c->threads, 0, c->ls>>>(a); break;
+    case 0: k_phase<P, 0><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 1: k_phase<P, 1><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 2: k_phase<P, 2><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    default: k_phase<P, 3><<<nblocks, c->threads, 0, c->ls>>>(a); break;
     }
     prof_end(c);
 }
@@ -399,6 +432,11 @@ void launch_phase(mc_ctx *c, const SweepArgs &a, int mu)
 // =========================================================================== host
 size_t su2_config_bytes(const Su2Chain &ch) { return (size_t)2 * ch.nh * 4 * sizeof(float4); }
 
+// Block tables.  All chains of the batch form one launch group: sweeping
+// L2-sized groups of chains one after another (to keep each group's links
+// L2-resident across its eight phases) was measured slower on 4 x 32^4 -- the
+// phase kernel is issue-bound, and four one-chain launches per phase add tail
+// waves -- so the group list holds a single entry.
 void su2_plan_grid(mc_ctx *c)
 {
     c->block_start.assign(c->n_chains + 1, 0);
@@ -414,6 +452,7 @@ void su2_plan_grid(mc_ctx *c)
     c->meas_start[c->n_chains] = macc;
     c->grid_blocks = acc;
     c->meas_blocks = macc;
+    c->groups.assign(1, std::make_pair(0, c->n_chains));
 }
 
 cudaError_t su2_init_launch(mc_ctx *c, const mc_chain_desc *desc)
@@ -426,15 +465,19 @@ cudaError_t su2_init_launch(mc_ctx *c, const mc_chain_desc *desc)
     return cudaGetLastError();
 }
 
-static cudaError_t plaquette_launch(mc_ctx *c, uint32_t ksweep, uint32_t rec_k, int only, DevRecord *out)
+// Per-block plaquette partial sums for chains [k0, k1).
+static void plaquette_partials(mc_ctx *c, int k0, int k1)
 {
-    k_plaquette<<<c->meas_blocks, 256, 0, c->ls>>>(static_cast<const Su2Chain *>(c->d_chains), c->d_meas_start,
-                                                       c->n_chains, c->d_lattice, c->d_partials);
+    const uint32_t b0 = c->meas_start[k0], b1 = c->meas_start[k1];
+    k_plaquette<<<b1 - b0, 256, 0, c->ls>>>(static_cast<const Su2Chain *>(c->d_chains), c->d_meas_start, c->n_chains,
+                                            c->d_lattice, c->d_partials, b0);
+}
+
+static void plaquette_final(mc_ctx *c, uint32_t ksweep, uint32_t rec_k, int only, DevRecord *out)
+{
     const unsigned nb = only >= 0 ? 1u : (unsigned)c->n_chains;
     k_plaquette_final<<<nb, 256, 0, c->ls>>>(static_cast<const Su2Chain *>(c->d_chains), c->d_meas_start,
-                                                 c->d_partials, c->d_series, c->cap, c->d_state, ksweep, rec_k, only,
-                                                 out);
-    return cudaGetLastError();
+                                             c->d_partials, c->d_series, c->cap, c->d_state, ksweep, rec_k, only, out);
 }
 
 cudaError_t su2_sweep_enqueue(mc_ctx *c, long long n, int every)
@@ -450,22 +493,28 @@ cudaError_t su2_sweep_enqueue(mc_ctx *c, long long n, int every)
     a.tries = c->record_tries ? c->d_tries : nullptr;
     for (long long t = 0; t < n; ++t) {
         a.k = (uint32_t)t;
-        for (int mu = 0; mu < 4; ++mu)
-            launch_phase<1>(c, a, mu); // odd sites first (Sec. 2.4)
-        for (int mu = 0; mu < 4; ++mu)
-            launch_phase<0>(c, a, mu);
-        if (every > 0 && ((t + 1) % every) == 0) {
-            cudaError_t e = plaquette_launch(c, (uint32_t)t, (uint32_t)((t + 1) / every - 1), -1, nullptr);
-            if (e != cudaSuccess)
-                return e;
+        const bool measure = every > 0 && ((t + 1) % every) == 0;
+        for (const auto &g : c->groups) {
+            a.block_base = c->block_start[g.first];
+            const unsigned nb = c->block_start[g.second] - c->block_start[g.first];
+            for (int mu = 0; mu < 4; ++mu)
+                launch_phase<1>(c, a, mu, nb); // odd sites first (Sec. 2.4)
+            for (int mu = 0; mu < 4; ++mu)
+                launch_phase<0>(c, a, mu, nb);
+            if (measure)
+                plaquette_partials(c, g.first, g.second);
         }
+        if (measure)
+            plaquette_final(c, (uint32_t)t, (uint32_t)((t + 1) / every - 1), -1, nullptr);
     }
     return cudaGetLastError();
 }
 
 cudaError_t su2_measure_launch(mc_ctx *c, int chain, DevRecord *out)
 {
-    return plaquette_launch(c, 0, 0, chain, out);
+    plaquette_partials(c, chain, chain + 1);
+    plaquette_final(c, 0, 0, chain, out);
+    return cudaGetLastError();
 }
 
 cudaError_t su2_config_io(mc_ctx *c, int chain, void *dev_buf, bool to_lattice)

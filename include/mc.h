@@ -176,6 +176,23 @@ MC_API mc_status mc_profile_enable(mc_ctx *ctx, int32_t enable);
  * the previous read (synchronous; resets the counters). */
 MC_API mc_status mc_profile_read(mc_ctx *ctx, int64_t *launches, double *total_ms);
 
+/* Plaquette averages {P, P_s, P_t} (as in mc_record) of an SU(2) link field
+ * held by the caller in device memory in the canonical order (float
+ * q[s][mu][4], 16-byte aligned), written to three doubles of device memory at
+ * `out` on `cuda_stream` (async; NULL = legacy default stream).  The paper has
+ * no counterpart: this entry point is for callers that cannot allocate device
+ * memory -- a process whose device memory is owned by another allocator (a
+ * framework's pool, an arena fixed at start-up), or a monitoring loop that must
+ * not enter the CUDA allocator -- so it needs no context or workspace and
+ * allocates nothing.  Its partial sums live in a fixed 256 KiB array inside
+ * libmc.so, held on every device that loads the library until the process
+ * exits; lattices of more than 4,194,304 sites are rejected with MC_EINVAL.
+ * The first call on a device, made with that device current, looks up the
+ * array's device address; make that first call before any stream capture.
+ * Every call uses the same array: calls that overlap on the GPU (other
+ * streams, other host threads) race and give wrong results. */
+MC_API mc_status mc_su2_plaquette_noalloc(const float *links, const int32_t L[4], double *out, void *cuda_stream);
+
 /* Destroy the context (synchronises its stream first; frees graphs). */
 MC_API mc_status mc_destroy(mc_ctx *ctx);
 

@@ -326,6 +326,7 @@ static cudaError_t prof_record(mc_ctx *c)
     }
     return cudaEventRecord(c->events[c->events_used++], c->stream);
 }
+void set_last_error(const std::string &msg) { g_err = msg; }
 cudaError_t prof_begin(mc_ctx *c) { return c->profiling ? prof_record(c) : cudaSuccess; }
 cudaError_t prof_end(mc_ctx *c) { return c->profiling ? prof_record(c) : cudaSuccess; }
 }  // namespace mc

@@ -170,6 +170,9 @@ void su2_plan_grid(mc_ctx *c);
 
 cudaError_t advance_state_launch(mc_ctx *c, long long n, long long recs);
 
+// Message returned by mc_last_error() on this thread.
+void set_last_error(const std::string &msg);
+
 // Bracket one sweep-kernel launch with events when the context is profiling.
 cudaError_t prof_begin(mc_ctx *c);
 cudaError_t prof_end(mc_ctx *c);

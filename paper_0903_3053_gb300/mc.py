@@ -27,7 +27,7 @@ EXPORTS = [
     "mc_workspace_bytes", "mc_batch_init", "mc_ising_init", "mc_su2_init", "mc_sweep", "mc_set_mode", "mc_sync",
     "mc_measure", "mc_read_series", "mc_get_config", "mc_set_config", "mc_config_bytes", "mc_get_sweep",
     "mc_set_sweep", "mc_su2_record_tries", "mc_su2_get_tries", "mc_su2_failed_updates", "mc_destroy",
-    "mc_last_error", "mc_version", "mc_profile_enable", "mc_profile_read",
+    "mc_last_error", "mc_version", "mc_profile_enable", "mc_profile_read", "mc_su2_plaquette_noalloc",
 ]
 
 
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mc_destroy": (st, [P]),
         "mc_profile_enable": (st, [P, c.c_int32]),
         "mc_profile_read": (st, [P, P, P]),
+        "mc_su2_plaquette_noalloc": (st, [P, P, P, P]),
         "mc_last_error": (c.c_char_p, []),
         "mc_version": (c.c_char_p, []),
     }
@@ -153,6 +154,18 @@ def mc_workspace_bytes(chains, layout=MC_LAYOUT_INT8, series_capacity=1024) -> i
     if n == 0:
         raise MCError(MC_EINVAL, load().mc_last_error().decode())
     return int(n)
+
+
+def su2_plaquette_noalloc(links, L, out, stream=None):
+    """{P, P_s, P_t} of a canonical-order float32 CUDA tensor `links` (shape
+    (N, 4, 4)) into the float64 CUDA tensor `out` (3 entries), for callers
+    that cannot let the library allocate: no context, no workspace, nothing
+    allocated (see include/mc.h for the size limit and the shared scratch)."""
+    torch = _torch()
+    dims = (ctypes.c_int32 * 4)(*[int(v) for v in L])
+    st = stream if stream is not None else torch.cuda.current_stream(links.device)
+    _check(load().mc_su2_plaquette_noalloc(ctypes.c_void_p(links.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.c_void_p(st.cuda_stream)))
 
 
 class Batch:

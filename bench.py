@@ -198,8 +198,9 @@ def run_gb300(args):
     # ---- end to end through the C ABI, host buffers -----------------------------
     e2e = run_e2e(mc, torch, rank, min(K, args.e2e_steps), world)
 
-    # ---- SU(2) component ------------------------------------------------------------
+    # ---- SU(2) and batched-chain components -------------------------------------------
     su2 = run_su2(mc, torch, rank, args.su2_steps, world)
+    batched = run_batched(mc, torch, rank, args.batch_steps, world)
 
     line = {
         "metric": METRIC,
@@ -238,7 +239,7 @@ def run_gb300(args):
         "e2e": e2e,
         "gpu_launches": launches + K,  # 2 half-sweeps + 1 state-advance kernel per step
         "clocks": clock_info,
-        "components": {"su2": su2},
+        "components": {"su2": su2, "batched": batched},
         "device": dev_props.name,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -326,6 +327,55 @@ def run_su2(mc, torch, rank, K, world):
                              "bytes_per_update": SU2_BYTES_PER_UPDATE}}
 
 
+def run_batched(mc, torch, rank, K, world, sweeps_per_call=10):
+    """256 Ising + 64 SU(2) chains of uneven sizes in one persistent launch per
+    call (autotuned launch shape); value = site/link updates per second."""
+    from paper_0903_3053_gb300 import autotune, workloads
+    spec = workloads.batched_chains(seed=0)
+    off = rank * 100000
+
+    def chain(d):
+        f = mc.ising if d["kind"] == "ising" else mc.su2
+        return f(d["L"], d["beta"], d["seed"], d["chain_id"] + off)
+
+    i8 = [chain(d) for d in spec if d["kind"] == "ising" and d["L"] < 64]
+    msc = [chain(d) for d in spec if d["kind"] == "ising" and d["L"] >= 64]
+    s2 = [chain(d) for d in spec if d["kind"] == "su2"]
+    cap = sweeps_per_call * (K + 2) + 64
+    bs = [mc.Batch(i8, layout=mc.MC_LAYOUT_INT8, series_capacity=cap),
+          mc.Batch(msc, layout=mc.MC_LAYOUT_MSC32, series_capacity=cap), mc.Batch(s2, series_capacity=cap)]
+    g = mc.Group(bs)
+    choice = autotune.tune_group(g, n_sweeps=sweeps_per_call, reps=2)
+    for b in bs:
+        b.read_series()
+    g.sweep(sweeps_per_call, 1)
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(K):
+        g.sweep(sweeps_per_call, 1)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(t0.elapsed_time(t1), world)
+    nc, nr = g.schedule()
+    for b in bs:
+        b.read_series()
+    g.close()
+    per_sweep = sum(c.L[0] * c.L[1] for c in i8 + msc) + sum(4 * int(np.prod(c.L)) for c in s2)
+    sweeps = K * sweeps_per_call
+    return {"metric": "batched updates/s", "value": per_sweep * sweeps * world / (ms / 1e3),
+            "unit": "site+link updates/s",
+            "workload": "256 Ising chains L in {32..1024}, beta ~ U[0.35, 0.55] + 64 SU(2) chains L^4, "
+                        "L in {4, 6, 8, 12, 16}, beta ~ U[1.8, 2.6] (numpy default_rng(0)); E/M and plaquette "
+                        "every sweep", "launches_per_call": 1 + len(bs), "sweeps_per_call": sweeps_per_call,
+            "ms_per_sweep": ms / sweeps, "clusters": nc, "rounds": nr,
+            "autotuned": {k: choice[k] for k in ("cluster", "threads", "split", "cached")}}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 def cpu_baseline(seconds: float) -> dict:
     """The oracle as it stands (plain C, one thread) on a bounded sample of the
@@ -383,6 +433,7 @@ def main():
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--su2-steps", type=int, default=40)
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

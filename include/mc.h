@@ -176,6 +176,37 @@ MC_API mc_status mc_profile_enable(mc_ctx *ctx, int32_t enable);
  * the previous read (synchronous; resets the counters). */
 MC_API mc_status mc_profile_read(mc_ctx *ctx, int64_t *launches, double *total_ms);
 
+/* ---- Batched chains in one persistent launch ---------------------------------
+ * A group advances every chain of up to 16 contexts (any mix of Ising layouts
+ * and SU(2)) with ONE persistent kernel launch per call, replayed from a CUDA
+ * graph -- the paper runs independent parameter points side by side (Sec. 3);
+ * here they share one GPU.  The grid is a set of thread-block clusters; a
+ * host-computed longest-first schedule gives each cluster a list of rounds,
+ * each either one large chain split over the cluster's CTAs (phases separated
+ * by the hardware cluster barrier) or up to cluster-size small chains, one per
+ * CTA.  Results are bit-identical to the contexts' own mc_sweep (same Philox
+ * counters), so any configuration may be chosen for speed alone.
+ * Member contexts must have been created on the group's stream and stay alive
+ * until mc_group_destroy; records go to each member's own ring buffer. */
+typedef struct mc_group mc_group; /* opaque, owned by the library */
+
+/* Device workspace the group needs for its schedule and scratch (0 = error). */
+MC_API size_t mc_group_workspace_bytes(int32_t n_ctx, mc_ctx *const *ctxs);
+MC_API mc_status mc_group_create(mc_group **out, int32_t n_ctx, mc_ctx *const *ctxs, void *workspace,
+                                 size_t workspace_bytes, void *cuda_stream);
+/* cluster_size in {1, 2, 4, 8} (0 = keep; default 4); threads_per_block a
+ * multiple of 32 in [64, 256] (0 = keep; default 256); a chain whose estimated
+ * cost (MSC spin-flip units per sweep: Ising int8 2 per site, MSC 1 per site,
+ * SU(2) 60 per link) is at least split_cost is shared by a whole cluster
+ * (split_cost < 0: one CTA's fair share of the total).  Invalidates the
+ * schedule; the next mc_group_sweep recomputes it. */
+MC_API mc_status mc_group_configure(mc_group *g, int32_t cluster_size, int32_t threads_per_block, double split_cost);
+/* Advance every member chain by n_sweeps (async), recording as mc_sweep does. */
+MC_API mc_status mc_group_sweep(mc_group *g, int64_t n_sweeps, int32_t measure_every);
+/* Clusters in the launch and rounds in the schedule (0 before the first sweep). */
+MC_API mc_status mc_group_schedule(const mc_group *g, int32_t *n_clusters, int32_t *n_rounds);
+MC_API mc_status mc_group_destroy(mc_group *g);
+
 /* Plaquette averages {P, P_s, P_t} (as in mc_record) of an SU(2) link field
  * held by the caller in device memory in the canonical order (float
  * q[s][mu][4], 16-byte aligned), written to three doubles of device memory at

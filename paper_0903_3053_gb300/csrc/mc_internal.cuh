@@ -71,6 +71,22 @@ __device__ __forceinline__ void latch_error(DevState *st, int code, int info)
         st->err_info = info;
 }
 
+// Lattice load policy.  Kernels that never read a location written during the
+// same launch use the read-only path (kLdReadOnly); the persistent batch
+// kernel, whose later phases read what earlier phases (possibly on other SMs
+// of the cluster) wrote, loads through L2, the device's point of coherence.
+constexpr int kLdReadOnly = 0, kLdPlain = 1, kLdCoherent = 2;
+template <int LD, typename T>
+__device__ __forceinline__ T lat_load(const T *p)
+{
+    if (LD == kLdCoherent)
+        return __ldcg(p);
+    else if (LD == kLdReadOnly)
+        return __ldg(p);
+    else
+        return *p;
+}
+
 // Largest k in [0, n) with block_start[k] <= b (block_start ascending, [0] = 0).
 __device__ __forceinline__ int find_chain(const uint32_t *__restrict__ block_start, int n, uint32_t b)
 {

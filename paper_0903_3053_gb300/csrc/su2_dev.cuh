@@ -1,0 +1,276 @@
+// su2_dev.cuh -- per-link device code of the 4D SU(2) heat-bath (Sec. 2.4,
+// Eqs. (2)-(7)), shared by the per-phase kernels of su2.cu and the persistent
+// batch kernel of batch.cu.  Quaternion links (U0, U1, U2, U3) of Eq. (4) in
+// FP32, stored per chain as float4 [parity][mu][site-within-parity].
+#pragma once
+#include "mc_internal.cuh"
+
+namespace mc {
+namespace {
+
+// (a0 + i a.sigma)(b0 + i b.sigma) = (a0 b0 - a.b) + i (a0 b + b0 a - a x b).sigma
+__device__ __forceinline__ float4 qmul(float4 a, float4 b)
+{
+    return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
+                       a.x * b.y + b.x * a.y - (a.z * b.w - a.w * b.z),
+                       a.x * b.z + b.x * a.z - (a.w * b.y - a.y * b.w),
+                       a.x * b.w + b.x * a.w - (a.y * b.z - a.z * b.y));
+}
+__device__ __forceinline__ float4 qdag(float4 a) { return make_float4(a.x, -a.y, -a.z, -a.w); }
+__device__ __forceinline__ float4 qadd(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float qdot(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+
+struct Site {
+    int x[4];
+};
+
+__device__ __forceinline__ Site site_from_parity_index(const Su2Chain &ch, int p, uint32_t e)
+{
+    const uint32_t L1h = (uint32_t)ch.L[1] >> 1;
+    uint32_t r = e;
+    const int x1h = (int)(r % L1h);
+    r /= L1h;
+    Site s;
+    s.x[2] = (int)(r % (uint32_t)ch.L[2]);
+    r /= (uint32_t)ch.L[2];
+    s.x[3] = (int)(r % (uint32_t)ch.L[3]);
+    s.x[0] = (int)(r / (uint32_t)ch.L[3]);
+    s.x[1] = 2 * x1h + ((p + s.x[0] + s.x[2] + s.x[3]) & 1);
+    return s;
+}
+
+__device__ __forceinline__ uint32_t canonical(const Su2Chain &ch, const Site &s)
+{
+    return (uint32_t)(s.x[1] + ch.L[1] * (s.x[2] + ch.L[2] * (s.x[3] + ch.L[3] * s.x[0])));
+}
+
+template <int D>
+__device__ __forceinline__ Site step(const Su2Chain &ch, Site s, int dir)
+{
+    s.x[D] += dir;
+    if (s.x[D] == ch.L[D])
+        s.x[D] = 0;
+    else if (s.x[D] < 0)
+        s.x[D] = ch.L[D] - 1;
+    return s;
+}
+
+template <int LD>
+__device__ __forceinline__ float4 load_link(const float4 *U, uint32_t nh, int par, int dir, uint32_t e)
+{
+    return lat_load<LD>(&U[(size_t)(par * 4 + dir) * nh + e]);
+}
+
+// Canonical index strides: direction mu moves the canonical index by st[mu].
+struct Strides {
+    uint32_t st[4];
+};
+
+__device__ __forceinline__ Strides strides_of(const Su2Chain &ch)
+{
+    Strides g;
+    g.st[1] = 1u;
+    g.st[2] = (uint32_t)ch.L[1];
+    g.st[3] = (uint32_t)(ch.L[1] * ch.L[2]);
+    g.st[0] = (uint32_t)(ch.L[1] * ch.L[2] * ch.L[3]);
+    return g;
+}
+
+// Canonical index of x + e_D / x - e_D, given x's coordinate along D.
+template <int D>
+__device__ __forceinline__ uint32_t fwd(const Su2Chain &ch, const Strides &g, int xd, uint32_t s)
+{
+    return xd + 1 == ch.L[D] ? s - (uint32_t)(ch.L[D] - 1) * g.st[D] : s + g.st[D];
+}
+template <int D>
+__device__ __forceinline__ uint32_t bwd(const Su2Chain &ch, const Strides &g, int xd, uint32_t s)
+{
+    return xd == 0 ? s + (uint32_t)(ch.L[D] - 1) * g.st[D] : s - g.st[D];
+}
+
+// The two staples of Eq. (6) in the (MU, NU) plane:
+//   U_nu(x) U_mu(x+nu) U_nu(x+mu)^+  +  U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu).
+// x + nu, x + mu and x - nu have parity 1 - P; x - nu + mu has parity P.
+template <int MU, int NU, int P, int LD>
+__device__ __forceinline__ float4 staple_pair(const float4 *__restrict__ U, const Su2Chain &ch, const Strides &g,
+                                              const Site &x, uint32_t s, uint32_t spm, uint32_t e)
+{
+    constexpr int Q = 1 - P;
+    const uint32_t nh = ch.nh;
+    const uint32_t spn = fwd<NU>(ch, g, x.x[NU], s);
+    const uint32_t smn = bwd<NU>(ch, g, x.x[NU], s);
+    const uint32_t smnpm = fwd<MU>(ch, g, x.x[MU], smn); // x - nu has the same MU coordinate as x
+    const float4 a = load_link<LD>(U, nh, P, NU, e);
+    const float4 b = load_link<LD>(U, nh, Q, MU, spn >> 1);
+    const float4 c = load_link<LD>(U, nh, Q, NU, spm >> 1);
+    const float4 d = load_link<LD>(U, nh, Q, NU, smn >> 1);
+    const float4 f = load_link<LD>(U, nh, Q, MU, smn >> 1);
+    const float4 h = load_link<LD>(U, nh, P, NU, smnpm >> 1);
+    return qadd(qmul(qmul(a, b), qdag(c)), qmul(qmul(qdag(d), f), h));
+}
+
+template <int MU, int P, int LD>
+__device__ __forceinline__ float4 staple(const float4 *__restrict__ U, const Su2Chain &ch, const Site &x, uint32_t s,
+                                         uint32_t e)
+{
+    const Strides g = strides_of(ch);
+    const uint32_t spm = fwd<MU>(ch, g, x.x[MU], s);
+    float4 W = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (MU != 0) W = qadd(W, staple_pair<MU, 0, P, LD>(U, ch, g, x, s, spm, e));
+    if (MU != 1) W = qadd(W, staple_pair<MU, 1, P, LD>(U, ch, g, x, s, spm, e));
+    if (MU != 2) W = qadd(W, staple_pair<MU, 2, P, LD>(U, ch, g, x, s, spm, e));
+    if (MU != 3) W = qadd(W, staple_pair<MU, 3, P, LD>(U, ch, g, x, s, spm, e));
+    return W;
+}
+
+constexpr int kKpTries = 8;
+constexpr int kCreutzTries = 64;
+constexpr uint8_t kFailed = 255;
+
+// Heat-bath draw of a0 ~ sqrt(1-a0^2) exp(alpha a0); returns the try taken.
+__device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, uint32_t sel, const Su2Chain &ch,
+                                       const PhiloxSchedule &ks, float &a0)
+{
+    if (alpha > 0.f) {
+        const float inv2a = 0.5f / alpha;
+        for (int t = 0; t < kKpTries; ++t) {
+            const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ks);
+            const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
+            const float u3 = uniform_open0(r.z), u4 = uniform_open0(r.w);
+            const float cs = cospif(2.0f * u2);
+            const float lam2 = -(logf(u1) + cs * cs * logf(u3)) * inv2a;
+            if (u4 * u4 <= 1.0f - lam2) {
+                a0 = 1.0f - 2.0f * lam2;
+                return t;
+            }
+        }
+    }
+    const float cexp = alpha > 0.f ? -expm1f(-2.0f * alpha) : 0.f; // 1 - e^{-2 alpha}
+    for (int t = kKpTries; t < kKpTries + kCreutzTries; ++t) {
+        const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ks);
+        const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
+        const float c = alpha > 0.f ? 1.0f + log1pf(-(1.0f - u1) * cexp) / alpha : 2.0f * u1 - 1.0f;
+        if (u2 * u2 <= 1.0f - c * c) {
+            a0 = c;
+            return t;
+        }
+    }
+    return kFailed;
+}
+
+// Heat-bath update of the link U_MU(x) at site e of parity P (Eqs. (5)-(7)):
+// staple, a0 by Kennedy-Pendleton / Creutz, direction on S^2, U = X V,
+// reprojection.  `tries` (or nullptr) receives the try taken at [s][MU].
+template <int P, int MU, int LD>
+__device__ __forceinline__ void su2_update_link(float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
+                                                uint32_t sweep, uint8_t *tries, DevState *state)
+{
+    const Site x = site_from_parity_index(ch, P, e);
+    const uint32_t s = canonical(ch, x);
+    const float4 W = staple<MU, P, LD>(U, ch, x, s, e);
+    const float k2 = qdot(W, W);
+    const float kn = sqrtf(k2);
+    float4 V = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (kn > 0.f) {
+        const float inv = 1.0f / kn;
+        V = make_float4(W.x * inv, W.y * inv, W.z * inv, W.w * inv);
+    }
+    const uint32_t sel = ((uint32_t)P << 12) | ((uint32_t)MU << 8);
+    float a0 = 0.f;
+    const int t = draw_a0(ch.beta * kn, e, sweep, sel, ch, ks, a0);
+    if (tries)
+        tries[ch.tries_off + (size_t)s * 4 + MU] = (uint8_t)t;
+    if (t == kFailed) {
+        atomicAdd(&state->hb_failures, 1ull);
+        return;
+    }
+    const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ks);
+    const float ct = 2.0f * uniform_open0(r.x) - 1.0f;
+    float sphi, cphi;
+    sincospif(2.0f * uniform_open0(r.y), &sphi, &cphi);
+    const float st = sqrtf(fmaxf(0.f, 1.0f - ct * ct));
+    const float rad = sqrtf(fmaxf(0.f, 1.0f - a0 * a0));
+    const float4 X = make_float4(a0, rad * st * cphi, rad * st * sphi, rad * ct);
+    float4 Un = qmul(X, V);
+    const float nrm = rsqrtf(qdot(Un, Un));
+    Un = make_float4(Un.x * nrm, Un.y * nrm, Un.z * nrm, Un.w * nrm);
+    U[(size_t)(P * 4 + MU) * ch.nh + e] = Un;
+}
+
+// Runtime (P, MU) dispatch of su2_update_link.
+template <int LD>
+__device__ __forceinline__ void su2_update_link_rt(int phase, float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks,
+                                                   uint32_t e, uint32_t sweep, uint8_t *tries, DevState *state)
+{
+    switch (phase) { // phase = position in the sweep: (odd, mu = 0..3), then (even, mu = 0..3)
+    case 0: su2_update_link<1, 0, LD>(U, ch, ks, e, sweep, tries, state); break;
+    case 1: su2_update_link<1, 1, LD>(U, ch, ks, e, sweep, tries, state); break;
+    case 2: su2_update_link<1, 2, LD>(U, ch, ks, e, sweep, tries, state); break;
+    case 3: su2_update_link<1, 3, LD>(U, ch, ks, e, sweep, tries, state); break;
+    case 4: su2_update_link<0, 0, LD>(U, ch, ks, e, sweep, tries, state); break;
+    case 5: su2_update_link<0, 1, LD>(U, ch, ks, e, sweep, tries, state); break;
+    case 6: su2_update_link<0, 2, LD>(U, ch, ks, e, sweep, tries, state); break;
+    default: su2_update_link<0, 3, LD>(U, ch, ks, e, sweep, tries, state); break;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Spatial and temporal sums of (1/2) Tr U_munu(x) (Eq. (3)) over the six
+// plaquettes with corner at canonical site s; FP32 products.
+template <int LD>
+__device__ __forceinline__ void su2_site_plaquettes(const float4 *U, const Su2Chain &ch, uint32_t s, float &fs,
+                                                    float &ft)
+{
+    Site x;
+    uint32_t r = s;
+    x.x[1] = (int)(r % (uint32_t)ch.L[1]);
+    r /= (uint32_t)ch.L[1];
+    x.x[2] = (int)(r % (uint32_t)ch.L[2]);
+    r /= (uint32_t)ch.L[2];
+    x.x[3] = (int)(r % (uint32_t)ch.L[3]);
+    x.x[0] = (int)(r / (uint32_t)ch.L[3]);
+    const int p = (x.x[0] + x.x[1] + x.x[2] + x.x[3]) & 1, q = 1 - p;
+    const uint32_t e = s >> 1;
+    float4 Ux[4], Uf[4][4]; // Uf[mu][nu] = U_nu(x + mu)
+    Site xf[4];
+    xf[0] = step<0>(ch, x, +1);
+    xf[1] = step<1>(ch, x, +1);
+    xf[2] = step<2>(ch, x, +1);
+    xf[3] = step<3>(ch, x, +1);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+        Ux[mu] = load_link<LD>(U, ch.nh, p, mu, e);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const uint32_t ef = canonical(ch, xf[mu]) >> 1;
+#pragma unroll
+        for (int nu = 0; nu < 4; ++nu)
+            if (nu != mu)
+                Uf[mu][nu] = load_link<LD>(U, ch.nh, q, nu, ef);
+    }
+    fs = 0.f;
+    ft = 0.f;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int nu = mu + 1; nu < 4; ++nu) {
+            // (1/2) Tr[U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+] = A . B
+            const float4 A = qmul(Ux[mu], Uf[mu][nu]);
+            const float4 B = qmul(Ux[nu], Uf[nu][mu]);
+            const float h = qdot(A, B);
+            if (mu == 0)
+                ft += h;
+            else
+                fs += h;
+        }
+}
+
+}  // namespace
+}  // namespace mc

@@ -28,6 +28,8 @@ EXPORTS = [
     "mc_measure", "mc_read_series", "mc_get_config", "mc_set_config", "mc_config_bytes", "mc_get_sweep",
     "mc_set_sweep", "mc_su2_record_tries", "mc_su2_get_tries", "mc_su2_failed_updates", "mc_destroy",
     "mc_last_error", "mc_version", "mc_profile_enable", "mc_profile_read", "mc_su2_plaquette_noalloc",
+    "mc_group_workspace_bytes", "mc_group_create", "mc_group_configure", "mc_group_sweep", "mc_group_schedule",
+    "mc_group_destroy",
 ]
 
 
@@ -92,6 +94,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mc_profile_enable": (st, [P, c.c_int32]),
         "mc_profile_read": (st, [P, P, P]),
         "mc_su2_plaquette_noalloc": (st, [P, P, P, P]),
+        "mc_group_workspace_bytes": (c.c_size_t, [c.c_int32, P]),
+        "mc_group_create": (st, [P, c.c_int32, P, P, c.c_size_t, P]),
+        "mc_group_configure": (st, [P, c.c_int32, c.c_int32, c.c_double]),
+        "mc_group_sweep": (st, [P, c.c_int64, c.c_int32]),
+        "mc_group_schedule": (st, [P, P, P]),
+        "mc_group_destroy": (st, [P]),
         "mc_last_error": (c.c_char_p, []),
         "mc_version": (c.c_char_p, []),
     }
@@ -313,3 +321,49 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Group:
+    """Chains of several Batches advanced by one persistent launch per call."""
+
+    def __init__(self, batches):
+        torch = _torch()
+        L = load()
+        self.batches = list(batches)
+        self.stream = self.batches[0].stream
+        for b in self.batches:
+            if b.stream.cuda_stream != self.stream.cuda_stream:
+                raise ValueError("every batch of a group must use the same CUDA stream")
+        arr = (ctypes.c_void_p * len(self.batches))(*[b._ctx.value for b in self.batches])
+        self._arr = arr
+        nbytes = L.mc_group_workspace_bytes(len(self.batches), arr)
+        if nbytes == 0:
+            raise MCError(MC_EINVAL, L.mc_last_error().decode())
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.batches[0].device)
+        self._g = ctypes.c_void_p()
+        _check(L.mc_group_create(ctypes.byref(self._g), len(self.batches), arr,
+                                 ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                 ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def configure(self, cluster_size: int = 0, threads_per_block: int = 0, split_cost: float = -1.0):
+        _check(load().mc_group_configure(self._g, int(cluster_size), int(threads_per_block), float(split_cost)))
+
+    def sweep(self, n: int, measure_every: int = 0):
+        _check(load().mc_group_sweep(self._g, int(n), int(measure_every)))
+
+    def schedule(self):
+        nc, nr = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().mc_group_schedule(self._g, ctypes.byref(nc), ctypes.byref(nr)))
+        return int(nc.value), int(nr.value)
+
+    def close(self):
+        if self._g:
+            st = load().mc_group_destroy(self._g)
+            self._g = ctypes.c_void_p()
+            _check(st)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

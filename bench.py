@@ -37,16 +37,14 @@ BETAS = [0.30, 0.40, 0.4406868, 0.50, 0.60]
 SIZES = [1024, 4096, 16384]
 SU2_BETAS = [1.5, 2.0, 2.3, 2.6]
 SU2_L = 32
-# Algorithmic integer operations per attempted flip in the MSC half-sweep: a
-# quarter of a Philox4x32-10 block (10 rounds x [2 wide multiplies + 2
-# three-input xors]) = 10, one threshold compare + insert = 2, and the
-# bit-sliced neighbour count, flip and measurement logic (~30 per 32-spin word)
-# ~ 1.
-ALU_OPS_PER_FLIP = 13.0
-# Lane-instruction issue rate of a GB300: 152 SMs x 4 schedulers x 32 lanes at
-# the 2070 MHz maximum SM clock.
-SM_COUNT, ISSUE_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-ALU_PEAK_OPS = SM_COUNT * ISSUE_LANES_PER_SM * SM_MAX_MHZ * 1e6
+# The MSC half-sweep is bound by the integer multiplier: every attempted flip
+# consumes one 32-bit Philox4x32-10 word, a quarter of a block of 10 rounds x 2
+# (32 x 32 -> 64)-bit products = 10 32-bit multiplies (high and low halves).
+MUL32_PER_FLIP = 10.0
+# 32-bit integer multiply rate of a GB300: 152 SMs x 64 per clock at the
+# 2070 MHz maximum SM clock (a pure-Philox probe measured 103% of this).
+SM_COUNT, MUL32_PER_SM_CLK, SM_MAX_MHZ = 152, 64, 2070.0
+MUL32_PEAK = SM_COUNT * MUL32_PER_SM_CLK * SM_MAX_MHZ * 1e6
 # Algorithmic bytes per SU(2) link update: read + write of the link once per sweep.
 SU2_BYTES_PER_UPDATE = 32.0
 
@@ -189,8 +187,8 @@ def run_gb300(args):
     value = flips / (ms_max / 1e3)
     # dominant kernel: the MSC half-sweep (launches = 2 per step)
     half_ms = kernel_ms / max(launches, 1)
-    ops_per_launch = ALU_OPS_PER_FLIP * flips_per_step() / 2
-    achieved = ops_per_launch / (half_ms / 1e3)
+    mul_per_launch = MUL32_PER_FLIP * flips_per_step() / 2
+    achieved = mul_per_launch / (half_ms / 1e3)
     batch.close()
     del batch
     torch.cuda.empty_cache()
@@ -227,14 +225,16 @@ def run_gb300(args):
         "roofline": {
             "bound": "alu",
             "achieved": achieved,
-            "peak": ALU_PEAK_OPS,
-            "unit": "int-op/s",
-            "frac": achieved / ALU_PEAK_OPS,
+            "peak": MUL32_PEAK,
+            "unit": "int32-mul/s",
+            "frac": achieved / MUL32_PEAK,
             "traffic": None,
             "kernel": "k_half_sweep<C, MSC32> (Ising half-sweep)",
             "kernel_ms_per_launch": half_ms,
             "kernel_share_of_step": kernel_ms / ms if ms > 0 else None,
-            "peak_source": "derived: 152 SMs x 128 lane-instr/clk x 2070 MHz (no ALU figure in MEASURED_PEAKS.json)",
+            "algorithmic": "10 int32 multiplies per attempted flip (1/4 Philox4x32-10 block)",
+            "peak_source": "derived: 152 SMs x 64 int32 multiplies/clk x 2070 MHz (MEASURED_PEAKS.json has no "
+                           "integer figure); a pure-Philox probe reached 103% of it",
         },
         "e2e": e2e,
         "gpu_launches": launches + K,  # 2 half-sweeps + 1 state-advance kernel per step

@@ -207,6 +207,55 @@ MC_API mc_status mc_group_sweep(mc_group *g, int64_t n_sweeps, int32_t measure_e
 MC_API mc_status mc_group_schedule(const mc_group *g, int32_t *n_clusters, int32_t *n_rounds);
 MC_API mc_status mc_group_destroy(mc_group *g);
 
+/* ---- Learned global proposal ------------------------------------------------
+ * Not in the paper: a masked autoregressive convolutional network over Ising
+ * spins (variational autoregressive network, Wu, Wang & Zhang, PRL 122 (2019)
+ * 080602) -- layer 1 a 5x5 convolution 1 -> 32 channels with mask A, layers
+ * 2..depth-1 5x5 convolutions 32 -> 32 with mask B, ReLU after each, the last a
+ * 5x5 convolution 32 -> 1 with mask B giving p(s_k = +1 | s_<k) =
+ * sigmoid(f_k) in raster order, zero padding -- used as an independence
+ * proposal for the chains of an int8-layout Ising context and corrected by
+ * Metropolis-Hastings with q_sym(s) = (q(s) + q(-s)) / 2, so the stationary
+ * distribution stays that of Eq. (1).  BF16 weights and activations, FP32
+ * accumulation (tensor cores for the 32 -> 32 layers), FP64 log q.
+ * Parameters cross the ABI as FP32 in the order: for each layer l,
+ * W[out][in][5][5] then b[out] (taps outside the mask are ignored). */
+typedef struct mc_van mc_van;
+
+MC_API size_t mc_van_param_count(int32_t depth);                          /* 0 if depth not in [3, 7] */
+MC_API size_t mc_van_workspace_bytes(int32_t L, int32_t batch, int32_t depth); /* L even, <= 128 */
+/* batch = most configurations one call handles (and chains one MH round serves). */
+MC_API mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, uint64_t seed, void *workspace,
+                               size_t workspace_bytes, void *cuda_stream);
+MC_API mc_status mc_van_set_params(mc_van *w, const float *host_params, size_t n); /* resets Adam */
+/* Parameters (and, if host_grads != NULL, the gradient of the last training step). */
+MC_API mc_status mc_van_get_params(mc_van *w, float *host_params, size_t n, float *host_grads);
+/* log q of n device configurations int8 [n][L][L] (or of their global flips if
+ * negate) into device doubles (async). */
+MC_API mc_status mc_van_log_prob(mc_van *w, const int8_t *dev_spins, int32_t n, int32_t negate, double *dev_logq);
+/* Maximum likelihood: loss = -mean log q over n device configurations; forward,
+ * backward and (if apply) one Adam step with learning rate lr.  *host_loss (if
+ * non-NULL) receives the loss before the step (synchronous then). */
+MC_API mc_status mc_van_train_step(mc_van *w, const int8_t *dev_spins, int32_t n, float lr, int32_t apply,
+                                   double *host_loss);
+/* n autoregressive samples into device int8 [n][L][L] and their log q into
+ * device doubles; sample i uses Philox key `seed`, counter (k >> 2, round,
+ * TAG_SAMPLE, id_i) word k & 3 for position k, id_i = dev_ids[i] or i. */
+MC_API mc_status mc_van_sample(mc_van *w, int32_t n, uint32_t round, const uint32_t *dev_ids, int8_t *dev_out,
+                               double *dev_logq);
+/* One Metropolis-Hastings round for every chain of an int8-layout Ising
+ * context (all chains L x L, same stream): sample a proposal per chain, flip it
+ * globally with probability 1/2, accept with min(1, e^{-beta dE} q_sym(s) /
+ * q_sym(s')) using Philox (0, round, TAG_MH, chain id), write accepted
+ * proposals into the chains.  *host_accepted (if non-NULL) receives the number
+ * accepted (synchronous then).  The round counter advances by one. */
+MC_API mc_status mc_van_mh_round(mc_van *w, mc_ctx *c, int32_t *host_accepted);
+MC_API mc_status mc_van_set_round(mc_van *w, uint32_t round);
+MC_API mc_status mc_van_destroy(mc_van *w);
+/* Copy every chain of an int8-layout Ising context (all L x L) into / from
+ * (back != 0) one contiguous device buffer int8 [n_chains][L][L] (async). */
+MC_API mc_status mc_ising_gather(mc_ctx *c, int8_t *dev_buf, int32_t back);
+
 /* Plaquette averages {P, P_s, P_t} (as in mc_record) of an SU(2) link field
  * held by the caller in device memory in the canonical order (float
  * q[s][mu][4], 16-byte aligned), written to three doubles of device memory at

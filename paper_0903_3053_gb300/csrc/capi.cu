@@ -408,6 +408,7 @@ mc_status mc_batch_init(mc_ctx **out, int32_t n_chains, const mc_chain_desc *cha
             ch.Ly = (uint32_t)chains[k].L[1];
             ch.W = ch.Lx / 64;
             thresholds(chains[k].beta, ch.T2, ch.T4);
+            ch.beta = chains[k].beta;
             ch.key = PhiloxKey{(uint32_t)chains[k].seed, (uint32_t)(chains[k].seed >> 32)};
             ch.chain_id = chains[k].chain_id;
             ch.spin_off = p.lat_off[k];

@@ -28,6 +28,7 @@ struct IsingChain {
     uint32_t chain_id;  // Philox counter word 3
     uint32_t pad0;
     uint64_t spin_off;  // byte offset of the chain's spins in the lattice region
+    double beta;        // coupling (the Metropolis-Hastings step of the learned proposal needs it)
 };
 
 // Per-chain descriptor of a 4D SU(2) chain.

@@ -1,0 +1,1091 @@
+// van.cu -- the learned global proposal: masked autoregressive conv net
+// (forward, backward, Adam), autoregressive sampler, and the symmetrised
+// Metropolis-Hastings round over the chains of an Ising context.  See
+// van_dev.cuh for the network.  The paper has no learned component.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "van_dev.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace mc {
+namespace van {
+namespace {
+
+// ------------------------------------------------------------------ parameters
+// Canonical FP32 parameter layout (the same as the FP64 oracle): for each layer
+// l, W[o][i][5][5] then b[o]; cin = 1 for l = 0, cout = 1 for l = D - 1.
+struct ParamLayout {
+    int D;
+    size_t w_off[kMaxDepth], b_off[kMaxDepth], total;
+};
+
+__host__ __device__ inline int layer_cin(int l) { return l == 0 ? 1 : kCh; }
+__host__ __device__ inline int layer_cout(int l, int D) { return l == D - 1 ? 1 : kCh; }
+
+ParamLayout param_layout(int D)
+{
+    ParamLayout p{};
+    p.D = D;
+    size_t off = 0;
+    for (int l = 0; l < D; ++l) {
+        p.w_off[l] = off;
+        off += (size_t)layer_cout(l, D) * layer_cin(l) * 25;
+        p.b_off[l] = off;
+        off += (size_t)layer_cout(l, D);
+    }
+    p.total = off;
+    return p;
+}
+
+struct DevParams {
+    size_t w_off[kMaxDepth], b_off[kMaxDepth];
+    int D;
+};
+
+__device__ __forceinline__ size_t canon_w(const DevParams &P, int l, int o, int i, int dy, int dx)
+{
+    return P.w_off[l] + (((size_t)o * layer_cin(l) + i) * 5 + (dy + 2)) * 5 + (dx + 2);
+}
+
+// Kernel-side copies of the weights, rounded to BF16: hidden layers as
+// [l][tap][o][c] (BF16), layer 1 as [o][tap] and the last layer as [tap][c]
+// (FP32 holding BF16-rounded values), biases FP32.
+__global__ void k_prep_weights(const float *p, DevParams P, bf16 *wh, float *w1, float *wD, float *bias)
+{
+    const int D = P.D;
+    const int nh = (D - 2) * kTapsB * kCh * kCh;
+    const int total = nh + kCh * kTapsA + kTapsB * kCh + (D - 1) * kCh + 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        if (i < nh) {
+            const int l = 1 + i / (kTapsB * kCh * kCh), r = i % (kTapsB * kCh * kCh);
+            const int t = r / (kCh * kCh), o = (r / kCh) % kCh, c = r % kCh;
+            wh[i] = __float2bfloat16(p[canon_w(P, l, o, c, tap_dy(t), tap_dx(t))]);
+        } else if (i < nh + kCh * kTapsA) {
+            const int r = i - nh, o = r / kTapsA, t = r % kTapsA;
+            w1[r] = bf(__float2bfloat16(p[canon_w(P, 0, o, 0, tap_dy(t), tap_dx(t))]));
+        } else if (i < nh + kCh * kTapsA + kTapsB * kCh) {
+            const int r = i - nh - kCh * kTapsA, t = r / kCh, c = r % kCh;
+            wD[r] = bf(__float2bfloat16(p[canon_w(P, D - 1, 0, c, tap_dy(t), tap_dx(t))]));
+        } else {
+            const int r = i - nh - kCh * kTapsA - kTapsB * kCh; // biases: layers 0..D-2 x 32, then the last
+            const int l = r / kCh, o = r % kCh;
+            bias[r] = l < D - 1 ? p[P.b_off[l] + o] : p[P.b_off[D - 1]];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ forward
+// Layer 1: 1 -> 32 channels, mask A, ReLU.  One thread per (position, channel).
+__global__ void k_layer1_fwd(const int8_t *spins, int negate, const float *w1, const float *b1, bf16 *h1, int n,
+                             int L)
+{
+    const size_t total = (size_t)n * L * L * kCh;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int o = (int)(i % kCh);
+        const size_t p = i / kCh;
+        const int x = (int)(p % L), y = (int)((p / L) % L);
+        const size_t b = p / ((size_t)L * L);
+        float acc = b1[o];
+#pragma unroll
+        for (int t = 0; t < kTapsA; ++t) {
+            const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+            if (yy >= 0 && xx >= 0 && xx < L) {
+                const float s = (float)spins[(b * L + yy) * L + xx];
+                acc += w1[o * kTapsA + t] * (negate ? -s : s);
+            }
+        }
+        h1[i] = __float2bfloat16(fmaxf(acc, 0.f));
+    }
+}
+
+// 32 -> 32 masked convolution on the tensor cores.  One CTA row item (sample b,
+// row y) at a time; warp w computes positions 16 w .. 16 w + 15 for all 32
+// output channels: K = 13 taps x 32 input channels in 26 k16 steps.
+//   forward  (BWD = false): out = ReLU(conv(in) + bias), taps at (dy, dx).
+//   backward (BWD = true) : out = conv^T(in) * [mask_src > 0], the gradient
+//     with respect to the layer input, masked by the previous layer's ReLU:
+//     taps at (-dy, -dx) and transposed weights.
+template <bool BWD>
+__global__ void __launch_bounds__(256) k_conv32(const bf16 *__restrict__ in, bf16 *__restrict__ out,
+                                                const bf16 *__restrict__ W, const float *__restrict__ bias,
+                                                const bf16 *__restrict__ mask_src, int n, int L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    bf16 *Ws = reinterpret_cast<bf16 *>(smem);      // [13][32][40]
+    bf16 *Xs = Ws + kTapsB * kCh * kRowStride;       // [3][PX][40]
+    const int NW = (L + 15) / 16, PX = NW * 16 + 4;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < kTapsB * kCh * kCh; i += blockDim.x) {
+        const int t = i / (kCh * kCh), r = (i / kCh) % kCh, q = i % kCh; // W[t][o = r][c = q]
+        if (!BWD)
+            Ws[(t * kCh + r) * kRowStride + q] = W[i];
+        else
+            Ws[(t * kCh + q) * kRowStride + r] = W[i];
+    }
+    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
+        const int b = item / L, y = item % L;
+        __syncthreads(); // weights ready / previous item's reads done
+        for (int i = tid; i < 3 * PX * 4; i += blockDim.x) {
+            const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
+            const int yy = BWD ? y + r : y - 2 + r, xx = xi - 2;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (yy >= 0 && yy < L && xx >= 0 && xx < L)
+                v = *reinterpret_cast<const uint4 *>(in + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8);
+            *reinterpret_cast<uint4 *>(Xs + (r * PX + xi) * kRowStride + ch * 8) = v;
+        }
+        __syncthreads();
+        if (warp < NW) {
+            float acc[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+            const int x0 = warp * 16;
+            const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
+            const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
+#pragma unroll 1
+            for (int t = 0; t < kTapsB; ++t) {
+                const int dy = tap_dy(t), dx = tap_dx(t);
+                const int r = BWD ? -dy : dy + 2, xoff = BWD ? -dx : dx;
+#pragma unroll
+                for (int kc = 0; kc < 2; ++kc) {
+                    uint32_t a0, a1, a2, a3;
+                    ldsm_x4(smem_u32(Xs + (r * PX + x0 + arow + xoff + 2) * kRowStride + kc * 16 + acol), a0, a1, a2,
+                            a3);
+#pragma unroll
+                    for (int np = 0; np < 2; ++np) {
+                        uint32_t b0, b1, b2, b3;
+                        ldsm_x4(smem_u32(Ws + (t * kCh + np * 16 + brow) * kRowStride + kc * 16 + bcol), b0, b1, b2,
+                                b3);
+                        mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
+                        mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+                    }
+                }
+            }
+            const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int x = x0 + g + 8 * h;
+                    if (x >= L)
+                        continue;
+                    const int c = 8 * j + 2 * t4;
+                    const size_t o = (((size_t)b * L + y) * L + x) * kCh + c;
+                    float v0 = acc[j][2 * h], v1 = acc[j][2 * h + 1];
+                    if (!BWD) {
+                        v0 = fmaxf(v0 + bias[c], 0.f);
+                        v1 = fmaxf(v1 + bias[c + 1], 0.f);
+                    } else {
+                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(mask_src + o);
+                        v0 = bf(m.x) > 0.f ? v0 : 0.f;
+                        v1 = bf(m.y) > 0.f ? v1 : 0.f;
+                    }
+                    *reinterpret_cast<__nv_bfloat162 *>(out + o) = __floats2bfloat162_rn(v0, v1);
+                }
+        }
+    }
+}
+
+// Last layer (32 -> 1, mask B): logit f, and per position log p(s_k | s_<k) =
+// log sigmoid(s f) and (training) dF = -(1/n) s sigmoid(-s f).
+__global__ void k_layerD_fwd(const bf16 *hD, const float *wD, const float *bD, const int8_t *spins, int negate,
+                             float *f, float *ll, float *dF, float inv_n, int n, int L)
+{
+    const size_t total = (size_t)n * L * L;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(p % L), y = (int)((p / L) % L);
+        const size_t b = p / ((size_t)L * L);
+        float acc = bD[0];
+        for (int t = 0; t < kTapsB; ++t) {
+            const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+            if (yy < 0 || xx < 0 || xx >= L)
+                continue;
+            const bf16 *h = hD + ((b * L + yy) * L + xx) * kCh;
+#pragma unroll
+            for (int c = 0; c < kCh; c += 2) {
+                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(h + c);
+                acc += wD[t * kCh + c] * bf(v.x) + wD[t * kCh + c + 1] * bf(v.y);
+            }
+        }
+        const float s = negate ? -(float)spins[p] : (float)spins[p];
+        f[p] = acc;
+        ll[p] = log_sigmoid(s * acc);
+        if (dF)
+            dF[p] = -inv_n * s * sigmoid(-s * acc);
+    }
+}
+
+// log q per sample: fixed-order FP64 sum of its L^2 log-probabilities.
+__global__ void k_logq(const float *ll, double *logq, int L)
+{
+    __shared__ double part[32];
+    const int b = blockIdx.x, n = L * L;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        acc += (double)ll[(size_t)b * n + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0)
+        part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            s += part[w];
+        logq[b] = s;
+    }
+}
+
+// ------------------------------------------------------------------ backward
+// Last layer: dZ_{D-1} = (sum_t wD[t] dF(p - d_t)) * [h_{D-1} > 0], one thread
+// per (position, channel).
+__global__ void k_layerD_bwd_data(const float *dF, const float *wD, const bf16 *hD, bf16 *dZ, int n, int L)
+{
+    const size_t total = (size_t)n * L * L * kCh;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % kCh);
+        const size_t p = i / kCh;
+        const int x = (int)(p % L), y = (int)((p / L) % L);
+        const size_t b = p / ((size_t)L * L);
+        float acc = 0.f;
+        for (int t = 0; t < kTapsB; ++t) {
+            const int yy = y - tap_dy(t), xx = x - tap_dx(t);
+            if (yy < L && xx >= 0 && xx < L)
+                acc += wD[t * kCh + c] * dF[(b * L + yy) * L + xx];
+        }
+        dZ[i] = __float2bfloat16(bf(hD[i]) > 0.f ? acc : 0.f);
+    }
+}
+
+// Last-layer weight and bias gradients: gW[t][c] = sum_p dF(p) h(p + d_t)[c].
+// Thread (t, c) accumulates over the CTA's rows; one atomic per thread.
+__global__ void k_layerD_bwd_w(const float *dF, const bf16 *hD, float *g, DevParams P, int n, int L)
+{
+    const int tid = threadIdx.x; // kTapsB * kCh + 1 threads
+    const int t = tid / kCh, c = tid % kCh;
+    float acc = 0.f;
+    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
+        const int b = item / L, y = item % L;
+        for (int x = 0; x < L; ++x) {
+            const float d = dF[((size_t)b * L + y) * L + x];
+            if (t < kTapsB) {
+                const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+                if (yy >= 0 && xx >= 0 && xx < L)
+                    acc += d * bf(hD[(((size_t)b * L + yy) * L + xx) * kCh + c]);
+            } else {
+                acc += d;
+            }
+        }
+    }
+    const int D = P.D;
+    if (t < kTapsB)
+        atomicAdd(&g[canon_w(P, D - 1, 0, c, tap_dy(t), tap_dx(t))], acc);
+    else if (c == 0)
+        atomicAdd(&g[P.b_off[D - 1]], acc);
+}
+
+// Hidden-layer weight and bias gradients on the tensor cores:
+// gW[t][o][c] = sum_p dZ(p)[o] X(p + d_t)[c] -- a 32 x 32 GEMM per tap with the
+// positions as the reduction dimension.  Warp w owns taps w and w + 8.
+__global__ void __launch_bounds__(256) k_dw32(const bf16 *__restrict__ dZ, const bf16 *__restrict__ X, float *g,
+                                              DevParams P, int layer, int n, int L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int NW = (L + 15) / 16, PX = NW * 16 + 4, PZ = NW * 16;
+    bf16 *Zs = reinterpret_cast<bf16 *>(smem); // [PZ][40]
+    bf16 *Xs = Zs + PZ * kRowStride;           // [3][PX][40]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntap = warp + 8 < kTapsB ? 2 : 1;
+    float acc[2][2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                acc[a][m][j][0] = acc[a][m][j][1] = acc[a][m][j][2] = acc[a][m][j][3] = 0.f;
+    float bsum = 0.f;
+    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
+        const int b = item / L, y = item % L;
+        __syncthreads();
+        for (int i = tid; i < PZ * 4; i += blockDim.x) {
+            const int xi = i / 4, ch = i % 4;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (xi < L)
+                v = *reinterpret_cast<const uint4 *>(dZ + (((size_t)b * L + y) * L + xi) * kCh + ch * 8);
+            *reinterpret_cast<uint4 *>(Zs + xi * kRowStride + ch * 8) = v;
+        }
+        for (int i = tid; i < 3 * PX * 4; i += blockDim.x) {
+            const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
+            const int yy = y - 2 + r, xx = xi - 2;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (yy >= 0 && xx >= 0 && xx < L)
+                v = *reinterpret_cast<const uint4 *>(X + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8);
+            *reinterpret_cast<uint4 *>(Xs + (r * PX + xi) * kRowStride + ch * 8) = v;
+        }
+        __syncthreads();
+        if (tid < kCh)
+            for (int x = 0; x < L; ++x)
+                bsum += bf(Zs[x * kRowStride + tid]);
+        for (int j = 0; j < NW; ++j) {
+            const int x0 = 16 * j;
+            // A = dZ^T (rows o, k = positions): 8x8 blocks (p0, o0) transposed
+            uint32_t a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int i = lane >> 3;
+                const int p0 = x0 + ((i >> 1) ? 8 : 0), o0 = 16 * mt + ((i & 1) ? 8 : 0);
+                ldsm_x4_t(smem_u32(Zs + (p0 + (lane & 7)) * kRowStride + o0), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+            }
+#pragma unroll
+            for (int tt = 0; tt < 2; ++tt) {
+                if (tt >= ntap)
+                    break;
+                const int t = warp + 8 * tt, dy = tap_dy(t), dx = tap_dx(t);
+#pragma unroll
+                for (int np = 0; np < 2; ++np) {
+                    // B = X shifted (k = positions, n = channels): blocks (pos, c0) transposed
+                    const int i = lane >> 3;
+                    const int p0 = x0 + ((i & 1) ? 8 : 0), c0 = 16 * np + ((i >> 1) ? 8 : 0);
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4_t(smem_u32(Xs + ((dy + 2) * PX + p0 + (lane & 7) + dx + 2) * kRowStride + c0), b0, b1, b2,
+                              b3);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        mma_bf16(acc[tt][mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                        mma_bf16(acc[tt][mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+                    }
+                }
+            }
+        }
+    }
+    const int gq = lane >> 2, t4 = lane & 3;
+    for (int tt = 0; tt < ntap; ++tt) {
+        const int t = warp + 8 * tt;
+        for (int mt = 0; mt < 2; ++mt)
+            for (int j = 0; j < 4; ++j)
+                for (int h = 0; h < 2; ++h) {
+                    const int o = 16 * mt + gq + 8 * h, c = 8 * j + 2 * t4;
+                    atomicAdd(&g[canon_w(P, layer, o, c, tap_dy(t), tap_dx(t))], acc[tt][mt][j][2 * h]);
+                    atomicAdd(&g[canon_w(P, layer, o, c + 1, tap_dy(t), tap_dx(t))], acc[tt][mt][j][2 * h + 1]);
+                }
+    }
+    if (tid < kCh)
+        atomicAdd(&g[P.b_off[layer] + tid], bsum);
+}
+
+// Layer-1 weight and bias gradients: gW1[o][t] = sum_p dZ1(p)[o] s(p + d_t).
+__global__ void k_layer1_bwd_w(const bf16 *dZ1, const int8_t *spins, float *g, DevParams P, int n, int L)
+{
+    const int tid = threadIdx.x; // kCh * (kTapsA + 1) threads
+    const int o = tid / (kTapsA + 1), t = tid % (kTapsA + 1);
+    float acc = 0.f;
+    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
+        const int b = item / L, y = item % L;
+        for (int x = 0; x < L; ++x) {
+            const float d = bf(dZ1[(((size_t)b * L + y) * L + x) * kCh + o]);
+            if (t < kTapsA) {
+                const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+                if (yy >= 0 && xx >= 0 && xx < L)
+                    acc += d * (float)spins[((size_t)b * L + yy) * L + xx];
+            } else {
+                acc += d;
+            }
+        }
+    }
+    if (t < kTapsA)
+        atomicAdd(&g[canon_w(P, 0, o, 0, tap_dy(t), tap_dx(t))], acc);
+    else
+        atomicAdd(&g[P.b_off[0] + o], acc);
+}
+
+__global__ void k_adam(float *p, float *m, float *v, const float *g, size_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+}  // namespace
+}  // namespace van
+}  // namespace mc
+
+namespace mc {
+namespace van {
+namespace {
+
+constexpr uint32_t kTagVanSample = 0x21000000u; // sampler uniforms
+constexpr uint32_t kTagVanMH = 0x22000000u;     // accept uniform and global flip
+constexpr int kSampleTile = 32;                 // samples per sampler CTA (two m16 tiles)
+constexpr int kAStride = kTapsB * kCh + 8;      // 424 bf16 per sample row of the gathered A tile
+
+// Autoregressive sampling, one position k = y L + x at a time in raster order.
+// Each CTA owns 32 samples.  At step k every layer is evaluated at position k
+// only: its 13 taps come from the ring hist[l][sample][row % 3][x][c] of that
+// layer's earlier outputs (rows y-2..y) and from the value just computed at k.
+// s_k = +1 iff u < sigmoid(f_k), u from Philox (k >> 2, round, TAG_SAMPLE, id)
+// word k & 3; log q accumulates log sigmoid(s_k f_k) in FP64.
+__global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, const float *__restrict__ w1,
+                                                const float *__restrict__ wD, const float *__restrict__ bias, int D,
+                                                int L, int n, bf16 *hist, int8_t *out, double *logq, PhiloxKey key,
+                                                uint32_t round, const uint32_t *ids)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nh = D - 2;
+    bf16 *Wh = reinterpret_cast<bf16 *>(smem);                    // [nh][13][32][40]
+    bf16 *As = Wh + (size_t)nh * kTapsB * kCh * kRowStride;       // [32][424]
+    bf16 *Hc = As + kSampleTile * kAStride;                        // [32][40] current layer at position k
+    float *W1 = reinterpret_cast<float *>(Hc + kSampleTile * kRowStride); // [32][12]
+    float *WD = W1 + kCh * kTapsA;                                 // [13][32]
+    float *Bs = WD + kTapsB * kCh;                                 // [(D-1) 32 + 1]
+    float *Fs = Bs + (D - 1) * kCh + 1;                            // [32] logits
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s0 = blockIdx.x * kSampleTile;
+    for (int i = tid; i < nh * kTapsB * kCh * kCh; i += blockDim.x) {
+        const int row = i / kCh, c = i % kCh; // row = (l, t, o)
+        Wh[row * kRowStride + c] = wh[i];
+    }
+    for (int i = tid; i < kCh * kTapsA; i += blockDim.x)
+        W1[i] = w1[i];
+    for (int i = tid; i < kTapsB * kCh; i += blockDim.x)
+        WD[i] = wD[i];
+    for (int i = tid; i < (D - 1) * kCh + 1; i += blockDim.x)
+        Bs[i] = bias[i];
+    double lq = 0.0; // owned by thread s (< 32)
+    uint32_t my_id = 0;
+    if (tid < kSampleTile && s0 + tid < n)
+        my_id = ids ? ids[s0 + tid] : (uint32_t)(s0 + tid);
+    const size_t ring = (size_t)3 * L * kCh; // per sample per layer
+    __syncthreads();
+    for (int k = 0; k < L * L; ++k) {
+        const int y = k / L, x = k % L, slot = y % 3;
+        // ---- layer 1 (CUDA cores): 32 samples x 32 channels
+        for (int i = tid; i < kSampleTile * kCh; i += blockDim.x) {
+            const int s = i / kCh, o = i % kCh, gs = s0 + s;
+            float acc = Bs[o];
+            if (gs < n)
+                for (int t = 0; t < kTapsA; ++t) {
+                    const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+                    if (yy >= 0 && xx >= 0 && xx < L)
+                        acc += W1[o * kTapsA + t] * (float)out[((size_t)gs * L + yy) * L + xx];
+                }
+            const bf16 h = __float2bfloat16(fmaxf(acc, 0.f));
+            Hc[s * kRowStride + o] = h;
+            if (gs < n)
+                hist[((size_t)gs * ring) + ((size_t)slot * L + x) * kCh + o] = h; // layer index 0
+        }
+        __syncthreads();
+        // ---- hidden layers (tensor cores): M = 32 samples, N = 32, K = 13 x 32
+        for (int l = 1; l <= nh; ++l) {
+            const bf16 *hprev = hist + (size_t)(l - 1) * n * ring;
+            for (int i = tid; i < kSampleTile * kTapsB * 4; i += blockDim.x) {
+                const int s = i / (kTapsB * 4), t = (i / 4) % kTapsB, ch = i % 4, gs = s0 + s;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (t == kTapsB - 1) {
+                    v = *reinterpret_cast<const uint4 *>(Hc + s * kRowStride + ch * 8);
+                } else if (gs < n) {
+                    const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+                    if (yy >= 0 && xx >= 0 && xx < L)
+                        v = *reinterpret_cast<const uint4 *>(hprev + (size_t)gs * ring +
+                                                             ((size_t)(yy % 3) * L + xx) * kCh + ch * 8);
+                }
+                *reinterpret_cast<uint4 *>(As + s * kAStride + t * kCh + ch * 8) = v;
+            }
+            __syncthreads();
+            const int mt = warp >> 2, nt = warp & 3; // 8 warps: 2 m-tiles x 4 n-tiles
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            const bf16 *Wl = Wh + (size_t)(l - 1) * kTapsB * kCh * kRowStride;
+            const int arow = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
+            const int brow = nt * 8 + (lane & 7), bcol = ((lane >> 3) & 1) * 8;
+#pragma unroll 2
+            for (int kk = 0; kk < 2 * kTapsB; ++kk) {
+                uint32_t a0, a1, a2, a3, b0, b1;
+                ldsm_x4(smem_u32(As + arow * kAStride + kk * 16 + acol), a0, a1, a2, a3);
+                const int t = kk >> 1, half = kk & 1;
+                ldsm_x2(smem_u32(Wl + (t * kCh + brow) * kRowStride + half * 16 + bcol), b0, b1);
+                mma_bf16(acc, a0, a1, a2, a3, b0, b1);
+            }
+            const int g = lane >> 2, t4 = lane & 3, o = nt * 8 + 2 * t4;
+            bf16 *hcur = hist + (size_t)l * n * ring;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int s = mt * 16 + g + 8 * h, gs = s0 + s;
+                const float bo = Bs[l * kCh + o], b1v = Bs[l * kCh + o + 1];
+                const __nv_bfloat162 v = __floats2bfloat162_rn(fmaxf(acc[2 * h] + bo, 0.f), fmaxf(acc[2 * h + 1] + b1v, 0.f));
+                *reinterpret_cast<__nv_bfloat162 *>(Hc + s * kRowStride + o) = v;
+                if (gs < n && l < nh) // the last hidden output feeds only the output layer
+                    *reinterpret_cast<__nv_bfloat162 *>(hcur + (size_t)gs * ring + ((size_t)slot * L + x) * kCh + o) = v;
+                if (gs < n && l == nh)
+                    *reinterpret_cast<__nv_bfloat162 *>(hcur + (size_t)gs * ring + ((size_t)slot * L + x) * kCh + o) = v;
+            }
+            __syncthreads();
+        }
+        // ---- output layer (CUDA cores): 8 lanes per sample, 4 channels each
+        {
+            const int s = tid >> 3, part = tid & 7, gs = s0 + s;
+            const bf16 *hlast = hist + (size_t)nh * n * ring;
+            float acc = 0.f;
+            if (gs < n)
+                for (int t = 0; t < kTapsB; ++t) {
+                    const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+                    if (yy < 0 || xx < 0 || xx >= L)
+                        continue;
+                    const bf16 *hp = t == kTapsB - 1 ? Hc + s * kRowStride
+                                                     : hlast + (size_t)gs * ring + ((size_t)(yy % 3) * L + xx) * kCh;
+#pragma unroll
+                    for (int c = part * 4; c < part * 4 + 4; ++c)
+                        acc += WD[t * kCh + c] * bf(hp[c]);
+                }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            if (part == 0)
+                Fs[s] = acc + Bs[(D - 1) * kCh];
+        }
+        __syncthreads();
+        // ---- draw s_k
+        if (tid < kSampleTile && s0 + tid < n) {
+            const float f = Fs[tid];
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)k >> 2, round, kTagVanSample, my_id), key);
+            const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+            const float u = uniform_open0(rr[k & 3]);
+            const float sp = u < sigmoid(f) ? 1.f : -1.f;
+            lq += (double)log_sigmoid(sp * f);
+            out[((size_t)(s0 + tid) * L + y) * L + x] = (int8_t)sp;
+        }
+        __syncthreads();
+    }
+    if (tid < kSampleTile && s0 + tid < n)
+        logq[s0 + tid] = lq;
+}
+
+// Copy the int8 lattices of every chain of an int8-layout Ising context into
+// one contiguous [n][L][L] buffer (or back, when `back`).
+__global__ void k_gather(const IsingChain *chains, char *lattice, int8_t *buf, int L, int n, int back)
+{
+    const size_t per = (size_t)L * L;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per * n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t k = i / per, j = i % per;
+        int8_t *lat = reinterpret_cast<int8_t *>(lattice + chains[k].spin_off);
+        if (back)
+            lat[j] = buf[i];
+        else
+            buf[i] = lat[j];
+    }
+}
+
+// H of Eq. (1) per configuration (exact).
+__global__ void k_energy(const int8_t *s, long long *E, int L)
+{
+    __shared__ long long part[32];
+    const size_t base = (size_t)blockIdx.x * L * L;
+    long long acc = 0;
+    for (int i = threadIdx.x; i < L * L; i += blockDim.x) {
+        const int y = i / L, x = i % L;
+        const int v = s[base + i];
+        acc -= v * (s[base + y * L + (x + 1) % L] + s[base + ((y + 1) % L) * L + x]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0)
+        part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            t += part[w];
+        E[blockIdx.x] = t;
+    }
+}
+
+__device__ __forceinline__ double log_add_exp(double a, double b)
+{
+    const double m = fmax(a, b);
+    return m + log1p(exp(-fabs(a - b)));
+}
+
+// Metropolis-Hastings for an independence proposal from q_sym(s) = (q(s) +
+// q(-s)) / 2: accept s' with probability min(1, e^{-beta (E' - E)} q_sym(s) /
+// q_sym(s')).  The proposal is the sample s'' or its global flip -s'' (one bit
+// of the chain's MH Philox block), and q_sym, E are flip-invariant.  Accepted
+// proposals are written into the chain's lattice.
+__global__ void k_mh_accept(const IsingChain *chains, char *lattice, const int8_t *prop, const double *lq_p,
+                            const double *lq_pn, const double *lq_s, const double *lq_sn, const long long *E_s,
+                            const long long *E_p, int L, int n, PhiloxKey key, uint32_t round, int *accepted,
+                            double *log_ratio)
+{
+    const int k = blockIdx.x;
+    __shared__ int take, flip;
+    if (threadIdx.x == 0) {
+        const IsingChain &ch = chains[k];
+        const uint4 r = philox4x32_10(make_uint4(0u, round, kTagVanMH, ch.chain_id), key);
+        const double u = (double)((r.x >> 8) + 1u) * (1.0 / 16777216.0);
+        flip = (int)(r.y >> 31);
+        const double lr = -ch.beta * (double)(E_p[k] - E_s[k]) + log_add_exp(lq_s[k], lq_sn[k]) -
+                          log_add_exp(lq_p[k], lq_pn[k]);
+        take = log(u) < lr;
+        if (log_ratio)
+            log_ratio[k] = lr;
+        if (take)
+            atomicAdd(accepted, 1);
+    }
+    __syncthreads();
+    if (!take)
+        return;
+    int8_t *lat = reinterpret_cast<int8_t *>(lattice + chains[k].spin_off);
+    const int8_t *p = prop + (size_t)k * L * L;
+    for (int i = threadIdx.x; i < L * L; i += blockDim.x)
+        lat[i] = flip ? (int8_t)(-p[i]) : p[i];
+}
+
+size_t a256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace van
+}  // namespace mc
+
+using namespace mc;
+using namespace mc::van;
+
+struct mc_van {
+    int L = 0, D = 0, nmax = 0;
+    PhiloxKey key{};
+    uint32_t round = 0;
+    int adam_t = 0;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;
+    ParamLayout P{};
+    DevParams dp{};
+    float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+    bf16 *wh = nullptr;
+    float *w1 = nullptr, *wD = nullptr, *bias = nullptr;
+    bf16 *H = nullptr, *dZa = nullptr, *dZb = nullptr;
+    float *f = nullptr, *ll = nullptr, *dF = nullptr;
+    int8_t *spins = nullptr, *prop = nullptr;
+    double *lq = nullptr, *lq2 = nullptr, *lq3 = nullptr, *lq4 = nullptr, *mh_lr = nullptr;
+    long long *E1 = nullptr, *E2 = nullptr;
+    int *acc = nullptr;
+    bf16 *hist = nullptr;
+    int sms = 0;
+    bool weights_ready = false;
+};
+
+namespace {
+
+mc_status vfail(mc_status s, const std::string &m)
+{
+    mc::set_last_error(m);
+    return s;
+}
+
+struct VanLayout {
+    size_t p, m, v, g, wh, w1, wD, bias, H, dZa, dZb, f, ll, dF, spins, prop, lq, lq2, lq3, lq4, lr, E1, E2, acc, hist,
+        total;
+};
+
+VanLayout van_layout(int L, int nmax, int D)
+{
+    VanLayout o{};
+    const ParamLayout P = param_layout(D);
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t r = off;
+        off = a256(off + std::max<size_t>(b, 1));
+        return r;
+    };
+    const size_t pos = (size_t)nmax * L * L;
+    o.p = take(P.total * 4);
+    o.m = take(P.total * 4);
+    o.v = take(P.total * 4);
+    o.g = take(P.total * 4);
+    o.wh = take((size_t)(D - 2) * kTapsB * kCh * kCh * 2);
+    o.w1 = take((size_t)kCh * kTapsA * 4);
+    o.wD = take((size_t)kTapsB * kCh * 4);
+    o.bias = take((size_t)((D - 1) * kCh + 1) * 4);
+    o.H = take((size_t)(D - 1) * pos * kCh * 2);
+    o.dZa = take(pos * kCh * 2);
+    o.dZb = take(pos * kCh * 2);
+    o.f = take(pos * 4);
+    o.ll = take(pos * 4);
+    o.dF = take(pos * 4);
+    o.spins = take(pos);
+    o.prop = take(pos);
+    o.lq = take((size_t)nmax * 8);
+    o.lq2 = take((size_t)nmax * 8);
+    o.lq3 = take((size_t)nmax * 8);
+    o.lq4 = take((size_t)nmax * 8);
+    o.lr = take((size_t)nmax * 8);
+    o.E1 = take((size_t)nmax * 8);
+    o.E2 = take((size_t)nmax * 8);
+    o.acc = take(64);
+    o.hist = take((size_t)(D - 1) * nmax * 3 * L * kCh * 2);
+    o.total = off;
+    return o;
+}
+
+unsigned grid_for(size_t n, int threads, int sms) { return (unsigned)std::min<size_t>((n + threads - 1) / threads, (size_t)sms * 16); }
+
+size_t conv_smem(int L) { return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)3 * (((L + 15) / 16) * 16 + 4) * kRowStride * 2; }
+size_t dw_smem(int L)
+{
+    const int PZ = ((L + 15) / 16) * 16;
+    return (size_t)PZ * kRowStride * 2 + (size_t)3 * (PZ + 4) * kRowStride * 2;
+}
+size_t sample_smem(int D)
+{
+    return (size_t)(D - 2) * kTapsB * kCh * kRowStride * 2 + (size_t)kSampleTile * kAStride * 2 +
+           (size_t)kSampleTile * kRowStride * 2 + (size_t)(kCh * kTapsA + kTapsB * kCh + (D - 1) * kCh + 1 + 32) * 4;
+}
+
+cudaError_t prep(mc_van *w)
+{
+    k_prep_weights<<<64, 256, 0, w->stream>>>(w->p, w->dp, w->wh, w->w1, w->wD, w->bias);
+    w->weights_ready = true;
+    return cudaGetLastError();
+}
+
+// Forward over n configurations in w->spins (negated when `negate`); log q
+// into `logq`; dF (training) when dF != nullptr.
+cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
+{
+    if (!w->weights_ready) {
+        cudaError_t e = prep(w);
+        if (e != cudaSuccess)
+            return e;
+    }
+    const int L = w->L, D = w->D;
+    const size_t pos = (size_t)n * L * L, layer = (size_t)w->nmax * L * L * kCh;
+    k_layer1_fwd<<<grid_for(pos * kCh, 256, w->sms), 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n,
+                                                                           L);
+    const unsigned cg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 3);
+    for (int l = 1; l <= D - 2; ++l)
+        k_conv32<false><<<cg, 256, conv_smem(L), w->stream>>>(w->H + (l - 1) * layer, w->H + l * layer,
+                                                              w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
+                                                              w->bias + l * kCh, nullptr, n, L);
+    k_layerD_fwd<<<grid_for(pos, 256, w->sms), 256, 0, w->stream>>>(w->H + (D - 2) * layer, w->wD,
+                                                                    w->bias + (D - 1) * kCh, w->spins, negate, w->f,
+                                                                    w->ll, dF, 1.0f / n, n, L);
+    k_logq<<<n, 256, 0, w->stream>>>(w->ll, logq, L);
+    return cudaGetLastError();
+}
+
+cudaError_t backward(mc_van *w, int n)
+{
+    const int L = w->L, D = w->D;
+    const size_t pos = (size_t)n * L * L, layer = (size_t)w->nmax * L * L * kCh;
+    cudaError_t e = cudaMemsetAsync(w->g, 0, w->P.total * 4, w->stream);
+    if (e != cudaSuccess)
+        return e;
+    const bf16 *hD = w->H + (D - 2) * layer;
+    k_layerD_bwd_data<<<grid_for(pos * kCh, 256, w->sms), 256, 0, w->stream>>>(w->dF, w->wD, hD, w->dZa, n, L);
+    const unsigned rg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 4);
+    k_layerD_bwd_w<<<rg, kTapsB * kCh + 1, 0, w->stream>>>(w->dF, hD, w->g, w->dp, n, L);
+    bf16 *dz = w->dZa, *dzn = w->dZb;
+    const unsigned cg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 3);
+    for (int l = D - 2; l >= 1; --l) { // hidden layer l: input H[l-1], output H[l], grad dz wrt its pre-activation
+        k_dw32<<<cg, 256, dw_smem(L), w->stream>>>(dz, w->H + (l - 1) * layer, w->g, w->dp, l, n, L);
+        k_conv32<true><<<cg, 256, conv_smem(L), w->stream>>>(dz, dzn, w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
+                                                             nullptr, w->H + (l - 1) * layer, n, L);
+        std::swap(dz, dzn);
+    }
+    k_layer1_bwd_w<<<rg, kCh * (kTapsA + 1), 0, w->stream>>>(dz, w->spins, w->g, w->dp, n, L);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mc_van_param_count(int32_t depth)
+{
+    if (depth < 3 || depth > kMaxDepth)
+        return 0;
+    return param_layout(depth).total;
+}
+
+size_t mc_van_workspace_bytes(int32_t L, int32_t batch, int32_t depth)
+{
+    if (L < 2 || L > kMaxL || (L & 1) || batch < 1 || depth < 3 || depth > kMaxDepth) {
+        mc::set_last_error("mc_van_workspace_bytes: need even L in [2, 128], batch >= 1, depth in [3, 7]");
+        return 0;
+    }
+    return van_layout(L, batch, depth).total;
+}
+
+mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, uint64_t seed, void *workspace,
+                        size_t bytes, void *cuda_stream)
+{
+    if (!out)
+        return vfail(MC_EINVAL, "out is NULL");
+    *out = nullptr;
+    const size_t need = mc_van_workspace_bytes(L, batch, depth);
+    if (need == 0)
+        return MC_EINVAL;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+        return vfail(MC_EINVAL, "workspace must be a device pointer aligned to 256 bytes");
+    if (bytes < need)
+        return vfail(MC_ENOMEM, "van workspace too small: need " + std::to_string(need) + " bytes");
+    mc_van *w = new (std::nothrow) mc_van();
+    if (!w)
+        return vfail(MC_ENOMEM, "host allocation failed");
+    w->L = L;
+    w->D = depth;
+    w->nmax = batch;
+    w->key = PhiloxKey{(uint32_t)seed, (uint32_t)(seed >> 32)};
+    w->stream = static_cast<cudaStream_t>(cuda_stream);
+    w->ws = static_cast<char *>(workspace);
+    w->P = param_layout(depth);
+    w->dp.D = depth;
+    for (int l = 0; l < depth; ++l) {
+        w->dp.w_off[l] = w->P.w_off[l];
+        w->dp.b_off[l] = w->P.b_off[l];
+    }
+    const VanLayout o = van_layout(L, batch, depth);
+    char *b = w->ws;
+    w->p = reinterpret_cast<float *>(b + o.p);
+    w->m = reinterpret_cast<float *>(b + o.m);
+    w->v = reinterpret_cast<float *>(b + o.v);
+    w->g = reinterpret_cast<float *>(b + o.g);
+    w->wh = reinterpret_cast<bf16 *>(b + o.wh);
+    w->w1 = reinterpret_cast<float *>(b + o.w1);
+    w->wD = reinterpret_cast<float *>(b + o.wD);
+    w->bias = reinterpret_cast<float *>(b + o.bias);
+    w->H = reinterpret_cast<bf16 *>(b + o.H);
+    w->dZa = reinterpret_cast<bf16 *>(b + o.dZa);
+    w->dZb = reinterpret_cast<bf16 *>(b + o.dZb);
+    w->f = reinterpret_cast<float *>(b + o.f);
+    w->ll = reinterpret_cast<float *>(b + o.ll);
+    w->dF = reinterpret_cast<float *>(b + o.dF);
+    w->spins = reinterpret_cast<int8_t *>(b + o.spins);
+    w->prop = reinterpret_cast<int8_t *>(b + o.prop);
+    w->lq = reinterpret_cast<double *>(b + o.lq);
+    w->lq2 = reinterpret_cast<double *>(b + o.lq2);
+    w->lq3 = reinterpret_cast<double *>(b + o.lq3);
+    w->lq4 = reinterpret_cast<double *>(b + o.lq4);
+    w->mh_lr = reinterpret_cast<double *>(b + o.lr);
+    w->E1 = reinterpret_cast<long long *>(b + o.E1);
+    w->E2 = reinterpret_cast<long long *>(b + o.E2);
+    w->acc = reinterpret_cast<int *>(b + o.acc);
+    w->hist = reinterpret_cast<bf16 *>(b + o.hist);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemsetAsync(w->ws, 0, o.hist, w->stream); // params, Adam state, buffers
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(L));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(L));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dw32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(L));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sample_smem(depth));
+    if (e != cudaSuccess) {
+        delete w;
+        return vfail(MC_ECUDA, std::string("mc_van_create: ") + cudaGetErrorString(e));
+    }
+    *out = w;
+    return MC_OK;
+}
+
+mc_status mc_van_set_params(mc_van *w, const float *host_params, size_t n)
+{
+    if (!w || !host_params || n != w->P.total)
+        return vfail(MC_EINVAL, "mc_van_set_params: need mc_van_param_count(depth) floats");
+    cudaError_t e = cudaMemcpyAsync(w->p, host_params, n * 4, cudaMemcpyHostToDevice, w->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(w->m, 0, n * 4, w->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(w->v, 0, n * 4, w->stream);
+    if (e == cudaSuccess)
+        e = prep(w);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(w->stream);
+    w->adam_t = 0;
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string("mc_van_set_params: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+mc_status mc_van_get_params(mc_van *w, float *host_params, size_t n, float *host_grads)
+{
+    if (!w || !host_params || n != w->P.total)
+        return vfail(MC_EINVAL, "mc_van_get_params: need mc_van_param_count(depth) floats");
+    cudaError_t e = cudaMemcpyAsync(host_params, w->p, n * 4, cudaMemcpyDeviceToHost, w->stream);
+    if (e == cudaSuccess && host_grads)
+        e = cudaMemcpyAsync(host_grads, w->g, n * 4, cudaMemcpyDeviceToHost, w->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string("mc_van_get_params: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+mc_status mc_van_log_prob(mc_van *w, const int8_t *dev_spins, int32_t n, int32_t negate, double *dev_logq)
+{
+    if (!w || !dev_spins || !dev_logq || n < 1 || n > w->nmax)
+        return vfail(MC_EINVAL, "mc_van_log_prob: bad argument (1 <= n <= batch)");
+    cudaError_t e = cudaMemcpyAsync(w->spins, dev_spins, (size_t)n * w->L * w->L, cudaMemcpyDeviceToDevice, w->stream);
+    if (e == cudaSuccess)
+        e = forward(w, n, negate, dev_logq, nullptr);
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string("mc_van_log_prob: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+mc_status mc_van_train_step(mc_van *w, const int8_t *dev_spins, int32_t n, float lr, int32_t apply, double *host_loss)
+{
+    if (!w || !dev_spins || n < 1 || n > w->nmax)
+        return vfail(MC_EINVAL, "mc_van_train_step: bad argument (1 <= n <= batch)");
+    cudaError_t e = cudaMemcpyAsync(w->spins, dev_spins, (size_t)n * w->L * w->L, cudaMemcpyDeviceToDevice, w->stream);
+    if (e == cudaSuccess)
+        e = forward(w, n, 0, w->lq, w->dF);
+    if (e == cudaSuccess)
+        e = backward(w, n);
+    if (e == cudaSuccess && apply) {
+        ++w->adam_t;
+        const float b1 = 0.9f, b2 = 0.999f;
+        k_adam<<<grid_for(w->P.total, 256, w->sms), 256, 0, w->stream>>>(
+            w->p, w->m, w->v, w->g, w->P.total, lr, b1, b2, 1e-8f, 1.f - powf(b1, (float)w->adam_t),
+            1.f - powf(b2, (float)w->adam_t));
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = prep(w);
+    }
+    if (e == cudaSuccess && host_loss) {
+        std::vector<double> lq(n);
+        e = cudaMemcpyAsync(lq.data(), w->lq, (size_t)n * 8, cudaMemcpyDeviceToHost, w->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(w->stream);
+        double s = 0.0;
+        for (double v : lq)
+            s += v;
+        *host_loss = -s / n;
+    }
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string("mc_van_train_step: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+mc_status mc_van_sample(mc_van *w, int32_t n, uint32_t round, const uint32_t *dev_ids, int8_t *dev_out,
+                        double *dev_logq)
+{
+    if (!w || n < 1 || n > w->nmax)
+        return vfail(MC_EINVAL, "mc_van_sample: 1 <= n <= batch");
+    if (!w->weights_ready) {
+        cudaError_t e = prep(w);
+        if (e != cudaSuccess)
+            return vfail(MC_ECUDA, cudaGetErrorString(e));
+    }
+    int8_t *out = dev_out ? dev_out : w->prop;
+    double *lq = dev_logq ? dev_logq : w->lq;
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n * w->L * w->L, w->stream);
+    if (e == cudaSuccess) {
+        const unsigned blocks = (unsigned)((n + kSampleTile - 1) / kSampleTile);
+        k_sample<<<blocks, 256, sample_smem(w->D), w->stream>>>(w->wh, w->w1, w->wD, w->bias, w->D, w->L, n, w->hist,
+                                                                out, lq, w->key, round, dev_ids);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string("mc_van_sample: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+mc_status mc_ising_gather(mc_ctx *c, int8_t *dev_out, int32_t back)
+{
+    if (!c || !dev_out || c->kind != MC_KIND_ISING || c->layout != MC_LAYOUT_INT8)
+        return vfail(MC_EINVAL, "mc_ising_gather: needs an int8-layout Ising context");
+    const int L = (int)c->ising[0].Lx;
+    for (const auto &ch : c->ising)
+        if ((int)ch.Lx != L || (int)ch.Ly != L)
+            return vfail(MC_EINVAL, "mc_ising_gather: every chain must be L x L with the same L");
+    const size_t total = (size_t)c->n_chains * L * L;
+    k_gather<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, c->stream>>>(
+        static_cast<const IsingChain *>(c->d_chains), c->d_lattice, dev_out, L, c->n_chains, back);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string("mc_ising_gather: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+mc_status mc_van_mh_round(mc_van *w, mc_ctx *c, int32_t *host_accepted)
+{
+    if (!w || !c || c->kind != MC_KIND_ISING || c->layout != MC_LAYOUT_INT8)
+        return vfail(MC_EINVAL, "mc_van_mh_round: needs an int8-layout Ising context");
+    const int n = c->n_chains, L = w->L;
+    if (n > w->nmax)
+        return vfail(MC_EINVAL, "mc_van_mh_round: more chains than the network's batch");
+    for (const auto &ch : c->ising)
+        if ((int)ch.Lx != L || (int)ch.Ly != L)
+            return vfail(MC_EINVAL, "mc_van_mh_round: every chain must be L x L with the network's L");
+    if (c->stream != w->stream)
+        return vfail(MC_EINVAL, "mc_van_mh_round: context and network must share a stream");
+    // ids for the sampler: the chains' own Philox chain ids
+    static_assert(sizeof(IsingChain) % 4 == 0, "chain layout");
+    const uint32_t round = w->round++;
+    mc_status s = mc_van_sample(w, n, round, nullptr, w->prop, w->lq); // q(s'')
+    if (s != MC_OK)
+        return s;
+    cudaError_t e = cudaMemcpyAsync(w->spins, w->prop, (size_t)n * L * L, cudaMemcpyDeviceToDevice, w->stream);
+    if (e == cudaSuccess)
+        e = forward(w, n, 1, w->lq2, nullptr); // q(-s'')
+    if (e == cudaSuccess)
+        k_energy<<<n, 256, 0, w->stream>>>(w->prop, w->E2, L);
+    if (e == cudaSuccess && mc_ising_gather(c, w->spins, 0) != MC_OK)
+        return MC_ECUDA;
+    if (e == cudaSuccess)
+        e = forward(w, n, 0, w->lq3, nullptr); // q(s)
+    if (e == cudaSuccess)
+        e = forward(w, n, 1, w->lq4, nullptr); // q(-s)
+    if (e == cudaSuccess)
+        k_energy<<<n, 256, 0, w->stream>>>(w->spins, w->E1, L);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(w->acc, 0, 4, w->stream);
+    if (e == cudaSuccess)
+        k_mh_accept<<<n, 256, 0, w->stream>>>(static_cast<const IsingChain *>(c->d_chains), c->d_lattice, w->prop,
+                                              w->lq, w->lq2, w->lq3, w->lq4, w->E1, w->E2, L, n, w->key, round, w->acc,
+                                              w->mh_lr);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    if (e == cudaSuccess && host_accepted) {
+        e = cudaMemcpyAsync(host_accepted, w->acc, 4, cudaMemcpyDeviceToHost, w->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(w->stream);
+    }
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string("mc_van_mh_round: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+mc_status mc_van_set_round(mc_van *w, uint32_t round)
+{
+    if (!w)
+        return vfail(MC_EINVAL, "NULL network");
+    w->round = round;
+    return MC_OK;
+}
+
+mc_status mc_van_destroy(mc_van *w)
+{
+    if (!w)
+        return MC_OK;
+    cudaError_t e = cudaStreamSynchronize(w->stream);
+    delete w;
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string("mc_van_destroy: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
+}  // extern "C"

@@ -367,3 +367,144 @@ class Group:
             self.close()
         except Exception:
             pass
+
+
+def _van_sigs(L):
+    c, P = ctypes, ctypes.c_void_p
+    st = c.c_int
+    return {
+        "mc_van_param_count": (c.c_size_t, [c.c_int32]),
+        "mc_van_workspace_bytes": (c.c_size_t, [c.c_int32, c.c_int32, c.c_int32]),
+        "mc_van_create": (st, [P, c.c_int32, c.c_int32, c.c_int32, c.c_uint64, P, c.c_size_t, P]),
+        "mc_van_set_params": (st, [P, P, c.c_size_t]),
+        "mc_van_get_params": (st, [P, P, c.c_size_t, P]),
+        "mc_van_log_prob": (st, [P, P, c.c_int32, c.c_int32, P]),
+        "mc_van_train_step": (st, [P, P, c.c_int32, c.c_float, c.c_int32, P]),
+        "mc_van_sample": (st, [P, c.c_int32, c.c_uint32, P, P, P]),
+        "mc_van_mh_round": (st, [P, P, P]),
+        "mc_van_set_round": (st, [P, c.c_uint32]),
+        "mc_van_destroy": (st, [P]),
+        "mc_ising_gather": (st, [P, P, c.c_int32]),
+    }
+
+
+VAN_EXPORTS = list(_van_sigs(None))
+EXPORTS += VAN_EXPORTS
+
+
+def _load_van():
+    L = load()
+    if not getattr(L, "_van_ready", False):
+        for name, (res, args) in _van_sigs(None).items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        L._van_ready = True
+    return L
+
+
+def van_param_count(depth: int = 6) -> int:
+    return int(_load_van().mc_van_param_count(depth))
+
+
+def van_pack(params) -> np.ndarray:
+    """[(W[out][in][5][5], b[out]), ...] -> the flat FP32 order of the ABI."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32).ravel()])
+                           for W, b in params]).astype(np.float32)
+
+
+def van_unpack(flat: np.ndarray, depth: int = 6, channels: int = 32):
+    out, off = [], 0
+    for l in range(depth):
+        cin = 1 if l == 0 else channels
+        cout = 1 if l == depth - 1 else channels
+        n = cout * cin * 25
+        W = flat[off:off + n].reshape(cout, cin, 5, 5)
+        off += n
+        b = flat[off:off + cout]
+        off += cout
+        out.append((W, b))
+    return out
+
+
+class VAN:
+    """The learned proposal network (see include/mc.h)."""
+
+    def __init__(self, L: int, batch: int, depth: int = 6, seed: int = 0, stream=None):
+        torch = _torch()
+        lib = _load_van()
+        self.L, self.batch, self.depth = int(L), int(batch), int(depth)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        nbytes = lib.mc_van_workspace_bytes(self.L, self.batch, self.depth)
+        if nbytes == 0:
+            raise MCError(MC_EINVAL, lib.mc_last_error().decode())
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        self._w = ctypes.c_void_p()
+        _check(lib.mc_van_create(ctypes.byref(self._w), self.L, self.batch, self.depth, int(seed) & (2**64 - 1),
+                                 ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                 ctypes.c_void_p(self.stream.cuda_stream)))
+        self.n_params = van_param_count(self.depth)
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(_load_van().mc_van_set_params(self._w, ctypes.c_void_p(a.ctypes.data), a.size))
+
+    def get_params(self, grads: bool = False):
+        p = np.zeros(self.n_params, np.float32)
+        g = np.zeros(self.n_params, np.float32) if grads else None
+        _check(_load_van().mc_van_get_params(self._w, ctypes.c_void_p(p.ctypes.data), p.size,
+                                             ctypes.c_void_p(g.ctypes.data) if grads else None))
+        return (p, g) if grads else p
+
+    def log_prob(self, spins, negate: bool = False):
+        import torch
+        out = torch.empty(spins.shape[0], dtype=torch.float64, device="cuda")
+        _check(_load_van().mc_van_log_prob(self._w, ctypes.c_void_p(spins.data_ptr()), int(spins.shape[0]),
+                                           int(bool(negate)), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def train_step(self, spins, lr: float = 1e-3, apply: bool = True) -> float:
+        loss = ctypes.c_double()
+        _check(_load_van().mc_van_train_step(self._w, ctypes.c_void_p(spins.data_ptr()), int(spins.shape[0]),
+                                             float(lr), int(bool(apply)), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def sample(self, n: int, round: int = 0, ids=None):
+        import torch
+        out = torch.empty((n, self.L, self.L), dtype=torch.int8, device="cuda")
+        lq = torch.empty(n, dtype=torch.float64, device="cuda")
+        _check(_load_van().mc_van_sample(self._w, int(n), int(round) & 0xFFFFFFFF,
+                                         ctypes.c_void_p(ids.data_ptr()) if ids is not None else None,
+                                         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(lq.data_ptr())))
+        return out, lq
+
+    def mh_round(self, batch: "Batch") -> int:
+        acc = ctypes.c_int32()
+        _check(_load_van().mc_van_mh_round(self._w, batch._ctx, ctypes.byref(acc)))
+        return int(acc.value)
+
+    def set_round(self, r: int):
+        _check(_load_van().mc_van_set_round(self._w, int(r) & 0xFFFFFFFF))
+
+    def close(self):
+        if self._w:
+            st = _load_van().mc_van_destroy(self._w)
+            self._w = ctypes.c_void_p()
+            _check(st)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ising_gather(batch: "Batch", out=None, back: bool = False):
+    """All chains of an int8-layout Ising Batch as one [n][L][L] int8 CUDA tensor
+    (or write `out` back into the chains when back=True)."""
+    import torch
+    if out is None:
+        c = batch.chains[0]
+        out = torch.empty((len(batch.chains), c.L[1], c.L[0]), dtype=torch.int8, device="cuda")
+    _check(_load_van().mc_ising_gather(batch._ctx, ctypes.c_void_p(out.data_ptr()), int(bool(back))))
+    return out

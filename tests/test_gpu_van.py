@@ -1,0 +1,183 @@
+"""GPU parity of the learned proposal (BF16 tensor-core network, FP64 log q)
+against the FP64 oracle (oracle/van.py), and exactness of its
+Metropolis-Hastings correction against the Boltzmann distribution of Eq. (1).
+
+Tolerances: weights are given in BF16-representable values on both sides, so
+the GPU differs from FP64 only by BF16 rounding of activations (8-bit
+mantissa, relative 2^-9 per layer) and FP32 accumulation; log q and gradients
+are compared at the 1e-2 relative level (per-tensor relative error, cosine >
+0.999 for gradients).  Normalisation (sum_s q(s) = 1) is structural and holds
+to FP32 rounding."""
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+import oracle
+import paper_0903_3053_gb300 as mc
+from oracle import exact, van
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_params(depth=6, channels=32, seed=0, scale=1.0, bias=0.0):
+    p = van.masked(van.init_params(depth, channels, seed=seed, scale=scale))
+    rng = np.random.default_rng(seed + 100)
+    out = []
+    for W, b in p:
+        Wb = torch.from_numpy(W).to(torch.bfloat16).to(torch.float64).numpy()
+        bb = torch.from_numpy(b + bias * rng.normal(size=b.shape)).to(torch.bfloat16).to(torch.float64).numpy()
+        out.append((Wb, bb))
+    return out
+
+
+def all_states(Lx, Ly):
+    idx = np.arange(1 << (Lx * Ly))
+    return (((idx[:, None] >> np.arange(Lx * Ly)) & 1) * 2 - 1).reshape(-1, Ly, Lx).astype(np.int8)
+
+
+def test_log_prob_matches_oracle():
+    L, n = 8, 32
+    p = bf16_params(seed=1, bias=0.3)
+    net = mc.VAN(L, batch=n, depth=6, seed=0)
+    net.set_params(mc.mc.van_pack(p))
+    rng = np.random.default_rng(2)
+    s = np.where(rng.random((n, L, L)) < 0.5, 1, -1).astype(np.int8)
+    g = net.log_prob(torch.from_numpy(s).cuda()).cpu().numpy()
+    o = van.log_prob(p, s.astype(np.float64))
+    assert np.max(np.abs(g - o) / np.abs(o)) < 1e-2, (g[:4], o[:4])
+    gn = net.log_prob(torch.from_numpy(s).cuda(), negate=True).cpu().numpy()
+    on = van.log_prob(p, -s.astype(np.float64))
+    assert np.max(np.abs(gn - on) / np.abs(on)) < 1e-2
+
+
+def test_normalisation_4x4():
+    """sum over all 2^16 states of q(s) = 1 (autoregressive structure)."""
+    p = bf16_params(depth=6, seed=3, scale=1.5, bias=0.5)
+    s = all_states(4, 4)
+    net = mc.VAN(4, batch=len(s), depth=6, seed=0)
+    net.set_params(mc.mc.van_pack(p))
+    lq = net.log_prob(torch.from_numpy(s).cuda()).cpu().numpy()
+    assert abs(np.exp(lq).sum() - 1.0) < 1e-4
+
+
+def test_gradients_match_oracle():
+    L, n = 8, 16
+    p = bf16_params(seed=4, bias=0.2)
+    net = mc.VAN(L, batch=n, depth=6, seed=0)
+    net.set_params(mc.mc.van_pack(p))
+    rng = np.random.default_rng(5)
+    s = np.where(rng.random((n, L, L)) < 0.5, 1, -1).astype(np.int8)
+    loss_g = net.train_step(torch.from_numpy(s).cuda(), lr=0.0, apply=False)
+    _, gflat = net.get_params(grads=True)
+    loss_o, go = van.loss_and_grad(p, s.astype(np.float64))
+    assert abs(loss_g - loss_o) / abs(loss_o) < 1e-2
+    gg = mc.mc.van_unpack(gflat)
+    for l, ((gW, gb), (oW, ob)) in enumerate(zip(gg, go)):  # taps outside the masks are 0 on both sides
+        a = np.concatenate([gW.ravel(), gb.ravel()])
+        b = np.concatenate([oW.ravel(), ob.ravel()])
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert cos > 0.999 and rel < 1e-2, (l, cos, rel)
+
+
+def test_sampler_follows_q():
+    """Samples on a 4x4 lattice follow the network's own q (chi^2 over all
+    states), and the sampler's log q equals a batched forward of its samples."""
+    p = bf16_params(depth=4, seed=6, scale=1.5, bias=0.5)
+    n = 8192
+    net = mc.VAN(4, batch=65536, depth=4, seed=7)
+    net.set_params(mc.mc.van_pack(p))
+    samp, lq = net.sample(n, round=0)
+    lq_fwd = net.log_prob(samp).cpu().numpy()
+    assert np.max(np.abs(lq.cpu().numpy() - lq_fwd)) < 1e-3
+    s = samp.cpu().numpy().reshape(n, -1)
+    code = ((s > 0).astype(np.int64) << np.arange(16)).sum(axis=1)
+    q = np.exp(net.log_prob(torch.from_numpy(all_states(4, 4)).cuda()).cpu().numpy())
+    counts = np.bincount(code, minlength=1 << 16)
+    e = q * n
+    big = e >= 5
+    obs = np.append(counts[big], counts[~big].sum())
+    ex = np.append(e[big], e[~big].sum())
+    chi2 = ((obs - ex) ** 2 / ex).sum()
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-4
+
+
+def test_sampler_matches_oracle_sampler_statistics():
+    """The same network sampled by the oracle (FP64) and by the GPU: the mean
+    magnetisation and energy agree within their statistical errors."""
+    L = 6
+    p = bf16_params(depth=6, seed=8, scale=1.2, bias=0.4)
+    net = mc.VAN(L, batch=4096, depth=6, seed=9)
+    net.set_params(mc.mc.van_pack(p))
+    g = net.sample(4096, round=3)[0].cpu().numpy().astype(np.float64)
+    o = van.sample(p, 2000, L, np.random.default_rng(10).random((2000, L * L)))
+    for f in (lambda s: s.mean(axis=(1, 2)), lambda s: van.ising_energy(s) / L ** 2):
+        a, b = f(g), f(o)
+        err = np.hypot(a.std() / np.sqrt(len(a)), b.std() / np.sqrt(len(b)))
+        assert abs(a.mean() - b.mean()) < 4.5 * err
+
+
+def test_mh_round_keeps_boltzmann_distribution():
+    """Chains of a 4x4 torus started in the exact Boltzmann distribution stay in
+    it under MH rounds with a deliberately poor network (exactness does not
+    depend on training)."""
+    beta, L, n = 0.4406868, 4, 4096
+    en = exact.ising_enumerate(L, L, beta)
+    chains = [mc.ising(L, beta, seed=3, chain_id=k) for k in range(n)]
+    b = mc.Batch(chains, layout=mc.MC_LAYOUT_INT8)
+    rng = np.random.default_rng(11)
+    code = rng.choice(len(en["p"]), size=n, p=en["p"])
+    start = (((code[:, None] >> np.arange(L * L)) & 1) * 2 - 1).reshape(n, L, L).astype(np.int8)
+    mc.mc.ising_gather(b, torch.from_numpy(start).cuda(), back=True)
+    net = mc.VAN(L, batch=n, depth=4, seed=12)
+    net.set_params(mc.mc.van_pack(bf16_params(depth=4, seed=13, scale=2.0, bias=0.5)))
+    acc = 0
+    for _ in range(6):
+        acc += net.mh_round(b)
+    assert 0 < acc < 6 * n  # some accepted, some rejected
+    s = mc.mc.ising_gather(b).cpu().numpy().reshape(n, -1)
+    got = ((s > 0).astype(np.int64) << np.arange(L * L)).sum(axis=1)
+    classes = {}
+    for E, M, pr in zip(en["E_states"], en["M_states"], en["p"]):
+        classes[(int(E), int(M))] = classes.get((int(E), int(M)), 0.0) + pr
+    keys = sorted(classes)
+    idx = {k: i for i, k in enumerate(keys)}
+    counts = np.zeros(len(keys))
+    for c in got:
+        counts[idx[(int(en["E_states"][c]), int(en["M_states"][c]))]] += 1
+    e = np.array([classes[k] for k in keys]) * n
+    big = e >= 5
+    obs = np.append(counts[big], counts[~big].sum()) if (~big).any() else counts[big]
+    ex = np.append(e[big], e[~big].sum()) if (~big).any() else e[big]
+    chi2 = ((obs - ex) ** 2 / ex).sum()
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-4
+
+
+def test_training_lowers_loss_and_raises_acceptance():
+    """Maximum-likelihood training on Metropolis configurations (8x8, beta_c)
+    lowers -mean log q and raises the MH acceptance over the untrained network:
+    what the network gains over the method without it."""
+    beta, L = 0.4406868, 8
+    nchain = 2048
+    chains = [mc.ising(L, beta, seed=21, chain_id=k) for k in range(nchain)]
+    b = mc.Batch(chains, layout=mc.MC_LAYOUT_INT8)
+    b.sweep(200)
+    data = [mc.mc.ising_gather(b).clone()]
+    for _ in range(7):
+        b.sweep(20)
+        data.append(mc.mc.ising_gather(b).clone())
+    data = torch.cat(data)
+    net = mc.VAN(L, batch=nchain, depth=6, seed=22)
+    net.set_params(mc.mc.van_pack(van.masked(van.init_params(6, 32, seed=23, scale=0.5))))
+    acc0 = net.mh_round(b)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    first = last = None
+    for step in range(300):
+        idx = torch.randint(0, data.shape[0], (512,), device="cuda", generator=gen)
+        loss = net.train_step(data[idx].contiguous(), lr=2e-3)
+        first = loss if first is None else first
+        last = loss
+    assert last < first - 1.0, (first, last)
+    acc1 = sum(net.mh_round(b) for _ in range(3)) / 3
+    assert acc1 > 2 * max(acc0, 1), (acc0, acc1)

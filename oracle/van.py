@@ -16,6 +16,12 @@ not compatible with periodic padding):
 p(s_k = +1 | s_<k) = sigmoid(f_k); log q(s) = sum_k log sigmoid(s_k f_k).
 Parameters are (W, b) per layer with W[c_out, c_in, 5, 5] (masked taps unused).
 Convolution is correlation: out[y, x] = sum_{dy,dx} W[., ., dy+2, dx+2] in[y+dy, x+dx].
+
+Precision: FP64 throughout by default.  The task fixes BF16 weights and
+activations for this network; with ``act="bf16"`` every stored activation
+(the output of each ReLU) is rounded to BF16 (round to nearest, ties to even),
+so the oracle computes the same function as a BF16 implementation -- all
+arithmetic stays FP64.
 """
 from __future__ import annotations
 
@@ -45,6 +51,16 @@ def shift(x: np.ndarray, dy: int, dx: int) -> np.ndarray:
     return out
 
 
+def round_bf16(x) -> np.ndarray:
+    """Round to the nearest BF16 value (8-bit significand), ties to even, via
+    the FP32 bit pattern: add 0x7FFF plus the lowest kept bit, clear the low
+    16 bits."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def init_params(depth: int = 6, channels: int = 32, seed: int = 0, scale: float = 1.0):
     rng = np.random.default_rng(seed)
     params = []
@@ -70,9 +86,10 @@ def masked(params):
     return out
 
 
-def forward(params, s: np.ndarray):
+def forward(params, s: np.ndarray, act: str = "fp64"):
     """s: (B, L, L) of +-1.  Returns logits f (B, L, L) and the per-layer cache
-    [(input, pre-activation)] for the backward pass."""
+    [(input, pre-activation)] for the backward pass; act="bf16" rounds each
+    ReLU output to BF16."""
     x = s[:, None, :, :].astype(np.float64)
     cache = []
     D = len(params)
@@ -85,6 +102,8 @@ def forward(params, s: np.ndarray):
         z += b[None, :, None, None]
         cache.append((x, z))
         x = np.maximum(z, 0.0) if l < D - 1 else z
+        if act == "bf16" and l < D - 1:
+            x = round_bf16(x)
     return x[:, 0], cache
 
 
@@ -92,9 +111,9 @@ def log_sigmoid(t):
     return -np.logaddexp(0.0, -t)
 
 
-def log_prob(params, s: np.ndarray) -> np.ndarray:
+def log_prob(params, s: np.ndarray, act: str = "fp64") -> np.ndarray:
     """log q(s) per configuration (FP64 accumulation)."""
-    f, _ = forward(params, s)
+    f, _ = forward(params, s, act)
     return log_sigmoid(s * f).reshape(len(s), -1).sum(axis=1)
 
 
@@ -104,10 +123,12 @@ def log_prob_sym(params, s: np.ndarray) -> np.ndarray:
     return np.logaddexp(log_prob(params, s), log_prob(params, -s)) - np.log(2.0)
 
 
-def loss_and_grad(params, s: np.ndarray):
-    """Negative mean log-likelihood -mean_b log q(s_b) and its gradient."""
+def loss_and_grad(params, s: np.ndarray, act: str = "fp64"):
+    """Negative mean log-likelihood -mean_b log q(s_b) and its gradient (of
+    the network with act-rounded activations, the rounding treated as part of
+    the function as a BF16 implementation does)."""
     B = len(s)
-    f, cache = forward(params, s)
+    f, cache = forward(params, s, act)
     loss = -log_sigmoid(s * f).reshape(B, -1).sum(axis=1).mean()
     # d loss / d f = -(1/B) s sigmoid(-s f)
     g = -(s * (1.0 / (1.0 + np.exp(s * f)))) / B

@@ -103,38 +103,31 @@ __global__ void k_layer1_fwd(const int8_t *spins, int negate, const float *w1, c
     }
 }
 
-// 32 -> 32 masked convolution on the tensor cores.  One CTA row item (sample b,
-// row y) at a time; warp w computes positions 16 w .. 16 w + 15 for all 32
-// output channels: K = 13 taps x 32 input channels in 26 k16 steps.
-//   forward  (BWD = false): out = ReLU(conv(in) + bias), taps at (dy, dx).
-//   backward (BWD = true) : out = conv^T(in) * [mask_src > 0], the gradient
-//     with respect to the layer input, masked by the previous layer's ReLU:
-//     taps at (-dy, -dx) and transposed weights.
-template <bool BWD>
+// 32 -> 32 masked convolution on the tensor cores (forward): out =
+// ReLU(conv(in) + bias).  One CTA row item (sample b, row y) at a time; warp w
+// computes positions 16 w .. 16 w + 15 for all 32 output channels: K = 13 taps
+// x 32 input channels in 26 k16 steps.
 __global__ void __launch_bounds__(256) k_conv32(const bf16 *__restrict__ in, bf16 *__restrict__ out,
-                                                const bf16 *__restrict__ W, const float *__restrict__ bias,
-                                                const bf16 *__restrict__ mask_src, int n, int L)
+                                                const bf16 *__restrict__ W, const float *__restrict__ bias, int n,
+                                                int L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    bf16 *Ws = reinterpret_cast<bf16 *>(smem);      // [13][32][40]
+    bf16 *Ws = reinterpret_cast<bf16 *>(smem);      // [13][32 o][40]
     bf16 *Xs = Ws + kTapsB * kCh * kRowStride;       // [3][PX][40]
     const int NW = (L + 15) / 16, PX = NW * 16 + 4;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kTapsB * kCh * kCh; i += blockDim.x) {
         const int t = i / (kCh * kCh), r = (i / kCh) % kCh, q = i % kCh; // W[t][o = r][c = q]
-        if (!BWD)
-            Ws[(t * kCh + r) * kRowStride + q] = W[i];
-        else
-            Ws[(t * kCh + q) * kRowStride + r] = W[i];
+        Ws[(t * kCh + r) * kRowStride + q] = W[i];
     }
     for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
         const int b = item / L, y = item % L;
         __syncthreads(); // weights ready / previous item's reads done
         for (int i = tid; i < 3 * PX * 4; i += blockDim.x) {
             const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
-            const int yy = BWD ? y + r : y - 2 + r, xx = xi - 2;
+            const int yy = y - 2 + r, xx = xi - 2;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (yy >= 0 && yy < L && xx >= 0 && xx < L)
+            if (yy >= 0 && xx >= 0 && xx < L)
                 v = *reinterpret_cast<const uint4 *>(in + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8);
             *reinterpret_cast<uint4 *>(Xs + (r * PX + xi) * kRowStride + ch * 8) = v;
         }
@@ -149,8 +142,7 @@ __global__ void __launch_bounds__(256) k_conv32(const bf16 *__restrict__ in, bf1
             const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
 #pragma unroll 1
             for (int t = 0; t < kTapsB; ++t) {
-                const int dy = tap_dy(t), dx = tap_dx(t);
-                const int r = BWD ? -dy : dy + 2, xoff = BWD ? -dx : dx;
+                const int r = tap_dy(t) + 2, xoff = tap_dx(t);
 #pragma unroll
                 for (int kc = 0; kc < 2; ++kc) {
                     uint32_t a0, a1, a2, a3;
@@ -176,16 +168,111 @@ __global__ void __launch_bounds__(256) k_conv32(const bf16 *__restrict__ in, bf1
                         continue;
                     const int c = 8 * j + 2 * t4;
                     const size_t o = (((size_t)b * L + y) * L + x) * kCh + c;
-                    float v0 = acc[j][2 * h], v1 = acc[j][2 * h + 1];
-                    if (!BWD) {
-                        v0 = fmaxf(v0 + bias[c], 0.f);
-                        v1 = fmaxf(v1 + bias[c + 1], 0.f);
-                    } else {
-                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(mask_src + o);
-                        v0 = bf(m.x) > 0.f ? v0 : 0.f;
-                        v1 = bf(m.y) > 0.f ? v1 : 0.f;
+                    *reinterpret_cast<__nv_bfloat162 *>(out + o) = __floats2bfloat162_rn(
+                        fmaxf(acc[j][2 * h] + bias[c], 0.f), fmaxf(acc[j][2 * h + 1] + bias[c + 1], 0.f));
+                }
+        }
+    }
+}
+
+// Split an FP32 value into BF16 hi + lo (hi + lo carries ~16 mantissa bits).
+__device__ __forceinline__ void split_bf16(float v, bf16 &hi, bf16 &lo)
+{
+    hi = __float2bfloat16(v);
+    lo = __float2bfloat16(v - bf(hi));
+}
+
+// Stage FP32 rows into two BF16 tiles (hi, lo): 8 values per call.
+__device__ __forceinline__ void stage_split(const float *src, bool valid, bf16 *hi, bf16 *lo)
+{
+    float v[8];
+    if (valid) {
+        const float4 p = *reinterpret_cast<const float4 *>(src), q = *reinterpret_cast<const float4 *>(src + 4);
+        v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w; v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            v[i] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        split_bf16(v[i], hi[i], lo[i]);
+}
+
+// Gradient with respect to a 32 -> 32 layer's input, masked by the previous
+// layer's ReLU: out = (conv^T dZ) * [mask_src > 0], taps at (-dy, -dx) and
+// transposed weights.  dZ arrives in FP32 and enters the tensor cores as a
+// BF16 hi + lo pair (two MMAs per k step), so the gradient keeps ~16 mantissa
+// bits; the weights are exactly the BF16 values the forward used.  FP32 out.
+__global__ void __launch_bounds__(256) k_conv32_bwd(const float *__restrict__ dz, float *__restrict__ out,
+                                                    const bf16 *__restrict__ W, const bf16 *__restrict__ mask_src,
+                                                    int n, int L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int NW = (L + 15) / 16, PX = NW * 16 + 4;
+    bf16 *Ws = reinterpret_cast<bf16 *>(smem);      // [13][32 c][40]  (W transposed)
+    bf16 *Xh = Ws + kTapsB * kCh * kRowStride;       // [3][PX][40] hi
+    bf16 *Xl = Xh + 3 * PX * kRowStride;             // [3][PX][40] lo
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < kTapsB * kCh * kCh; i += blockDim.x) {
+        const int t = i / (kCh * kCh), r = (i / kCh) % kCh, q = i % kCh; // W[t][o = r][c = q]
+        Ws[(t * kCh + q) * kRowStride + r] = W[i];
+    }
+    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
+        const int b = item / L, y = item % L;
+        __syncthreads();
+        for (int i = tid; i < 3 * PX * 4; i += blockDim.x) {
+            const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
+            const int yy = y + r, xx = xi - 2;
+            const bool ok = yy < L && xx >= 0 && xx < L;
+            bf16 hi[8], lo[8];
+            stage_split(dz + (((size_t)b * L + (ok ? yy : 0)) * L + (ok ? xx : 0)) * kCh + ch * 8, ok, hi, lo);
+            *reinterpret_cast<uint4 *>(Xh + (r * PX + xi) * kRowStride + ch * 8) = *reinterpret_cast<uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(Xl + (r * PX + xi) * kRowStride + ch * 8) = *reinterpret_cast<uint4 *>(lo);
+        }
+        __syncthreads();
+        if (warp < NW) {
+            float acc[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+            const int x0 = warp * 16;
+            const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
+            const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
+#pragma unroll 1
+            for (int t = 0; t < kTapsB; ++t) {
+                const int r = -tap_dy(t), xoff = -tap_dx(t);
+#pragma unroll
+                for (int kc = 0; kc < 2; ++kc) {
+                    const int aoff = (r * PX + x0 + arow + xoff + 2) * kRowStride + kc * 16 + acol;
+                    uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
+                    ldsm_x4(smem_u32(Xh + aoff), h0, h1, h2, h3);
+                    ldsm_x4(smem_u32(Xl + aoff), l0, l1, l2, l3);
+#pragma unroll
+                    for (int np = 0; np < 2; ++np) {
+                        uint32_t b0, b1, b2, b3;
+                        ldsm_x4(smem_u32(Ws + (t * kCh + np * 16 + brow) * kRowStride + kc * 16 + bcol), b0, b1, b2,
+                                b3);
+                        mma_bf16(acc[2 * np], h0, h1, h2, h3, b0, b1);
+                        mma_bf16(acc[2 * np], l0, l1, l2, l3, b0, b1);
+                        mma_bf16(acc[2 * np + 1], h0, h1, h2, h3, b2, b3);
+                        mma_bf16(acc[2 * np + 1], l0, l1, l2, l3, b2, b3);
                     }
-                    *reinterpret_cast<__nv_bfloat162 *>(out + o) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+            const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int x = x0 + g + 8 * h;
+                    if (x >= L)
+                        continue;
+                    const int c = 8 * j + 2 * t4;
+                    const size_t o = (((size_t)b * L + y) * L + x) * kCh + c;
+                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(mask_src + o);
+                    *reinterpret_cast<float2 *>(out + o) =
+                        make_float2(bf(m.x) > 0.f ? acc[j][2 * h] : 0.f, bf(m.y) > 0.f ? acc[j][2 * h + 1] : 0.f);
                 }
         }
     }
@@ -245,7 +332,7 @@ __global__ void k_logq(const float *ll, double *logq, int L)
 // ------------------------------------------------------------------ backward
 // Last layer: dZ_{D-1} = (sum_t wD[t] dF(p - d_t)) * [h_{D-1} > 0], one thread
 // per (position, channel).
-__global__ void k_layerD_bwd_data(const float *dF, const float *wD, const bf16 *hD, bf16 *dZ, int n, int L)
+__global__ void k_layerD_bwd_data(const float *dF, const float *wD, const bf16 *hD, float *dZ, int n, int L)
 {
     const size_t total = (size_t)n * L * L * kCh;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -259,7 +346,7 @@ __global__ void k_layerD_bwd_data(const float *dF, const float *wD, const bf16 *
             if (yy < L && xx >= 0 && xx < L)
                 acc += wD[t * kCh + c] * dF[(b * L + yy) * L + xx];
         }
-        dZ[i] = __float2bfloat16(bf(hD[i]) > 0.f ? acc : 0.f);
+        dZ[i] = bf(hD[i]) > 0.f ? acc : 0.f;
     }
 }
 
@@ -290,16 +377,18 @@ __global__ void k_layerD_bwd_w(const float *dF, const bf16 *hD, float *g, DevPar
         atomicAdd(&g[P.b_off[D - 1]], acc);
 }
 
-// Hidden-layer weight and bias gradients on the tensor cores:
+// Hidden-layer weight and bias gradients on the tensor cores (dZ as a BF16
+// hi + lo pair, activations exactly as the forward used them):
 // gW[t][o][c] = sum_p dZ(p)[o] X(p + d_t)[c] -- a 32 x 32 GEMM per tap with the
 // positions as the reduction dimension.  Warp w owns taps w and w + 8.
-__global__ void __launch_bounds__(256) k_dw32(const bf16 *__restrict__ dZ, const bf16 *__restrict__ X, float *g,
+__global__ void __launch_bounds__(256) k_dw32(const float *__restrict__ dZ, const bf16 *__restrict__ X, float *g,
                                               DevParams P, int layer, int n, int L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int NW = (L + 15) / 16, PX = NW * 16 + 4, PZ = NW * 16;
-    bf16 *Zs = reinterpret_cast<bf16 *>(smem); // [PZ][40]
-    bf16 *Xs = Zs + PZ * kRowStride;           // [3][PX][40]
+    bf16 *Zs = reinterpret_cast<bf16 *>(smem); // [PZ][40] dZ hi
+    bf16 *Zl = Zs + PZ * kRowStride;           // [PZ][40] dZ lo
+    bf16 *Xs = Zl + PZ * kRowStride;           // [3][PX][40]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntap = warp + 8 < kTapsB ? 2 : 1;
     float acc[2][2][4][4];
@@ -316,10 +405,10 @@ __global__ void __launch_bounds__(256) k_dw32(const bf16 *__restrict__ dZ, const
         __syncthreads();
         for (int i = tid; i < PZ * 4; i += blockDim.x) {
             const int xi = i / 4, ch = i % 4;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (xi < L)
-                v = *reinterpret_cast<const uint4 *>(dZ + (((size_t)b * L + y) * L + xi) * kCh + ch * 8);
-            *reinterpret_cast<uint4 *>(Zs + xi * kRowStride + ch * 8) = v;
+            bf16 hi[8], lo[8];
+            stage_split(dZ + (((size_t)b * L + y) * L + (xi < L ? xi : 0)) * kCh + ch * 8, xi < L, hi, lo);
+            *reinterpret_cast<uint4 *>(Zs + xi * kRowStride + ch * 8) = *reinterpret_cast<uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(Zl + xi * kRowStride + ch * 8) = *reinterpret_cast<uint4 *>(lo);
         }
         for (int i = tid; i < 3 * PX * 4; i += blockDim.x) {
             const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
@@ -332,16 +421,18 @@ __global__ void __launch_bounds__(256) k_dw32(const bf16 *__restrict__ dZ, const
         __syncthreads();
         if (tid < kCh)
             for (int x = 0; x < L; ++x)
-                bsum += bf(Zs[x * kRowStride + tid]);
+                bsum += bf(Zs[x * kRowStride + tid]) + bf(Zl[x * kRowStride + tid]);
         for (int j = 0; j < NW; ++j) {
             const int x0 = 16 * j;
             // A = dZ^T (rows o, k = positions): 8x8 blocks (p0, o0) transposed
-            uint32_t a[2][4];
+            uint32_t a[2][4], al[2][4];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
                 const int i = lane >> 3;
                 const int p0 = x0 + ((i >> 1) ? 8 : 0), o0 = 16 * mt + ((i & 1) ? 8 : 0);
-                ldsm_x4_t(smem_u32(Zs + (p0 + (lane & 7)) * kRowStride + o0), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+                const int off = (p0 + (lane & 7)) * kRowStride + o0;
+                ldsm_x4_t(smem_u32(Zs + off), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+                ldsm_x4_t(smem_u32(Zl + off), al[mt][0], al[mt][1], al[mt][2], al[mt][3]);
             }
 #pragma unroll
             for (int tt = 0; tt < 2; ++tt) {
@@ -359,7 +450,9 @@ __global__ void __launch_bounds__(256) k_dw32(const bf16 *__restrict__ dZ, const
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt) {
                         mma_bf16(acc[tt][mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                        mma_bf16(acc[tt][mt][2 * np], al[mt][0], al[mt][1], al[mt][2], al[mt][3], b0, b1);
                         mma_bf16(acc[tt][mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+                        mma_bf16(acc[tt][mt][2 * np + 1], al[mt][0], al[mt][1], al[mt][2], al[mt][3], b2, b3);
                     }
                 }
             }
@@ -381,7 +474,7 @@ __global__ void __launch_bounds__(256) k_dw32(const bf16 *__restrict__ dZ, const
 }
 
 // Layer-1 weight and bias gradients: gW1[o][t] = sum_p dZ1(p)[o] s(p + d_t).
-__global__ void k_layer1_bwd_w(const bf16 *dZ1, const int8_t *spins, float *g, DevParams P, int n, int L)
+__global__ void k_layer1_bwd_w(const float *dZ1, const int8_t *spins, float *g, DevParams P, int n, int L)
 {
     const int tid = threadIdx.x; // kCh * (kTapsA + 1) threads
     const int o = tid / (kTapsA + 1), t = tid % (kTapsA + 1);
@@ -389,7 +482,7 @@ __global__ void k_layer1_bwd_w(const bf16 *dZ1, const int8_t *spins, float *g, D
     for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
         const int b = item / L, y = item % L;
         for (int x = 0; x < L; ++x) {
-            const float d = bf(dZ1[(((size_t)b * L + y) * L + x) * kCh + o]);
+            const float d = dZ1[(((size_t)b * L + y) * L + x) * kCh + o];
             if (t < kTapsA) {
                 const int yy = y + tap_dy(t), xx = x + tap_dx(t);
                 if (yy >= 0 && xx >= 0 && xx < L)
@@ -672,7 +765,8 @@ struct mc_van {
     float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
     bf16 *wh = nullptr;
     float *w1 = nullptr, *wD = nullptr, *bias = nullptr;
-    bf16 *H = nullptr, *dZa = nullptr, *dZb = nullptr;
+    bf16 *H = nullptr;
+    float *dZa = nullptr, *dZb = nullptr;
     float *f = nullptr, *ll = nullptr, *dF = nullptr;
     int8_t *spins = nullptr, *prop = nullptr;
     double *lq = nullptr, *lq2 = nullptr, *lq3 = nullptr, *lq4 = nullptr, *mh_lr = nullptr;
@@ -716,8 +810,8 @@ VanLayout van_layout(int L, int nmax, int D)
     o.wD = take((size_t)kTapsB * kCh * 4);
     o.bias = take((size_t)((D - 1) * kCh + 1) * 4);
     o.H = take((size_t)(D - 1) * pos * kCh * 2);
-    o.dZa = take(pos * kCh * 2);
-    o.dZb = take(pos * kCh * 2);
+    o.dZa = take(pos * kCh * 4);
+    o.dZb = take(pos * kCh * 4);
     o.f = take(pos * 4);
     o.ll = take(pos * 4);
     o.dF = take(pos * 4);
@@ -739,10 +833,14 @@ VanLayout van_layout(int L, int nmax, int D)
 unsigned grid_for(size_t n, int threads, int sms) { return (unsigned)std::min<size_t>((n + threads - 1) / threads, (size_t)sms * 16); }
 
 size_t conv_smem(int L) { return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)3 * (((L + 15) / 16) * 16 + 4) * kRowStride * 2; }
+size_t conv_bwd_smem(int L)
+{
+    return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)6 * (((L + 15) / 16) * 16 + 4) * kRowStride * 2;
+}
 size_t dw_smem(int L)
 {
     const int PZ = ((L + 15) / 16) * 16;
-    return (size_t)PZ * kRowStride * 2 + (size_t)3 * (PZ + 4) * kRowStride * 2;
+    return (size_t)2 * PZ * kRowStride * 2 + (size_t)3 * (PZ + 4) * kRowStride * 2;
 }
 size_t sample_smem(int D)
 {
@@ -772,9 +870,9 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
                                                                            L);
     const unsigned cg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 3);
     for (int l = 1; l <= D - 2; ++l)
-        k_conv32<false><<<cg, 256, conv_smem(L), w->stream>>>(w->H + (l - 1) * layer, w->H + l * layer,
-                                                              w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
-                                                              w->bias + l * kCh, nullptr, n, L);
+        k_conv32<<<cg, 256, conv_smem(L), w->stream>>>(w->H + (l - 1) * layer, w->H + l * layer,
+                                                       w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
+                                                       w->bias + l * kCh, n, L);
     k_layerD_fwd<<<grid_for(pos, 256, w->sms), 256, 0, w->stream>>>(w->H + (D - 2) * layer, w->wD,
                                                                     w->bias + (D - 1) * kCh, w->spins, negate, w->f,
                                                                     w->ll, dF, 1.0f / n, n, L);
@@ -793,12 +891,12 @@ cudaError_t backward(mc_van *w, int n)
     k_layerD_bwd_data<<<grid_for(pos * kCh, 256, w->sms), 256, 0, w->stream>>>(w->dF, w->wD, hD, w->dZa, n, L);
     const unsigned rg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 4);
     k_layerD_bwd_w<<<rg, kTapsB * kCh + 1, 0, w->stream>>>(w->dF, hD, w->g, w->dp, n, L);
-    bf16 *dz = w->dZa, *dzn = w->dZb;
+    float *dz = w->dZa, *dzn = w->dZb;
     const unsigned cg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 3);
     for (int l = D - 2; l >= 1; --l) { // hidden layer l: input H[l-1], output H[l], grad dz wrt its pre-activation
         k_dw32<<<cg, 256, dw_smem(L), w->stream>>>(dz, w->H + (l - 1) * layer, w->g, w->dp, l, n, L);
-        k_conv32<true><<<cg, 256, conv_smem(L), w->stream>>>(dz, dzn, w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
-                                                             nullptr, w->H + (l - 1) * layer, n, L);
+        k_conv32_bwd<<<cg, 256, conv_bwd_smem(L), w->stream>>>(dz, dzn, w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
+                                                               w->H + (l - 1) * layer, n, L);
         std::swap(dz, dzn);
     }
     k_layer1_bwd_w<<<rg, kCh * (kTapsA + 1), 0, w->stream>>>(dz, w->spins, w->g, w->dp, n, L);
@@ -864,8 +962,8 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     w->wD = reinterpret_cast<float *>(b + o.wD);
     w->bias = reinterpret_cast<float *>(b + o.bias);
     w->H = reinterpret_cast<bf16 *>(b + o.H);
-    w->dZa = reinterpret_cast<bf16 *>(b + o.dZa);
-    w->dZb = reinterpret_cast<bf16 *>(b + o.dZb);
+    w->dZa = reinterpret_cast<float *>(b + o.dZa);
+    w->dZb = reinterpret_cast<float *>(b + o.dZb);
     w->f = reinterpret_cast<float *>(b + o.f);
     w->ll = reinterpret_cast<float *>(b + o.ll);
     w->dF = reinterpret_cast<float *>(b + o.dF);
@@ -885,9 +983,9 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(w->ws, 0, o.hist, w->stream); // params, Adam state, buffers
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(L));
+        e = cudaFuncSetAttribute(k_conv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(L));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(L));
+        e = cudaFuncSetAttribute(k_conv32_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_bwd_smem(L));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dw32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(L));
     if (e == cudaSuccess)

@@ -2,12 +2,16 @@
 against the FP64 oracle (oracle/van.py), and exactness of its
 Metropolis-Hastings correction against the Boltzmann distribution of Eq. (1).
 
-Tolerances: weights are given in BF16-representable values on both sides, so
-the GPU differs from FP64 only by BF16 rounding of activations (8-bit
-mantissa, relative 2^-9 per layer) and FP32 accumulation; log q and gradients
-are compared at the 1e-2 relative level (per-tensor relative error, cosine >
-0.999 for gradients).  Normalisation (sum_s q(s) = 1) is structural and holds
-to FP32 rounding."""
+Tolerances.  Weights are BF16-representable on both sides.  Against the oracle
+run with BF16-rounded activations (the precision the task fixes), the GPU
+differs only by FP32 accumulation order: log q to 1e-4 relative, gradients to
+1e-3 relative per tensor.  Against the plain FP64 oracle the network itself is
+a slightly different function -- each activation carries a relative rounding
+of up to 2^-9 -- so log q agrees to 1e-2 relative, and a weight gradient, a sum
+of ~10^3 terms of both signs, to cos > 0.995 and 10% relative (the measured
+gap between the FP64 and BF16-activation oracles is cos 0.9984, rel 0.057 for
+the test's network).  Normalisation (sum_s q(s) = 1) is structural and holds to
+FP32 rounding."""
 import numpy as np
 import pytest
 import torch
@@ -46,6 +50,8 @@ def test_log_prob_matches_oracle():
     g = net.log_prob(torch.from_numpy(s).cuda()).cpu().numpy()
     o = van.log_prob(p, s.astype(np.float64))
     assert np.max(np.abs(g - o) / np.abs(o)) < 1e-2, (g[:4], o[:4])
+    ob = van.log_prob(p, s.astype(np.float64), act="bf16")
+    assert np.max(np.abs(g - ob) / np.abs(ob)) < 1e-4, (g[:4], ob[:4])
     gn = net.log_prob(torch.from_numpy(s).cuda(), negate=True).cpu().numpy()
     on = van.log_prob(p, -s.astype(np.float64))
     assert np.max(np.abs(gn - on) / np.abs(on)) < 1e-2
@@ -70,15 +76,16 @@ def test_gradients_match_oracle():
     s = np.where(rng.random((n, L, L)) < 0.5, 1, -1).astype(np.int8)
     loss_g = net.train_step(torch.from_numpy(s).cuda(), lr=0.0, apply=False)
     _, gflat = net.get_params(grads=True)
-    loss_o, go = van.loss_and_grad(p, s.astype(np.float64))
-    assert abs(loss_g - loss_o) / abs(loss_o) < 1e-2
     gg = mc.mc.van_unpack(gflat)
-    for l, ((gW, gb), (oW, ob)) in enumerate(zip(gg, go)):  # taps outside the masks are 0 on both sides
-        a = np.concatenate([gW.ravel(), gb.ravel()])
-        b = np.concatenate([oW.ravel(), ob.ravel()])
-        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
-        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-        assert cos > 0.999 and rel < 1e-2, (l, cos, rel)
+    for act, cos_min, rel_max in (("bf16", 1 - 1e-6, 1e-3), ("fp64", 0.995, 0.1)):
+        loss_o, go = van.loss_and_grad(p, s.astype(np.float64), act=act)
+        assert abs(loss_g - loss_o) / abs(loss_o) < (1e-5 if act == "bf16" else 1e-2)
+        for l, ((gW, gb), (oW, ob)) in enumerate(zip(gg, go)):  # taps outside the masks are 0 on both sides
+            a = np.concatenate([gW.ravel(), gb.ravel()])
+            b = np.concatenate([oW.ravel(), ob.ravel()])
+            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            assert cos > cos_min and rel < rel_max, (act, l, cos, rel)
 
 
 def test_sampler_follows_q():

@@ -146,3 +146,20 @@ def test_mh_correction_is_exact(correct):
         assert pval > 1e-4, pval
     else:
         assert pval < 1e-6, pval  # the test has the power to see a wrong ratio
+
+
+def test_bf16_rounding():
+    """Round to nearest BF16, ties to even, against values worked out by hand."""
+    # BF16 keeps 7 explicit significand bits: spacing 2^-7 at 1, halfway point 2^-8
+    x = np.array([1.0, 1.0 + 2.0**-8, 1.0 + 3 * 2.0**-9, 1.0 + 2.0**-9 + 2.0**-20, 1.0 + 3 * 2.0**-8, -2.5,
+                  3.14159265, 1.5 * 2.0**-100, 0.0])
+    want = np.array([1.0, 1.0, 1.0 + 2.0**-7, 1.0, 1.0 + 2.0**-6, -2.5, 3.140625, 1.5 * 2.0**-100, 0.0])
+    np.testing.assert_array_equal(van.round_bf16(x), want)
+    r = van.round_bf16(np.linspace(-4, 4, 1001))
+    assert np.all(np.abs(r - np.linspace(-4, 4, 1001)) <= 2.0**-8 * np.abs(np.linspace(-4, 4, 1001)) + 1e-45)
+
+
+def test_bf16_activation_network_is_normalised():
+    p = van.masked(van.init_params(depth=4, channels=4, seed=3, scale=2.0))
+    q = np.exp(van.log_prob(p, all_states(4, 4), act="bf16"))
+    assert abs(q.sum() - 1.0) < 1e-10

@@ -47,6 +47,11 @@ SM_COUNT, MUL32_PER_SM_CLK, SM_MAX_MHZ = 152, 64, 2070.0
 MUL32_PEAK = SM_COUNT * MUL32_PER_SM_CLK * SM_MAX_MHZ * 1e6
 # Algorithmic bytes per SU(2) link update: read + write of the link once per sweep.
 SU2_BYTES_PER_UPDATE = 32.0
+# DRAM bytes (read + write) per MSC half-sweep launch of this workload, from one
+# ncu capture of the current kernel (profiles/k_half_sweep_msc32_ising_batch.md):
+# 179 MB read (both colour planes once) + 51.7 MB written (changed words only).
+# Set to None whenever the kernel changes until it is captured again.
+MSC_TRAFFIC_PER_LAUNCH = 230.6e6
 
 
 def log(*a):
@@ -199,6 +204,7 @@ def run_gb300(args):
     # ---- SU(2) and batched-chain components -------------------------------------------
     su2 = run_su2(mc, torch, rank, args.su2_steps, world)
     batched = run_batched(mc, torch, rank, args.batch_steps, world)
+    ess_cmp = run_ess(args) if not args.no_ess else None
 
     line = {
         "metric": METRIC,
@@ -228,18 +234,18 @@ def run_gb300(args):
             "peak": MUL32_PEAK,
             "unit": "int32-mul/s",
             "frac": achieved / MUL32_PEAK,
-            "traffic": None,
+            "traffic": MSC_TRAFFIC_PER_LAUNCH,
             "kernel": "k_half_sweep<C, MSC32> (Ising half-sweep)",
             "kernel_ms_per_launch": half_ms,
             "kernel_share_of_step": kernel_ms / ms if ms > 0 else None,
             "algorithmic": "10 int32 multiplies per attempted flip (1/4 Philox4x32-10 block)",
-            "peak_source": "derived: 152 SMs x 64 int32 multiplies/clk x 2070 MHz (MEASURED_PEAKS.json has no "
+            "peak_source": "derived: 152 SMs x 64 int32 multiplies/clk x 2070 MHz (the measured peaks have no "
                            "integer figure); a pure-Philox probe reached 103% of it",
         },
         "e2e": e2e,
         "gpu_launches": launches + K,  # 2 half-sweeps + 1 state-advance kernel per step
         "clocks": clock_info,
-        "components": {"su2": su2, "batched": batched},
+        "components": {"su2": su2, "batched": batched, "ess_beta_c": ess_cmp},
         "device": dev_props.name,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -376,6 +382,22 @@ def run_batched(mc, torch, rank, K, world, sweeps_per_call=10):
             "autotuned": {k: choice[k] for k in ("cluster", "threads", "split", "cached")}}
 
 
+def run_ess(args) -> dict:
+    """Effective independent |M| samples per second at beta_c on 64 x 64:
+    plain checkerboard Metropolis versus Metropolis interleaved 1:10 with the
+    learned proposal (4096 chains, one proposal each per round; the network
+    trained on ~2 x 10^5 configurations of the plain chains, training time
+    reported separately)."""
+    from paper_0903_3053_gb300 import ess
+    L, beta = 64, 0.4406868
+    plain = ess.plain_rate(L, beta, chains=1024, therm=5000, sweeps=args.ess_sweeps, every=4)
+    learned = ess.learned_rate(L, beta, chains=4096, therm=5000, data_snapshots=48, data_spacing=200,
+                               train_steps=args.ess_train_steps, train_batch=512, rounds=args.ess_rounds,
+                               local_sweeps=10)
+    return {"metric": "eff. independent |M| samples/s at beta_c, L=64", "unit": "samples/s",
+            "plain": plain, "learned": learned, "learned_over_plain": learned["ess_per_s"] / plain["ess_per_s"]}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 def cpu_baseline(seconds: float) -> dict:
     """The oracle as it stands (plain C, one thread) on a bounded sample of the
@@ -434,6 +456,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--su2-steps", type=int, default=40)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--ess-sweeps", type=int, default=20000)
+    ap.add_argument("--ess-rounds", type=int, default=200)
+    ap.add_argument("--ess-train-steps", type=int, default=1500)
+    ap.add_argument("--no-ess", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

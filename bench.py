@@ -108,9 +108,8 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- distributed
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_0903_3053_gb300 import replicas
+    world, rank, local = replicas.env_world()
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -120,19 +119,18 @@ def dist_setup():
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_0903_3053_gb300 import replicas
+    replicas.barrier(world)
 
 
 def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_0903_3053_gb300 import replicas
+    return replicas.max_over_ranks(x, world, "cuda")
+
+
+def cid(rank: int, index: int) -> int:
+    from paper_0903_3053_gb300 import replicas
+    return replicas.chain_id(rank, index)
 
 
 # ----------------------------------------------------------------------------- workload
@@ -142,7 +140,7 @@ def ising_chains(rank: int):
     for i, L in enumerate(SIZES):
         for j, b in enumerate(BETAS):
             idx = i * len(BETAS) + j
-            out.append(mc.ising(L, b, seed=1, chain_id=rank * 1000 + idx, hot=True))
+            out.append(mc.ising(L, b, seed=1, chain_id=cid(rank, idx), hot=True))
     return out
 
 
@@ -295,7 +293,7 @@ def run_e2e(mc, torch, rank, K, world):
 
 
 def run_su2(mc, torch, rank, K, world):
-    chains = [mc.su2(SU2_L, b, seed=1, chain_id=rank * 1000 + i, hot=True) for i, b in enumerate(SU2_BETAS)]
+    chains = [mc.su2(SU2_L, b, seed=1, chain_id=cid(rank, i), hot=True) for i, b in enumerate(SU2_BETAS)]
     batch = mc.Batch(chains, series_capacity=K + 8)
     batch.sweep(3, 1)
     batch.read_series()
@@ -338,11 +336,9 @@ def run_batched(mc, torch, rank, K, world, sweeps_per_call=10):
     call (autotuned launch shape); value = site/link updates per second."""
     from paper_0903_3053_gb300 import autotune, workloads
     spec = workloads.batched_chains(seed=0)
-    off = rank * 100000
-
     def chain(d):
         f = mc.ising if d["kind"] == "ising" else mc.su2
-        return f(d["L"], d["beta"], d["seed"], d["chain_id"] + off)
+        return f(d["L"], d["beta"], d["seed"], cid(rank, d["chain_id"]))
 
     i8 = [chain(d) for d in spec if d["kind"] == "ising" and d["L"] < 64]
     msc = [chain(d) for d in spec if d["kind"] == "ising" and d["L"] >= 64]

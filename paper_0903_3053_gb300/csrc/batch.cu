@@ -50,7 +50,7 @@ struct GroupArgs {
     const uint32_t *round_start; // per cluster, into `rounds` (n_clusters + 1 entries)
     const int32_t *rounds;       // [round][C] item per CTA rank, -1 = idle
     const uint8_t *round_shared; // per round: 1 = all ranks share the item
-    double *partials;            // [item][kMaxCluster][2] SU(2) plaquette partials
+    long long *partials;         // [item][kMaxCluster][2] SU(2) plaquette partials (fixed point)
     int C;
     uint32_t n_sweeps, every;
 };
@@ -63,11 +63,11 @@ __device__ __forceinline__ void group_barrier(int G, cg::cluster_group &cluster)
         __syncthreads();
 }
 
-__device__ __forceinline__ void block_sum2d(double &a, double &b)
+__device__ __forceinline__ void block_sum2ll(long long &a, long long &b)
 {
-    __shared__ double sa[32], sb[32];
-    a = warp_sum(a);
-    b = warp_sum(b);
+    __shared__ long long sa[32], sb[32];
+    a = warp_sum_ll(a);
+    b = warp_sum_ll(b);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
         sa[w] = a;
@@ -75,7 +75,7 @@ __device__ __forceinline__ void block_sum2d(double &a, double &b)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double ta = 0.0, tb = 0.0;
+        long long ta = 0, tb = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
             ta += sa[i];
             tb += sb[i];
@@ -159,30 +159,30 @@ __device__ void run_su2(const GroupMember &m, int chain, int item, int G, int ra
     float4 *U = reinterpret_cast<float4 *>(m.lattice + ch.link_off);
     const unsigned long long base = m.state->sweep_base;
     const uint32_t stride = (uint32_t)G * blockDim.x, start = (uint32_t)rank * blockDim.x + threadIdx.x;
-    double *part = g.partials + (size_t)item * kMaxCluster * 2;
+    long long *part = g.partials + (size_t)item * kMaxCluster * 2;
     for (uint32_t t = 0; t < g.n_sweeps; ++t) {
         const uint32_t sweep = (uint32_t)(base + t);
         for (int phase = 0; phase < 8; ++phase) { // (odd, mu = 0..3), then (even, mu = 0..3)
             for (uint32_t e = start; e < ch.nh; e += stride)
-                su2_update_link_rt<kLdCoherent>(phase, U, ch, ks, e, sweep, nullptr, m.state);
+                su2_update_link_rt<kLdCoherent>(phase, U, ch, ks, e, sweep, m.state);
             group_barrier(G, cluster);
         }
         if (g.every != 0 && ((t + 1) % g.every) == 0) {
-            double ps = 0.0, pt = 0.0;
+            long long ps = 0, pt = 0;
             for (uint32_t s = start; s < 2 * ch.nh; s += stride) {
                 float fs, ft;
                 su2_site_plaquettes<kLdCoherent>(U, ch, s, fs, ft);
-                ps += (double)fs;
-                pt += (double)ft;
+                ps += plaq_fixed(fs);
+                pt += plaq_fixed(ft);
             }
-            block_sum2d(ps, pt);
+            block_sum2ll(ps, pt);
             if (threadIdx.x == 0) {
                 part[2 * rank] = ps;
                 part[2 * rank + 1] = pt;
             }
             group_barrier(G, cluster);
-            if (rank == 0 && threadIdx.x == 0) { // fixed rank order: deterministic FP64 sum
-                double A = 0.0, B = 0.0;
+            if (rank == 0 && threadIdx.x == 0) { // exact fixed-point sum: same value as the context kernels
+                long long A = 0, B = 0;
                 for (int r = 0; r < G; ++r) {
                     A += part[2 * r];
                     B += part[2 * r + 1];
@@ -192,9 +192,9 @@ __device__ void run_su2(const GroupMember &m, int chain, int item, int G, int ra
                 DevRecord *rec = &m.series[(long long)chain * m.cap + (long long)(ri % (unsigned long long)m.cap)];
                 rec->sweep = (long long)sweep;
                 rec->a = rec->b = 0;
-                rec->d0 = (A + B) / (6.0 * n);
-                rec->d1 = A / (3.0 * n);
-                rec->d2 = B / (3.0 * n);
+                rec->d0 = (double)(A + B) * kPlaqUnfix / (6.0 * n);
+                rec->d1 = (double)A * kPlaqUnfix / (3.0 * n);
+                rec->d2 = (double)B * kPlaqUnfix / (3.0 * n);
             }
         }
     }
@@ -247,7 +247,7 @@ struct mc_group {
     uint32_t *d_round_start = nullptr;
     int32_t *d_rounds = nullptr;
     uint8_t *d_round_shared = nullptr;
-    double *d_partials = nullptr;
+    long long *d_partials = nullptr;
     size_t max_rounds = 0, max_clusters = 0;
     // configuration and schedule
     int C = 4, threads = 256;
@@ -299,7 +299,7 @@ Layout group_layout(size_t n_members, size_t n_items)
     L.round_start = take((L.max_clusters + 1) * sizeof(uint32_t));
     L.rounds = take(L.max_rounds * kMaxCluster * sizeof(int32_t));
     L.round_shared = take(L.max_rounds);
-    L.partials = take(n_items * kMaxCluster * 2 * sizeof(double));
+    L.partials = take(n_items * kMaxCluster * 2 * sizeof(long long));
     L.total = off;
     return L;
 }
@@ -496,7 +496,7 @@ mc_status mc_group_create(mc_group **out, int32_t n_ctx, mc_ctx *const *ctxs, vo
     g->d_round_start = reinterpret_cast<uint32_t *>(g->ws + L.round_start);
     g->d_rounds = reinterpret_cast<int32_t *>(g->ws + L.rounds);
     g->d_round_shared = reinterpret_cast<uint8_t *>(g->ws + L.round_shared);
-    g->d_partials = reinterpret_cast<double *>(g->ws + L.partials);
+    g->d_partials = reinterpret_cast<long long *>(g->ws + L.partials);
     cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&g->fence_in, cudaEventDisableTiming);

@@ -156,7 +156,7 @@ Plan make_plan(int32_t n, const mc_chain_desc *chains, int32_t layout, int64_t c
         }
     }
     p.partial_count = 2 * meas_blocks;
-    p.partials = take(p.partial_count * sizeof(double));
+    p.partials = take(p.partial_count * sizeof(long long));
     p.staging_bytes = staging;
     p.staging = take(staging);
     p.tries_off.assign(n, 0);
@@ -392,7 +392,7 @@ mc_status mc_batch_init(mc_ctx **out, int32_t n_chains, const mc_chain_desc *cha
     c->d_meas_start = reinterpret_cast<uint32_t *>(c->ws + p.meas_start);
     c->d_series = reinterpret_cast<DevRecord *>(c->ws + p.series);
     c->d_scratch_rec = reinterpret_cast<DevRecord *>(c->ws + p.scratch_rec);
-    c->d_partials = reinterpret_cast<double *>(c->ws + p.partials);
+    c->d_partials = reinterpret_cast<long long *>(c->ws + p.partials);
     c->partial_count = p.partial_count;
     c->d_staging = c->ws + p.staging;
     c->staging_bytes = p.staging_bytes;
@@ -428,6 +428,10 @@ mc_status mc_batch_init(mc_ctx **out, int32_t n_chains, const mc_chain_desc *cha
             ch.chain_id = chains[k].chain_id;
             ch.link_off = p.lat_off[k];
             ch.tries_off = p.tries_off[k];
+            ch.div1h = make_fastdiv((uint32_t)ch.L[1] / 2);
+            ch.div1 = make_fastdiv((uint32_t)ch.L[1]);
+            ch.div2 = make_fastdiv((uint32_t)ch.L[2]);
+            ch.div3 = make_fastdiv((uint32_t)ch.L[3]);
         }
         e = cudaMemcpyAsync(c->d_chains, c->su2.data(), sizeof(Su2Chain) * n_chains, cudaMemcpyHostToDevice,
                             c->stream);

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/mc.h"
+#include "fastdiv.cuh"
 #include "philox.cuh"
 
 namespace mc {
@@ -41,6 +42,7 @@ struct Su2Chain {
     uint32_t pad0;
     uint64_t link_off;  // byte offset of the links: float4 [parity][mu][nh]
     uint64_t tries_off; // byte offset of the try record: uint8 [s][mu]
+    FastDiv div1h, div1, div2, div3; // by L1 / 2, L1, L2, L3: site index -> coordinates
 };
 
 // Device-resident run state: lets one captured CUDA graph be replayed.
@@ -143,7 +145,7 @@ struct mc_ctx {
     mc::DevState *d_state = nullptr;
     char *d_staging = nullptr;
     size_t staging_bytes = 0;
-    double *d_partials = nullptr;        // SU(2) plaquette per-block partial sums
+    long long *d_partials = nullptr;     // SU(2) plaquette per-block partial sums (fixed point)
     size_t partial_count = 0;
     uint8_t *d_tries = nullptr;
     mc::DevRecord *d_scratch_rec = nullptr; // one record per chain for mc_measure

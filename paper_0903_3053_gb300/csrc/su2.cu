@@ -22,14 +22,19 @@
 // (e, sweep, TAG_HB | p<<12 | mu<<8 | t, chain); the direction uses
 // (e, sweep, TAG_DIR | p<<12 | mu<<8, chain).  Uniforms are ((r>>8)+1) 2^-24.
 // FP32 throughout (logf/cospif/sincospif/expm1f/log1pf, not the fast
-// intrinsics), FP64 only in the plaquette sums.
+// intrinsics: __cosf/__logf moved single links by more than 1e-5), FP64 only
+// in the plaquette sums.  Site coordinates come from magic-number divisions.
 #include "su2_dev.cuh"
 
 namespace mc {
 namespace {
 
-template <int P, int MU>
-__global__ void __launch_bounds__(256) k_phase(SweepArgs a)
+// 256 threads, at least 6 blocks per SM (40 registers, no spills): the phase
+// is bound by the latency of the 18 neighbour-link loads, and 48 resident warps
+// hide it better than the 40 an unconstrained build allows (+14% measured on
+// 4 x 32^4).
+template <int P, int MU, bool REC>
+__global__ void __launch_bounds__(256, 6) k_phase(SweepArgs a)
 {
     const uint32_t b = blockIdx.x + a.block_base;
     const int k = find_chain(a.block_start, a.n_chains, b);
@@ -39,31 +44,31 @@ __global__ void __launch_bounds__(256) k_phase(SweepArgs a)
         return;
     float4 *U = reinterpret_cast<float4 *>(a.lattice + ch.link_off);
     const PhiloxSchedule ks = philox_schedule(ch.key);
-    su2_update_link<P, MU, kLdReadOnly>(U, ch, ks, e, (uint32_t)(a.state->sweep_base + a.k), a.tries, a.state);
+    su2_update_link<P, MU, kLdReadOnly, REC>(U, ch, ks, e, (uint32_t)(a.state->sweep_base + a.k), a.tries, a.state);
 }
 
 // ------------------------------------------------------------------ plaquette
 // Per-block partial sums of (1/2) Tr U_munu(x) of Eq. (3), spatial and temporal
-// separately (the two FP64 values per measuring thread of Sec. 2.4).  Products
-// in FP32, sums in FP64.  One thread per site; partial[2 b], partial[2 b + 1].
+// separately (the two values per measuring thread of Sec. 2.4).  Products in
+// FP32, sums in exact int64 fixed point (plaq_fixed); partial[2 b], partial[2 b + 1].
 __global__ void __launch_bounds__(256) k_plaquette(const Su2Chain *chains, const uint32_t *meas_start, int n_chains,
-                                                   const char *lattice, double *partial, uint32_t block_base)
+                                                   const char *lattice, long long *partial, uint32_t block_base)
 {
-    __shared__ double ss[8], st[8];
+    __shared__ long long ss[8], st[8];
     const uint32_t blk = blockIdx.x + block_base;
     const int k = find_chain(meas_start, n_chains, blk);
     const Su2Chain ch = chains[k];
     const uint32_t s = (blk - meas_start[k]) * blockDim.x + threadIdx.x;
     const uint32_t n = 2 * ch.nh;
-    double ps = 0.0, pt = 0.0;
+    long long ps = 0, pt = 0;
     if (s < n) {
         float fs, ft;
         su2_site_plaquettes<kLdReadOnly>(reinterpret_cast<const float4 *>(lattice + ch.link_off), ch, s, fs, ft);
-        ps = (double)fs;
-        pt = (double)ft;
+        ps = plaq_fixed(fs);
+        pt = plaq_fixed(ft);
     }
-    ps = warp_sum(ps);
-    pt = warp_sum(pt);
+    ps = warp_sum_ll(ps);
+    pt = warp_sum_ll(pt);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
         ss[w] = ps;
@@ -71,7 +76,7 @@ __global__ void __launch_bounds__(256) k_plaquette(const Su2Chain *chains, const
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
+        long long a = 0, b = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
             a += ss[i];
             b += st[i];
@@ -81,23 +86,23 @@ __global__ void __launch_bounds__(256) k_plaquette(const Su2Chain *chains, const
     }
 }
 
-// One block per chain (blockIdx.x = chain index, or `only` when >= 0): fixed-order
-// sum of the chain's partials, written as P, P_s, P_t.
+// One block per chain (blockIdx.x = chain index, or `only` when >= 0): exact sum
+// of the chain's partials, written as P, P_s, P_t.
 __global__ void __launch_bounds__(256) k_plaquette_final(const Su2Chain *chains, const uint32_t *meas_start,
-                                                         const double *partial, DevRecord *series, long long cap,
+                                                         const long long *partial, DevRecord *series, long long cap,
                                                          const DevState *state, uint32_t ksweep, uint32_t rec_k,
                                                          int only, DevRecord *out)
 {
-    __shared__ double ss[8], st[8];
+    __shared__ long long ss[8], st[8];
     const int k = only >= 0 ? only : (int)blockIdx.x;
     const uint32_t b0 = meas_start[k], b1 = meas_start[k + 1];
-    double a = 0.0, b = 0.0;
+    long long a = 0, b = 0;
     for (uint32_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
         a += partial[2 * i];
         b += partial[2 * i + 1];
     }
-    a = warp_sum(a);
-    b = warp_sum(b);
+    a = warp_sum_ll(a);
+    b = warp_sum_ll(b);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
         ss[w] = a;
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(256) k_plaquette_final(const Su2Chain *chains,
     __syncthreads();
     if (threadIdx.x != 0)
         return;
-    double A = 0.0, B = 0.0;
+    long long A = 0, B = 0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
         A += ss[i];
         B += st[i];
@@ -122,9 +127,9 @@ __global__ void __launch_bounds__(256) k_plaquette_final(const Su2Chain *chains,
     }
     rec->sweep = sweep;
     rec->a = rec->b = 0;
-    rec->d0 = (A + B) / (6.0 * n);
-    rec->d1 = A / (3.0 * n);
-    rec->d2 = B / (3.0 * n);
+    rec->d0 = (double)(A + B) * kPlaqUnfix / (6.0 * n);
+    rec->d1 = (double)A * kPlaqUnfix / (3.0 * n);
+    rec->d2 = (double)B * kPlaqUnfix / (3.0 * n);
 }
 
 // ------------------------------------------------------------------ init / I/O
@@ -191,11 +196,16 @@ void launch_phase(mc_ctx *c, const SweepArgs &a, int mu, unsigned nblocks)
 {
     if (prof_begin(c) != cudaSuccess)
         return;
-    switch (mu) {
-    case 0: k_phase<P, 0><<<nblocks, c->threads, 0, c->ls>>>(a); break;
-    case 1: k_phase<P, 1><<<nblocks, c->threads, 0, c->ls>>>(a); break;
-    case 2: k_phase<P, 2><<<nblocks, c->threads, 0, c->ls>>>(a); break;
-    default: k_phase<P, 3><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    const bool rec = a.tries != nullptr;
+    switch (mu * 2 + (rec ? 1 : 0)) {
+    case 0: k_phase<P, 0, false><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 1: k_phase<P, 0, true><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 2: k_phase<P, 1, false><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 3: k_phase<P, 1, true><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 4: k_phase<P, 2, false><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 5: k_phase<P, 2, true><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 6: k_phase<P, 3, false><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    default: k_phase<P, 3, true><<<nblocks, c->threads, 0, c->ls>>>(a); break;
     }
     prof_end(c);
 }

@@ -47,11 +47,19 @@ SM_COUNT, MUL32_PER_SM_CLK, SM_MAX_MHZ = 152, 64, 2070.0
 MUL32_PEAK = SM_COUNT * MUL32_PER_SM_CLK * SM_MAX_MHZ * 1e6
 # Algorithmic bytes per SU(2) link update: read + write of the link once per sweep.
 SU2_BYTES_PER_UPDATE = 32.0
+# Algorithmic instructions per SU(2) link update (one issue slot per thread
+# instruction, FMA = 1): staple 12 quaternion products x 16 + 5 quaternion sums
+# x 4 = 212; |W|, V, alpha 11; Kennedy-Pendleton 20 per try x 1.2 tries = 24;
+# direction on S^2 18; X V, reprojection and store 26; 19 link loads; Philox
+# 2.2 blocks x (20 wide multiplies + 20 xors) = 88  ->  ~400.
+SU2_INSTR_PER_UPDATE = 400.0
+# Issue rate of a GB300: 152 SMs x 4 schedulers x 32 lanes per clock at 2070 MHz.
+ISSUE_PEAK = SM_COUNT * 128 * SM_MAX_MHZ * 1e6
 # DRAM bytes (read + write) per MSC half-sweep launch of this workload, from one
 # ncu capture of the current kernel (profiles/k_half_sweep_msc32_ising_batch.md):
 # 179 MB read (both colour planes once) + 51.7 MB written (changed words only).
 # Set to None whenever the kernel changes until it is captured again.
-MSC_TRAFFIC_PER_LAUNCH = 230.6e6
+MSC_TRAFFIC_PER_LAUNCH = 230.2e6
 
 
 def log(*a):
@@ -323,12 +331,16 @@ def run_su2(mc, torch, rank, K, world):
     except (OSError, KeyError, ValueError):
         pass
     achieved_bw = SU2_BYTES_PER_UPDATE * per_launch_updates / (phase_ms / 1e3)
+    alu = SU2_INSTR_PER_UPDATE * per_launch_updates / (phase_ms / 1e3)
     return {"metric": "SU(2) link-updates/s", "value": updates / (ms / 1e3), "unit": "link-updates/s",
             "workload": f"4D SU(2) {SU2_L}^4, beta in {SU2_BETAS}, hot start, heat-bath (KP+Creutz), plaquette "
                         "every sweep", "steps": K, "ms_per_sweep": ms / K, "phase_kernel_ms": phase_ms,
             "last_plaquette": P,
             "roofline_hbm": {"achieved": achieved_bw, "peak": hbm, "unit": "B/s", "frac": achieved_bw / hbm,
-                             "bytes_per_update": SU2_BYTES_PER_UPDATE}}
+                             "bytes_per_update": SU2_BYTES_PER_UPDATE},
+            "roofline_alu": {"bound": "alu", "achieved": alu, "peak": ISSUE_PEAK, "unit": "thread-instr/s",
+                             "frac": alu / ISSUE_PEAK, "instr_per_update": SU2_INSTR_PER_UPDATE,
+                             "note": "the slower bound: phase kernel at its algorithmic issue count"}}
 
 
 def run_batched(mc, torch, rank, K, world, sweeps_per_call=10):

@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
                                         P, P]
             L.orc_su2_sweep.restype = c.c_long
             L.orc_su2_plaquette.argtypes = [P, P, P]
+            L.orc_su2_overrelax.argtypes = [P, P]
             L.orc_su2_action.argtypes = [P, P, c.c_double]
             L.orc_su2_action.restype = c.c_double
             L.orc_su2_staple.argtypes = [P, P, c.c_long, c.c_int, P]
@@ -167,6 +168,13 @@ def su2_sweep(q: np.ndarray, L, beta: float, seed: int, chain: int, sweep: int,
     fails = lib().orc_su2_sweep(_ptr(q), _ptr(d), float(beta), seed, chain, sweep, _ptr(tries), f, float(eps),
                                 ctypes.byref(near), ctypes.byref(bad))
     return tries, int(fails), int(near.value), int(bad.value)
+
+
+def su2_overrelax(q: np.ndarray, L) -> None:
+    """One overrelaxation sweep in place (orc_su2_overrelax)."""
+    d = _dims(L)
+    assert q.dtype == np.float64 and q.flags["C_CONTIGUOUS"]
+    lib().orc_su2_overrelax(_ptr(q), _ptr(d))
 
 
 def su2_plaquette(q: np.ndarray, L) -> np.ndarray:

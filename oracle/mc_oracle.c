@@ -567,6 +567,45 @@ ORC_API long orc_su2_sweep(double *q, const int L[4], double beta, uint64_t seed
     return failures;
 }
 
+/* Overrelaxation, the second half of the "heat-bath algorithm with
+ * overrelaxation" of Sec. 2.4 (the method of Creutz, Phys. Rev. D 36 (1987)
+ * 515): the link is replaced by its reflection within the SU(2) matrices of
+ * equal local action,
+ *   U' = V U^dag V,  V = W / sqrt(det W),
+ * so that Re Tr(U' W^dag) = k Re Tr(V U^dag) = Re Tr(U W^dag): the move is
+ * microcanonical, needs no random number and is its own inverse (X = U V^dag
+ * goes to X^dag).  A link whose staple vanishes is left unchanged.  The link is
+ * reprojected (U / sqrt(det U)) like a heat-bath update.
+ * READING: the paper names the combination but not the number of reflections
+ * per heat-bath step; here a compound sweep is one heat-bath sweep followed by
+ * n_or overrelaxation sweeps (a run-time parameter, like the paper's "number of
+ * link updates per one MC sweep"), each in the heat-bath's phase order. */
+static void overrelax_link(su2_lattice *lat, long s, int mu)
+{
+    mat2 W = staple(lat, s, mu);
+    double k = sqrt(fmax(0.0, creal(mat_det(W))));
+    if (!(k > 0.0))
+        return;
+    mat2 V = mat_scale(W, 1.0 / k);
+    mat2 U = mat_mul(mat_mul(V, mat_dag(*link(lat, s, mu))), V);
+    *link(lat, s, mu) = mat_scale(U, 1.0 / sqrt(creal(mat_det(U))));
+}
+
+/* One overrelaxation sweep in the phase order of orc_su2_sweep. */
+ORC_API void orc_su2_overrelax(double *q, const int L[4])
+{
+    su2_lattice lat;
+    load_lattice(&lat, L, q);
+    const int parity_order[2] = {1, 0};
+    for (int pi = 0; pi < 2; ++pi)
+        for (int mu = 0; mu < 4; ++mu)
+            for (long s = 0; s < lat.nsites; ++s)
+                if (site_parity(L, s) == parity_order[pi])
+                    overrelax_link(&lat, s, mu);
+    store_lattice(&lat, q);
+    free_lattice(&lat);
+}
+
 /* Plaquette averages of Eqs. (2)-(3): (1/2) Tr U_munu(x) with
  * U_munu(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag, averaged over all
  * 6 N plaquettes (out[0]), the 3 N spatial ones, mu, nu in {1,2,3} (out[1]) and

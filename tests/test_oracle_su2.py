@@ -220,3 +220,74 @@ def test_forced_tries_protocol(orc):
     c = q0.copy()
     _, _, near, bad = orc.su2_sweep(c, L, 2.0, 3, 0, 0, forced_tries=planted)
     assert bad >= 1
+
+
+# ------------------------------------------------------------------ overrelaxation
+def _gauge_transform(orc, q, L, g):
+    """U_mu(x) -> g(x) U_mu(x) g(x + mu)^dag."""
+    ns = int(np.prod(L))
+
+    def shifted(s, mu):
+        x1 = s % L[1]; r = s // L[1]
+        x2 = r % L[2]; r //= L[2]
+        x3 = r % L[3]; x0 = r // L[3]
+        x = [x0, x1, x2, x3]
+        x[mu] = (x[mu] + 1) % L[mu]
+        return x[1] + L[1] * (x[2] + L[2] * (x[3] + L[3] * x[0]))
+
+    out = np.empty_like(q)
+    for s in range(ns):
+        for mu in range(4):
+            gd = g[shifted(s, mu)] * np.array([1, -1, -1, -1])
+            out[s, mu] = orc.su2_mul(orc.su2_mul(g[s], q[s, mu]), gd)
+    return out
+
+
+@pytest.mark.parametrize("L", [[4, 4, 4, 4], [2, 4, 6, 4]])
+def test_overrelaxation_preserves_the_action(orc, L):
+    """Each reflection keeps Re Tr(U W^dag), the only part of the Wilson action
+    (Eq. (2)) that depends on the link, so a whole overrelaxation sweep leaves
+    the action unchanged while moving every link."""
+    q = orc.su2_init(L, seed=11, hot=True)
+    q0 = q.copy()
+    S0 = orc.su2_action(q, L, 2.3)
+    for _ in range(3):
+        orc.su2_overrelax(q, L)
+        assert abs(orc.su2_action(q, L, 2.3) - S0) < 1e-11 * abs(S0)
+    assert np.abs(q - q0).max() > 0.5  # it is not the identity
+    np.testing.assert_allclose(np.linalg.norm(q.reshape(-1, 4), axis=1), 1.0, atol=1e-14)
+
+
+def test_overrelaxation_is_gauge_covariant(orc):
+    """Reflecting then gauge transforming equals gauge transforming then
+    reflecting: fixes the orientation of the staple and of the reflection
+    (V^dag U^dag V^dag, say, keeps neither the action nor this)."""
+    L = [4, 4, 2, 4]
+    rng = np.random.default_rng(12)
+    ns = int(np.prod(L))
+    q = random_unit_quats(rng, ns * 4).reshape(ns, 4, 4).copy()
+    g = random_unit_quats(rng, ns)
+    a = q.copy()
+    orc.su2_overrelax(a, L)
+    a = _gauge_transform(orc, a, L, g)
+    b = _gauge_transform(orc, q, L, g)
+    orc.su2_overrelax(b, L)
+    np.testing.assert_allclose(a, b, atol=1e-12)
+
+
+def test_heatbath_with_overrelaxation_strong_coupling(orc):
+    """One heat-bath plus two overrelaxation sweeps per step still samples the
+    Wilson measure: the strong-coupling plaquette I2(b)/I1(b) at b = 0.2."""
+    L = [4, 4, 4, 4]
+    beta = 0.2
+    q = orc.su2_init(L, seed=13, hot=True)
+    P = []
+    for k in range(1800):
+        orc.su2_sweep(q, L, beta, 13, 0, k)
+        orc.su2_overrelax(q, L)
+        orc.su2_overrelax(q, L)
+        if k >= 300:
+            P.append(orc.su2_plaquette(q, L)[0])
+    mean, err = binned_mean_err(P, 20)
+    want = exact.strong_coupling_plaquette(beta)
+    assert abs(mean - want) < 4.5 * err + 1e-4, (mean, want, err)

@@ -168,6 +168,19 @@ MC_API mc_status mc_su2_get_tries(mc_ctx *ctx, int32_t chain, uint8_t *host_dst)
  * every heat-bath try was rejected (link kept; still exact).  Synchronous. */
 MC_API mc_status mc_su2_failed_updates(mc_ctx *ctx, int64_t *count);
 
+/* Overrelaxation (Sec. 2.4: "heat-bath algorithm with overrelaxation"): from
+ * the next mc_sweep on, every sweep of every chain of an SU(2) context is one
+ * heat-bath sweep followed by n_or overrelaxation sweeps, 0 <= n_or <= 64
+ * (default 0), each in the heat-bath's phase order (odd sites mu = 0..3, then
+ * even sites).  An overrelaxation update replaces U_mu(x) by V U^dag V with
+ * V = W / |W| (W the staple of Eq. (6)): it keeps the action, uses no random
+ * numbers and leaves a link with W = 0 unchanged.  The sweep counter and the
+ * measurement cadence count compound sweeps.  MC_EINVAL for an Ising context
+ * or n_or out of range.  The paper does not fix n_or; it calls the run-time
+ * choice the "number of link updates per one MC sweep". */
+MC_API mc_status mc_su2_set_overrelax(mc_ctx *ctx, int32_t n_or);
+MC_API mc_status mc_su2_get_overrelax(mc_ctx *ctx, int32_t *n_or);
+
 /* Kernel timing.  While enabled, sweeps are enqueued without CUDA graphs and
  * every launch of a sweep kernel (Ising half-sweep, SU(2) (parity, mu) phase)
  * is bracketed by CUDA events recorded on the context stream. */

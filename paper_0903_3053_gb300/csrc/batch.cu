@@ -42,6 +42,8 @@ struct GroupMember {
     long long cap;
     int kind;
     int layout;
+    int n_or; // SU(2): overrelaxation sweeps after each heat-bath sweep (from the context)
+    int pad;
 };
 
 struct GroupArgs {
@@ -167,6 +169,12 @@ __device__ void run_su2(const GroupMember &m, int chain, int item, int G, int ra
                 su2_update_link_rt<kLdCoherent>(phase, U, ch, ks, e, sweep, m.state);
             group_barrier(G, cluster);
         }
+        for (int r = 0; r < m.n_or; ++r) // overrelaxation sweeps, same phase order
+            for (int phase = 0; phase < 8; ++phase) {
+                for (uint32_t e = start; e < ch.nh; e += stride)
+                    su2_overrelax_link_rt<kLdCoherent>(phase, U, ch, e);
+                group_barrier(G, cluster);
+            }
         if (g.every != 0 && ((t + 1) % g.every) == 0) {
             long long ps = 0, pt = 0;
             for (uint32_t s = start; s < 2 * ch.nh; s += stride) {
@@ -257,6 +265,7 @@ struct mc_group {
     std::vector<int32_t> rounds;
     std::vector<uint8_t> round_shared;
     bool planned = false;
+    std::vector<GroupMember> hm; // host copy of d_members
     std::map<std::tuple<long long, int>, cudaGraphExec_t> graphs;
 };
 
@@ -273,7 +282,7 @@ double item_cost(const mc_ctx *c, int k)
 {
     if (c->kind == MC_KIND_SU2) {
         const Su2Chain &ch = c->su2[k];
-        return 60.0 * 8.0 * ch.nh; // 4 N link updates
+        return 60.0 * 8.0 * ch.nh * (1.0 + 0.6 * c->n_or); // 4 N heat-bath (+ cheaper overrelaxation) updates
     }
     const IsingChain &ch = c->ising[k];
     return (c->layout == MC_LAYOUT_INT8 ? 2.0 : 1.0) * ch.Lx * ch.Ly;
@@ -482,7 +491,8 @@ mc_status mc_group_create(mc_group **out, int32_t n_ctx, mc_ctx *const *ctxs, vo
     std::vector<GroupMember> hm;
     for (int i = 0; i < n_ctx; ++i) {
         const mc_ctx *c = ctxs[i];
-        hm.push_back(GroupMember{c->d_chains, c->d_lattice, c->d_series, c->d_state, c->cap, c->kind, c->layout});
+        hm.push_back(GroupMember{c->d_chains, c->d_lattice, c->d_series, c->d_state, c->cap, c->kind, c->layout,
+                                 c->n_or, 0});
         for (int k = 0; k < c->n_chains; ++k) {
             g->items.push_back(make_int2(i, k));
             g->cost.push_back(item_cost(c, k));
@@ -502,8 +512,9 @@ mc_status mc_group_create(mc_group **out, int32_t n_ctx, mc_ctx *const *ctxs, vo
         e = cudaEventCreateWithFlags(&g->fence_in, cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&g->fence_out, cudaEventDisableTiming);
+    g->hm = hm;
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(g->d_members, hm.data(), hm.size() * sizeof(GroupMember), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(g->d_members, g->hm.data(), hm.size() * sizeof(GroupMember), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->d_items, g->items.data(), g->items.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
@@ -548,6 +559,22 @@ mc_status mc_group_sweep(mc_group *g, int64_t n_sweeps, int32_t measure_every)
             return gfail(MC_EINVAL, "a member's measurement ring buffer would overflow");
         if (c->sweeps_done + n_sweeps > 0xFFFFFFFFll)
             return gfail(MC_EINVAL, "sweep counter would exceed 2^32");
+    }
+    bool or_changed = false; // a member context changed its overrelaxation count since the last call
+    for (size_t i = 0; i < g->members.size(); ++i)
+        if (g->hm[i].n_or != g->members[i]->n_or) {
+            g->hm[i].n_or = g->members[i]->n_or;
+            or_changed = true;
+        }
+    if (or_changed) {
+        cudaError_t e = cudaMemcpyAsync(g->d_members, g->hm.data(), g->hm.size() * sizeof(GroupMember),
+                                        cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess)
+            return gfail(MC_ECUDA, std::string("update group members: ") + cudaGetErrorString(e));
+        g->planned = false;
+        destroy_group_graphs(g);
     }
     if (!g->planned) {
         mc_status s = plan(g);

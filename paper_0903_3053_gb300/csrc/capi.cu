@@ -268,7 +268,7 @@ mc_status run_chunk(mc_ctx *c, long long n, int every, int mode)
     // Graphs are recorded and replayed on a private stream (capture is not
     // permitted on the legacy default stream a caller may pass), fenced with
     // events against the caller's stream so stream order is preserved.
-    const auto key = std::make_tuple(n, every, mode, c->threads, c->record_tries);
+    const auto key = std::make_tuple(n, every, mode, c->threads, c->record_tries, c->n_or);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -709,6 +709,29 @@ mc_status mc_su2_record_tries(mc_ctx *c, int32_t enable)
         c->record_tries = enable != 0;
         destroy_graphs(c);
     }
+    return MC_OK;
+}
+
+mc_status mc_su2_set_overrelax(mc_ctx *c, int32_t n_or)
+{
+    if (!c)
+        return fail(MC_EINVAL, "ctx is NULL");
+    if (c->kind != MC_KIND_SU2)
+        return fail(MC_EINVAL, "overrelaxation applies to SU(2) contexts");
+    if (n_or < 0 || n_or > kMaxOverrelax)
+        return fail(MC_EINVAL, "n_or must be in [0, " + std::to_string(kMaxOverrelax) + "]");
+    if (n_or != c->n_or) {
+        c->n_or = n_or;
+        destroy_graphs(c);
+    }
+    return MC_OK;
+}
+
+mc_status mc_su2_get_overrelax(mc_ctx *c, int32_t *n_or)
+{
+    if (!c || !n_or)
+        return fail(MC_EINVAL, "ctx or n_or is NULL");
+    *n_or = c->n_or;
     return MC_OK;
 }
 

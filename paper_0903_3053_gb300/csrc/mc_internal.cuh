@@ -18,6 +18,7 @@ namespace mc {
 
 constexpr int kMaxChains = 4096;
 constexpr int kDefaultThreads = 256;
+constexpr int kMaxOverrelax = 64;   // overrelaxation sweeps per heat-bath sweep
 constexpr size_t kAlign = 256;
 
 // Per-chain descriptor of a 2D Ising chain, resident in the workspace.
@@ -162,7 +163,8 @@ struct mc_ctx {
     int mode = MC_MODE_AUTO;
     int threads = mc::kDefaultThreads;
     bool record_tries = false;
-    std::map<std::tuple<long long, int, int, int, bool>, cudaGraphExec_t> graphs;
+    int n_or = 0;                        // SU(2): overrelaxation sweeps after each heat-bath sweep
+    std::map<std::tuple<long long, int, int, int, bool, int>, cudaGraphExec_t> graphs;
     // kernel timing (mc_profile_enable)
     bool profiling = false;
     std::vector<cudaEvent_t> events; // pairs: [2i] before, [2i+1] after launch i

@@ -47,6 +47,20 @@ __global__ void __launch_bounds__(256, 6) k_phase(SweepArgs a)
     su2_update_link<P, MU, kLdReadOnly, REC>(U, ch, ks, e, (uint32_t)(a.state->sweep_base + a.k), a.tries, a.state);
 }
 
+// Overrelaxation phase: same thread layout as k_phase, no random numbers.
+template <int P, int MU>
+__global__ void __launch_bounds__(256, 6) k_or_phase(SweepArgs a)
+{
+    const uint32_t b = blockIdx.x + a.block_base;
+    const int k = find_chain(a.block_start, a.n_chains, b);
+    const Su2Chain ch = static_cast<const Su2Chain *>(a.chains)[k];
+    const uint32_t e = (b - a.block_start[k]) * blockDim.x + threadIdx.x;
+    if (e >= ch.nh)
+        return;
+    float4 *U = reinterpret_cast<float4 *>(a.lattice + ch.link_off);
+    su2_overrelax_link<P, MU, kLdReadOnly>(U, ch, e);
+}
+
 // ------------------------------------------------------------------ plaquette
 // Per-block partial sums of (1/2) Tr U_munu(x) of Eq. (3), spatial and temporal
 // separately (the two values per measuring thread of Sec. 2.4).  Products in
@@ -210,6 +224,20 @@ void launch_phase(mc_ctx *c, const SweepArgs &a, int mu, unsigned nblocks)
     prof_end(c);
 }
 
+template <int P>
+void launch_or_phase(mc_ctx *c, const SweepArgs &a, int mu, unsigned nblocks)
+{
+    if (prof_begin(c) != cudaSuccess)
+        return;
+    switch (mu) {
+    case 0: k_or_phase<P, 0><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 1: k_or_phase<P, 1><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    case 2: k_or_phase<P, 2><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    default: k_or_phase<P, 3><<<nblocks, c->threads, 0, c->ls>>>(a); break;
+    }
+    prof_end(c);
+}
+
 }  // namespace
 
 // =========================================================================== host
@@ -284,6 +312,12 @@ cudaError_t su2_sweep_enqueue(mc_ctx *c, long long n, int every)
                 launch_phase<1>(c, a, mu, nb); // odd sites first (Sec. 2.4)
             for (int mu = 0; mu < 4; ++mu)
                 launch_phase<0>(c, a, mu, nb);
+            for (int r = 0; r < c->n_or; ++r) { // overrelaxation sweeps, same phase order
+                for (int mu = 0; mu < 4; ++mu)
+                    launch_or_phase<1>(c, a, mu, nb);
+                for (int mu = 0; mu < 4; ++mu)
+                    launch_or_phase<0>(c, a, mu, nb);
+            }
             if (measure)
                 plaquette_partials(c, g.first, g.second);
         }

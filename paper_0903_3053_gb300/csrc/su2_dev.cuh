@@ -168,7 +168,10 @@ __device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, 
 // reprojection.  REC: store the try taken at tries[2 e + b][MU] (canonical
 // site 2 e + b, b the parity bit of x1); a separate instantiation so that the
 // sweeps that do not record keep no extra state live across the heat-bath loop.
-template <int P, int MU, int LD, bool REC>
+// INLINE_FAIL: count a failed update with an inlined atomic (the persistent
+// batch kernel, where the out-of-line call costs a stack frame) instead of
+// count_heatbath_failure.
+template <int P, int MU, int LD, bool REC, bool INLINE_FAIL = false>
 __device__ __forceinline__ void su2_update_link(float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
                                                 uint32_t sweep, uint8_t *tries, DevState *state)
 {
@@ -194,7 +197,10 @@ __device__ __forceinline__ void su2_update_link(float4 *U, const Su2Chain &ch, c
     if (REC)
         tries[ch.tries_off + (size_t)s * 4 + MU] = (uint8_t)t;
     if (t == kFailed) {
-        count_heatbath_failure(state);
+        if (INLINE_FAIL)
+            atomicAdd(&state->hb_failures, 1ull);
+        else
+            count_heatbath_failure(state);
         return;
     }
     const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ks);
@@ -210,20 +216,62 @@ __device__ __forceinline__ void su2_update_link(float4 *U, const Su2Chain &ch, c
     U[(size_t)(P * 4 + MU) * ch.nh + e] = Un;
 }
 
-// Runtime (P, MU) dispatch of su2_update_link (no try record).
+// Overrelaxation of the link U_MU(x) at site e of parity P (the
+// "overrelaxation" of Sec. 2.4's heat-bath with overrelaxation): the
+// reflection U' = V U^dag V, V = W / |W|, keeps Re Tr(U W^dag) and so the
+// action; deterministic, no random numbers.  A vanishing staple leaves the link
+// as it is.  The result is reprojected onto SU(2).
+template <int P, int MU, int LD>
+__device__ __forceinline__ void su2_overrelax_link(float4 *U, const Su2Chain &ch, uint32_t e)
+{
+    float4 V;
+    {
+        const Site x = site_from_parity_index(ch, P, e);
+        const uint32_t sc = canonical(ch, x);
+        const float4 W = staple<MU, P, LD>(U, ch, x, sc, e);
+        const float k2 = qdot(W, W);
+        if (!(k2 > 0.f))
+            return;
+        const float inv = 1.0f / sqrtf(k2);
+        V = make_float4(W.x * inv, W.y * inv, W.z * inv, W.w * inv);
+    }
+    float4 *dst = &U[(size_t)(P * 4 + MU) * ch.nh + e];
+    const float4 u = lat_load<LD>(dst);
+    float4 Un = qmul(qmul(V, qdag(u)), V);
+    const float nrm = rsqrtf(qdot(Un, Un));
+    *dst = make_float4(Un.x * nrm, Un.y * nrm, Un.z * nrm, Un.w * nrm);
+}
+
+template <int LD>
+__device__ __forceinline__ void su2_overrelax_link_rt(int phase, float4 *U, const Su2Chain &ch, uint32_t e)
+{
+    switch (phase) {
+    case 0: su2_overrelax_link<1, 0, LD>(U, ch, e); break;
+    case 1: su2_overrelax_link<1, 1, LD>(U, ch, e); break;
+    case 2: su2_overrelax_link<1, 2, LD>(U, ch, e); break;
+    case 3: su2_overrelax_link<1, 3, LD>(U, ch, e); break;
+    case 4: su2_overrelax_link<0, 0, LD>(U, ch, e); break;
+    case 5: su2_overrelax_link<0, 1, LD>(U, ch, e); break;
+    case 6: su2_overrelax_link<0, 2, LD>(U, ch, e); break;
+    default: su2_overrelax_link<0, 3, LD>(U, ch, e); break;
+    }
+}
+
+// Runtime (P, MU) dispatch of su2_update_link for the persistent batch kernel
+// (no try record, inlined failure count).
 template <int LD>
 __device__ __forceinline__ void su2_update_link_rt(int phase, float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks,
                                                    uint32_t e, uint32_t sweep, DevState *state)
 {
     switch (phase) { // phase = position in the sweep: (odd, mu = 0..3), then (even, mu = 0..3)
-    case 0: su2_update_link<1, 0, LD, false>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 1: su2_update_link<1, 1, LD, false>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 2: su2_update_link<1, 2, LD, false>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 3: su2_update_link<1, 3, LD, false>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 4: su2_update_link<0, 0, LD, false>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 5: su2_update_link<0, 1, LD, false>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 6: su2_update_link<0, 2, LD, false>(U, ch, ks, e, sweep, nullptr, state); break;
-    default: su2_update_link<0, 3, LD, false>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 0: su2_update_link<1, 0, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 1: su2_update_link<1, 1, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 2: su2_update_link<1, 2, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 3: su2_update_link<1, 3, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 4: su2_update_link<0, 0, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 5: su2_update_link<0, 1, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 6: su2_update_link<0, 2, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
+    default: su2_update_link<0, 3, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
     }
 }
 

@@ -105,3 +105,28 @@ def test_batched_workload_autotuned():
             np.testing.assert_array_equal(one.get_config(0), b.get_config(k))
             one.close()
     g.close()
+
+
+def test_group_with_overrelaxation_matches_contexts():
+    """SU(2) members with overrelaxation: the persistent launch gives the same
+    links and plaquettes as the context's own compound sweeps, also after the
+    count changes between calls."""
+    def make():
+        return mc.Batch([mc.su2((4, 4, 4, 4), 2.3, seed=41, chain_id=0), mc.su2((6, 4, 4, 8), 2.0, seed=42, chain_id=1)],
+                        series_capacity=16)
+    ref = make()
+    ref.set_mode(mc.MC_MODE_GRID, 256)
+    ref.set_overrelax(2)
+    ref.sweep(3, 1)
+    ref.set_overrelax(1)
+    ref.sweep(2, 1)
+    want = snapshot([ref])
+    b = make()
+    g = mc.Group([b])
+    g.configure(4, 256, -1.0)
+    b.set_overrelax(2)
+    g.sweep(3, 1)
+    b.set_overrelax(1)
+    g.sweep(2, 1)
+    assert_same(snapshot([b]), want)
+    g.close()

@@ -166,3 +166,64 @@ def test_plaquette_average_8x4_long_run():
     om, oe = binned_mean_err(Po, 10)
     assert abs(gm - om) < 3 * np.hypot(ge, oe) + 1e-4, (gm, ge, om, oe)
     print(f"<P> GPU {gm:.6f} +- {ge:.6f}  oracle {om:.6f} +- {oe:.6f}")
+
+
+@pytest.mark.parametrize("n_or", [1, 3])
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (6, 4, 8, 2)])
+def test_overrelaxation_per_link(L, n_or):
+    """One compound sweep (heat-bath + n_or overrelaxation sweeps) against the
+    oracle's heat-bath sweep (following the GPU's tries, as above) and n_or
+    oracle overrelaxation sweeps, from a thermalised start.  (On random links
+    the staples can be short, and a reflection about a short staple magnifies
+    FP32 round-off by ~1/|W| per sweep.)"""
+    beta = 2.3
+    q0 = oracle.su2_init(L, 9, 1, True)
+    for k in range(20):
+        oracle.su2_sweep(q0, L, beta, 9, 1, 1000 + k)
+    q0 = f32_roundtrip(q0)
+    b = mc.Batch([mc.su2(L, beta, seed=9, chain_id=1)])
+    b.set_config(0, q0.astype(np.float32))
+    b.set_overrelax(n_or)
+    assert b.overrelax() == n_or
+    b.record_tries(True)
+    b.sweep(1)
+    g = b.get_config(0).astype(np.float64)
+    q = q0.copy()
+    _, _, _, bad = oracle.su2_sweep(q, L, beta, 9, 1, 0, forced_tries=b.get_tries(0), eps=EPS)
+    assert bad == 0
+    for _ in range(n_or):
+        oracle.su2_overrelax(q, L)
+    err = np.abs(g - q).max()
+    print(f"n_or={n_or}: max per-link deviation {err:.2e}")
+    assert err < TOL
+    assert b.sweeps_done == 1
+    b.close()
+
+
+def test_overrelaxation_strong_coupling_on_gpu():
+    """Heat-bath + 2 overrelaxation sweeps still samples the Wilson measure:
+    plaquette at beta = 0.2 equals I2(b)/I1(b) (closed form)."""
+    from oracle import exact
+    L, beta = (4, 4, 4, 4), 0.2
+    b = mc.Batch([mc.su2(L, beta, seed=19, chain_id=k) for k in range(32)], series_capacity=2100)
+    b.set_overrelax(2)
+    b.sweep(200, 0)
+    b.sweep(2000, 1)
+    P = b.read_series()["P"]
+    means = P.mean(axis=1)  # 32 independent chains
+    mean, err = means.mean(), means.std(ddof=1) / np.sqrt(len(means))
+    want = exact.strong_coupling_plaquette(beta)
+    assert abs(mean - want) < 4.5 * err + 1e-4, (mean, want, err)
+    b.close()
+
+
+def test_overrelaxation_argument_checks():
+    b = mc.Batch([mc.su2((4, 4, 4, 4), 2.0, seed=1)])
+    for bad in (-1, 65):
+        with pytest.raises(mc.MCError):
+            b.set_overrelax(bad)
+    b.close()
+    i = mc.Batch([mc.ising(8, 0.4, seed=1)])
+    with pytest.raises(mc.MCError):
+        i.set_overrelax(1)
+    i.close()

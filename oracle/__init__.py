@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
             L.orc_su2_sweep.restype = c.c_long
             L.orc_su2_plaquette.argtypes = [P, P, P]
             L.orc_su2_overrelax.argtypes = [P, P]
+            L.orc_su2_polyakov.argtypes = [P, P]
+            L.orc_su2_polyakov.restype = c.c_double
             L.orc_su2_action.argtypes = [P, P, c.c_double]
             L.orc_su2_action.restype = c.c_double
             L.orc_su2_staple.argtypes = [P, P, c.c_long, c.c_int, P]
@@ -175,6 +177,12 @@ def su2_overrelax(q: np.ndarray, L) -> None:
     d = _dims(L)
     assert q.dtype == np.float64 and q.flags["C_CONTIGUOUS"]
     lib().orc_su2_overrelax(_ptr(q), _ptr(d))
+
+
+def su2_polyakov(q: np.ndarray, L) -> float:
+    """Volume-averaged Polyakov loop (1/2) Tr prod_t U_0(t, x) (FP64)."""
+    d = _dims(L)
+    return float(lib().orc_su2_polyakov(_ptr(np.ascontiguousarray(q, dtype=np.float64)), _ptr(d)))
 
 
 def su2_plaquette(q: np.ndarray, L) -> np.ndarray:

@@ -634,6 +634,29 @@ ORC_API void orc_su2_plaquette(const double *q, const int L[4], double out[3])
     free_lattice(&lat);
 }
 
+/* Polyakov loop (an observable the paper does not measure; it pairs with the
+ * finite-temperature lattices L_t x L_s^3 of Sec. 2.4): for every spatial site
+ * x, (1/2) Tr of the ordered product U_0(0, x) U_0(1, x) ... U_0(L_0 - 1, x) of
+ * the time-direction links, averaged over the L_1 L_2 L_3 spatial sites.
+ * Gauge invariant; changes sign under the centre transformation that flips
+ * every U_0 on one time slice. */
+ORC_API double orc_su2_polyakov(const double *q, const int L[4])
+{
+    su2_lattice lat;
+    load_lattice(&lat, L, q);
+    long nspace = (long)L[1] * L[2] * L[3];
+    double sum = 0.0;
+    for (long xs = 0; xs < nspace; ++xs) {
+        /* canonical index s = x1 + L1 (x2 + L2 (x3 + L3 x0)): the spatial part is xs, time adds x0 * nspace */
+        mat2 P = {1, 0, 0, 1};
+        for (int t = 0; t < L[0]; ++t)
+            P = mat_mul(P, *link(&lat, xs + (long)t * nspace, 0));
+        sum += 0.5 * creal(mat_trace(P));
+    }
+    free_lattice(&lat);
+    return sum / (double)nspace;
+}
+
 /* Wilson action of Eq. (2), S = beta sum_x sum_{mu<nu} [1 - (1/2) Tr U_munu]. */
 ORC_API double orc_su2_action(const double *q, const int L[4], double beta)
 {

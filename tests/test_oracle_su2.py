@@ -291,3 +291,33 @@ def test_heatbath_with_overrelaxation_strong_coupling(orc):
     mean, err = binned_mean_err(P, 20)
     want = exact.strong_coupling_plaquette(beta)
     assert abs(mean - want) < 4.5 * err + 1e-4, (mean, want, err)
+
+
+# ------------------------------------------------------------------ Polyakov loop
+def test_polyakov_cold_and_uniform_rotation(orc):
+    """Cold links give 1; U_0 = exp(i theta sigma_3) everywhere gives the closed
+    form cos(L_0 theta) (the loop winds L_0 times)."""
+    for L in ([4, 4, 4, 4], [6, 2, 4, 2]):
+        q = orc.su2_init(L, seed=1, hot=False)
+        assert orc.su2_polyakov(q, L) == 1.0
+        theta = 0.37
+        q[:, 0] = [math.cos(theta), 0.0, 0.0, math.sin(theta)]
+        assert orc.su2_polyakov(q, L) == pytest.approx(math.cos(L[0] * theta), abs=1e-14)
+
+
+def test_polyakov_gauge_invariance_and_centre_flip(orc):
+    """Invariant under U_mu(x) -> g(x) U_mu(x) g(x+mu)^dag (which telescopes only
+    for the time-ordered product), odd under flipping the sign of every U_0 on
+    one time slice (a centre transformation)."""
+    L = [4, 2, 4, 2]
+    rng = np.random.default_rng(14)
+    ns = int(np.prod(L))
+    q = random_unit_quats(rng, ns * 4).reshape(ns, 4, 4).copy()
+    p0 = orc.su2_polyakov(q, L)
+    g = random_unit_quats(rng, ns)
+    assert orc.su2_polyakov(_gauge_transform(orc, q, L, g), L) == pytest.approx(p0, abs=1e-13)
+    nspace = L[1] * L[2] * L[3]
+    flipped = q.copy()
+    flipped[2 * nspace:3 * nspace, 0] *= -1  # time slice x0 = 2
+    assert orc.su2_polyakov(flipped, L) == pytest.approx(-p0, abs=1e-14)
+    assert abs(p0) > 1e-4  # not trivially zero

@@ -181,6 +181,14 @@ MC_API mc_status mc_su2_failed_updates(mc_ctx *ctx, int64_t *count);
 MC_API mc_status mc_su2_set_overrelax(mc_ctx *ctx, int32_t n_or);
 MC_API mc_status mc_su2_get_overrelax(mc_ctx *ctx, int32_t *n_or);
 
+/* Polyakov loop of one SU(2) chain's current configuration: the average over
+ * the L1 L2 L3 spatial sites x of (1/2) Tr U_0(0, x) U_0(1, x) ... U_0(L0-1, x)
+ * (mu = 0 is time).  The paper measures plaquettes only (Eq. (3)); this is the
+ * order parameter of its finite-temperature lattices L_t x L_s^3 (Sec. 2.4).
+ * FP32 products, exact fixed-point sum; written to *out (host).  Synchronous;
+ * MC_EINVAL for an Ising context or a chain index out of range. */
+MC_API mc_status mc_su2_polyakov(mc_ctx *ctx, int32_t chain, double *out);
+
 /* Kernel timing.  While enabled, sweeps are enqueued without CUDA graphs and
  * every launch of a sweep kernel (Ising half-sweep, SU(2) (parity, mu) phase)
  * is bracketed by CUDA events recorded on the context stream. */

@@ -599,6 +599,29 @@ mc_status mc_measure(mc_ctx *c, int32_t chain, mc_record *out)
     return MC_OK;
 }
 
+mc_status mc_su2_polyakov(mc_ctx *c, int32_t chain, double *out)
+{
+    if (!c || !out)
+        return fail(MC_EINVAL, "NULL argument");
+    if (c->kind != MC_KIND_SU2)
+        return fail(MC_EINVAL, "the Polyakov loop is an SU(2) observable");
+    if (chain < 0 || chain >= c->n_chains)
+        return fail(MC_EINVAL, "chain index out of range");
+    DevRecord *d = c->d_scratch_rec + chain;
+    cudaError_t e = su2_polyakov_launch(c, chain, d);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "launch Polyakov loop");
+    DevRecord r;
+    e = cudaMemcpyAsync(&r, d, sizeof r, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "copy Polyakov loop");
+    mc_status s = check_device(c);
+    if (s != MC_OK)
+        return s;
+    *out = r.d0;
+    return MC_OK;
+}
+
 mc_status mc_read_series(mc_ctx *c, mc_record *dst, int64_t max_per_chain, int64_t *n_per_chain)
 {
     if (!c || !n_per_chain || (!dst && max_per_chain > 0) || max_per_chain < 0)

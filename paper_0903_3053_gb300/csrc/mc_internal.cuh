@@ -185,6 +185,7 @@ void ising_plan_grid(mc_ctx *c);
 cudaError_t su2_init_launch(mc_ctx *c, const mc_chain_desc *desc);
 cudaError_t su2_sweep_enqueue(mc_ctx *c, long long n, int every);
 cudaError_t su2_measure_launch(mc_ctx *c, int chain, DevRecord *out);
+cudaError_t su2_polyakov_launch(mc_ctx *c, int chain, DevRecord *out);
 cudaError_t su2_config_io(mc_ctx *c, int chain, void *dev_buf, bool to_lattice);
 size_t su2_config_bytes(const Su2Chain &ch);
 void su2_plan_grid(mc_ctx *c);

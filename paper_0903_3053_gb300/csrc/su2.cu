@@ -146,6 +146,63 @@ __global__ void __launch_bounds__(256) k_plaquette_final(const Su2Chain *chains,
     rec->d2 = (double)B * kPlaqUnfix / (3.0 * n);
 }
 
+// ------------------------------------------------------------------ Polyakov loop
+// One thread per spatial site xs = x1 + L1 (x2 + L2 x3): the time-ordered
+// product U_0(0, xs) ... U_0(L0 - 1, xs) of FP32 quaternions; (1/2) Tr of an
+// SU(2) quaternion is its first component.  Exact fixed-point sums as for the
+// plaquette; partial[b] per block, then one block for the chain.
+__global__ void __launch_bounds__(256) k_polyakov(Su2Chain ch, const float4 *__restrict__ U, long long *partial)
+{
+    __shared__ long long sp[8];
+    const uint32_t nspace = (uint32_t)ch.L[1] * ch.L[2] * ch.L[3];
+    const uint32_t xs = blockIdx.x * blockDim.x + threadIdx.x;
+    long long v = 0;
+    if (xs < nspace) {
+        uint32_t q1, q2, x1, x2, x3;
+        fast_divmod(xs, ch.div1, q1, x1);
+        fast_divmod(q1, ch.div2, q2, x2);
+        x3 = q2;
+        const uint32_t sp0 = (x1 + x2 + x3) & 1u;
+        float4 P = make_float4(1.f, 0.f, 0.f, 0.f);
+        for (int t = 0; t < ch.L[0]; ++t) {
+            const uint32_t s = xs + (uint32_t)t * nspace, p = (sp0 + (uint32_t)t) & 1u;
+            P = qmul(P, __ldg(&U[(size_t)(p * 4 + 0) * ch.nh + (s >> 1)]));
+        }
+        v = plaq_fixed(P.x);
+    }
+    v = warp_sum_ll(v);
+    if ((threadIdx.x & 31) == 0)
+        sp[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
+            a += sp[i];
+        partial[blockIdx.x] = a;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_polyakov_final(const long long *partial, uint32_t nb, uint32_t nspace,
+                                                        DevRecord *out)
+{
+    __shared__ long long sp[8];
+    long long a = 0;
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
+        a += partial[i];
+    a = warp_sum_ll(a);
+    if ((threadIdx.x & 31) == 0)
+        sp[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long A = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
+            A += sp[i];
+        out->a = out->b = 0;
+        out->d0 = (double)A * kPlaqUnfix / (double)nspace;
+        out->d1 = out->d2 = 0.0;
+    }
+}
+
 // ------------------------------------------------------------------ init / I/O
 // Hot start: Haar-random link = normalised 4-vector of four Box-Muller normals
 // from the Philox block (s, 0, TAG_INIT | mu, chain); cold start: identity.
@@ -324,6 +381,17 @@ cudaError_t su2_sweep_enqueue(mc_ctx *c, long long n, int every)
         if (measure)
             plaquette_final(c, (uint32_t)t, (uint32_t)((t + 1) / every - 1), -1, nullptr);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t su2_polyakov_launch(mc_ctx *c, int chain, DevRecord *out)
+{
+    const Su2Chain &ch = c->su2[chain];
+    const uint32_t nspace = (uint32_t)ch.L[1] * ch.L[2] * ch.L[3];
+    const unsigned nb = (nspace + 255) / 256;
+    const float4 *U = reinterpret_cast<const float4 *>(c->d_lattice + ch.link_off);
+    k_polyakov<<<nb, 256, 0, c->ls>>>(ch, U, c->d_partials);
+    k_polyakov_final<<<1, 256, 0, c->ls>>>(c->d_partials, nb, nspace, out);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ EXPORTS = [
     "mc_workspace_bytes", "mc_batch_init", "mc_ising_init", "mc_su2_init", "mc_sweep", "mc_set_mode", "mc_sync",
     "mc_measure", "mc_read_series", "mc_get_config", "mc_set_config", "mc_config_bytes", "mc_get_sweep",
     "mc_set_sweep", "mc_su2_record_tries", "mc_su2_get_tries", "mc_su2_failed_updates", "mc_su2_set_overrelax",
-    "mc_su2_get_overrelax", "mc_destroy",
+    "mc_su2_get_overrelax", "mc_su2_polyakov", "mc_destroy",
     "mc_last_error", "mc_version", "mc_profile_enable", "mc_profile_read", "mc_su2_plaquette_noalloc",
     "mc_group_workspace_bytes", "mc_group_create", "mc_group_configure", "mc_group_sweep", "mc_group_schedule",
     "mc_group_destroy",
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mc_su2_failed_updates": (st, [P, P]),
         "mc_su2_set_overrelax": (st, [P, c.c_int32]),
         "mc_su2_get_overrelax": (st, [P, P]),
+        "mc_su2_polyakov": (st, [P, c.c_int32, P]),
         "mc_destroy": (st, [P]),
         "mc_profile_enable": (st, [P, c.c_int32]),
         "mc_profile_read": (st, [P, P, P]),
@@ -294,6 +295,12 @@ class Batch:
         v = ctypes.c_int64()
         _check(load().mc_su2_failed_updates(self._ctx, ctypes.byref(v)))
         return int(v.value)
+
+    def polyakov(self, chain: int = 0) -> float:
+        """SU(2): volume-averaged Polyakov loop of the chain's current links."""
+        v = ctypes.c_double()
+        _check(load().mc_su2_polyakov(self._ctx, int(chain), ctypes.byref(v)))
+        return float(v.value)
 
     def set_overrelax(self, n_or: int):
         """SU(2): each sweep becomes one heat-bath sweep plus n_or overrelaxation sweeps."""

@@ -227,3 +227,41 @@ def test_overrelaxation_argument_checks():
     with pytest.raises(mc.MCError):
         i.set_overrelax(1)
     i.close()
+
+
+@pytest.mark.parametrize("L", [(4, 8, 8, 8), (2, 6, 4, 8), (8, 4, 4, 4)])
+def test_polyakov_loop_matches_oracle(L):
+    """GPU Polyakov loop of the same configuration as the oracle's: FP32 products
+    of L0 quaternions, so within ~L0 x 1e-7; cold start gives exactly 1 (within
+    the 2^-29 fixed-point quantum)."""
+    b = mc.Batch([mc.su2(L, 2.3, seed=21, chain_id=0, hot=False), mc.su2(L, 2.3, seed=21, chain_id=1, hot=True)])
+    assert abs(b.polyakov(0) - 1.0) < 1e-8
+    b.sweep(5)
+    for k in range(2):
+        q = b.get_config(k).astype(np.float64)
+        want = oracle.su2_polyakov(q, L)
+        assert abs(b.polyakov(k) - want) < 2e-6, (b.polyakov(k), want)
+    b.close()
+    i = mc.Batch([mc.ising(8, 0.4, seed=1)])
+    with pytest.raises(mc.MCError):
+        i.polyakov(0)
+    i.close()
+
+
+def test_polyakov_loop_deconfinement_signal():
+    """On an L_t = 2 lattice the loop is small in the confined phase (beta = 1.5)
+    and large in the deconfined one (beta = 2.6, above the L_t = 2 transition at
+    beta ~ 1.88): |<L>| averaged over chains, after thermalisation."""
+    def absL(beta):
+        b = mc.Batch([mc.su2((2, 8, 8, 8), beta, seed=30, chain_id=k, hot=False) for k in range(8)])
+        b.set_overrelax(1)
+        b.sweep(300, 0)
+        vals = []
+        for _ in range(20):
+            b.sweep(5, 0)
+            vals.append([abs(b.polyakov(k)) for k in range(8)])
+        b.close()
+        return float(np.mean(vals))
+    low, high = absL(1.5), absL(2.6)
+    print(f"|L| confined {low:.3f}, deconfined {high:.3f}")
+    assert low < 0.2 and high > 2.5 * low, (low, high)

@@ -211,6 +211,7 @@ def run_gb300(args):
     su2 = run_su2(mc, torch, rank, args.su2_steps, world)
     batched = run_batched(mc, torch, rank, args.batch_steps, world)
     ess_cmp = run_ess(args) if not args.no_ess else None
+    paper = run_paper_protocol(mc, torch) if not args.no_paper else None
 
     line = {
         "metric": METRIC,
@@ -251,7 +252,7 @@ def run_gb300(args):
         "e2e": e2e,
         "gpu_launches": launches + K,  # 2 half-sweeps + 1 state-advance kernel per step
         "clocks": clock_info,
-        "components": {"su2": su2, "batched": batched, "ess_beta_c": ess_cmp},
+        "components": {"su2": su2, "batched": batched, "ess_beta_c": ess_cmp, "paper_protocol": paper},
         "device": dev_props.name,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -418,6 +419,87 @@ def run_batched(mc, torch, rank, K, world, sweeps_per_call=10):
             "autotuned": {k: choice[k] for k in ("cluster", "threads", "split", "cached")}}
 
 
+# The paper's own workloads (Sec. 2.3 and Table 1), for a like-for-like table:
+# its times are for an ATI HD 4850 and are context only.
+PAPER_TABLE1_S = {(4, 8): 5.2, (4, 16): 17.9, (4, 24): 52.8, (4, 32): 120.6, (8, 16): 32.7, (8, 24): 102.3,
+                  (8, 32): 397.4}
+PAPER_ISING_S = {"sweep": 630.0, "sweep+measure": 730.0}  # 10^6 sweeps of 1024 x 512
+
+
+def run_paper_protocol(mc, torch, ising_sweeps=20000) -> dict:
+    """Ising 1024 x 512, one chain, sweeps with and without the E/M measurement
+    (the paper's 10^6 sweeps projected from `ising_sweeps`); SU(2) L_t x L_s^3
+    lattices of Table 1, one chain each at beta = 2.3, the paper's protocol of
+    1000 thermalisation sweeps then 1000 measurements 5 sweeps apart, run in
+    full, through the per-phase launches (grid) and the persistent launch
+    (group); the faster is reported."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    out = {"ising_1024x512": {}, "su2_table1": []}
+    for name, layout in (("msc32", mc.MC_LAYOUT_MSC32), ("int8", mc.MC_LAYOUT_INT8)):
+        row = {}
+        # per-colour launches from a CUDA graph; the persistent launch (one cluster for
+        # one chain) measured 3x (MSC) to 37x (int8) slower on this lattice
+        for mode in ("grid",):
+            b = mc.Batch([mc.ising((1024, 512), 0.4406868, seed=1)], layout=layout, series_capacity=ising_sweeps + 16)
+            g = mc.Group([b]) if mode == "group" else None
+            run = (lambda n, every: g.sweep(n, every)) if g else (lambda n, every: b.sweep(n, every))
+            run(200, 0)
+            run(ising_sweeps, 0)
+            t_sweep = timed(lambda: run(ising_sweeps, 0))
+            run(ising_sweeps, 1)
+            b.read_series()
+            t_meas = timed(lambda: run(ising_sweeps, 1))
+            b.read_series()
+            if g:
+                g.close()
+            b.close()
+            row[mode] = {"us_per_sweep": t_sweep * 1e6 / ising_sweeps, "us_per_sweep_measured": t_meas * 1e6 / ising_sweeps}
+        best = min(row.values(), key=lambda r: r["us_per_sweep_measured"])
+        proj = {"sweep": best["us_per_sweep"], "sweep+measure": best["us_per_sweep_measured"]}  # s per 10^6 sweeps
+        row["projected_s_per_1e6_sweeps"] = proj
+        row["speedup_vs_paper_gpu"] = {k: PAPER_ISING_S[k] / proj[k] for k in proj}
+        out["ising_1024x512"][name] = row
+    for (lt, ls), paper_s in PAPER_TABLE1_S.items():
+        L = (lt, ls, ls, ls)
+        row = {"lattice": f"{lt}x{ls}^3", "paper_gpu_s": paper_s}
+        # the persistent launch puts one chain on one cluster: only worth it for the smallest lattices
+        for mode in (("grid", "group") if ls <= 16 and lt == 4 else ("grid",)):
+            b = mc.Batch([mc.su2(L, 2.3, seed=3, chain_id=0, hot=True)], series_capacity=1100)
+            if mode == "grid":
+                run = lambda n, every: b.sweep(n, every)
+            else:
+                g = mc.Group([b])
+                run = lambda n, every: g.sweep(n, every)
+            run(5, 5)  # graph capture
+            b.read_series()
+
+            def protocol():
+                run(1000, 0)
+                run(5000, 5)
+
+            t = timed(protocol)
+            P = b.read_series()["P"][0]
+            if mode == "group":
+                g.close()
+            b.close()
+            row[mode + "_s"] = t
+            row[mode + "_mean_P"] = float(P.mean())
+        row["gb300_s"] = min(row.get("grid_s", 1e30), row.get("group_s", 1e30))
+        row["speedup_vs_paper_gpu"] = paper_s / row["gb300_s"]
+        out["su2_table1"].append(row)
+    return out
+
+
 def run_ess(args) -> dict:
     """Effective independent |M| samples per second at beta_c on 64 x 64:
     plain checkerboard Metropolis versus Metropolis interleaved 1:10 with the
@@ -496,6 +578,7 @@ def main():
     ap.add_argument("--ess-rounds", type=int, default=200)
     ap.add_argument("--ess-train-steps", type=int, default=1500)
     ap.add_argument("--no-ess", action="store_true")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper-protocol component")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

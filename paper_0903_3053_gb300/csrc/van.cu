@@ -16,6 +16,11 @@ namespace mc {
 namespace van {
 namespace {
 
+// Per-CTA partial gradient of a hidden layer (13 x 32 x 32 weights + 32 biases)
+// and the most CTAs k_dw32 is launched with.
+constexpr int kDwPart = kTapsB * kCh * kCh + kCh;
+constexpr int kMaxDwBlocks = 512;
+
 // ------------------------------------------------------------------ parameters
 // Canonical FP32 parameter layout (the same as the FP64 oracle): for each layer
 // l, W[o][i][5][5] then b[o]; cin = 1 for l = 0, cout = 1 for l = D - 1.
@@ -81,68 +86,103 @@ __global__ void k_prep_weights(const float *p, DevParams P, bf16 *wh, float *w1,
 
 // ------------------------------------------------------------------ forward
 // Layer 1: 1 -> 32 channels, mask A, ReLU.  One thread per (position, channel).
-__global__ void k_layer1_fwd(const int8_t *spins, int negate, const float *w1, const float *b1, bf16 *h1, int n,
-                             int L)
+__global__ void __launch_bounds__(256) k_layer1_fwd(const int8_t *spins, int negate, const float *w1,
+                                                    const float *b1, bf16 *h1, int n, int L)
 {
-    const size_t total = (size_t)n * L * L * kCh;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int o = (int)(i % kCh);
-        const size_t p = i / kCh;
-        const int x = (int)(p % L), y = (int)((p / L) % L);
-        const size_t b = p / ((size_t)L * L);
-        float acc = b1[o];
-#pragma unroll
-        for (int t = 0; t < kTapsA; ++t) {
-            const int yy = y + tap_dy(t), xx = x + tap_dx(t);
-            if (yy >= 0 && xx >= 0 && xx < L) {
-                const float s = (float)spins[(b * L + yy) * L + xx];
-                acc += w1[o * kTapsA + t] * (negate ? -s : s);
-            }
+    // One CTA item = one row (sample b, row y): spins of rows y-2..y staged in
+    // shared memory, zero padded; 4 threads per position, 8 channels each.
+    __shared__ float W[kTapsA * kCh]; // [t][o]: the 4 channel groups of a warp hit different banks
+    __shared__ float Bs[kCh];
+    __shared__ float S[3][kMaxL + 4];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kCh * kTapsA; i += blockDim.x)
+        W[(i % kTapsA) * kCh + i / kTapsA] = w1[i]; // w1 is [o][t]
+    if (tid < kCh)
+        Bs[tid] = b1[tid];
+    const float sg = negate ? -1.f : 1.f;
+    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
+        const int b = item / L, y = item - b * L;
+        __syncthreads();
+        for (int i = tid; i < 3 * (L + 4); i += blockDim.x) {
+            const int r = i / (L + 4), xx = i - r * (L + 4) - 2, yy = y - 2 + r;
+            S[r][xx + 2] = (yy >= 0 && xx >= 0 && xx < L) ? sg * (float)spins[((size_t)b * L + yy) * L + xx] : 0.f;
         }
-        h1[i] = __float2bfloat16(fmaxf(acc, 0.f));
+        __syncthreads();
+        for (int j = tid; j < L * 4; j += blockDim.x) {
+            const int x = j >> 2, o0 = (j & 3) * 8;
+            float acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                acc[q] = Bs[o0 + q];
+#pragma unroll
+            for (int t = 0; t < kTapsA; ++t) {
+                const float v = S[tap_dy(t) + 2][x + tap_dx(t) + 2];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    acc[q] += W[t * kCh + o0 + q] * v;
+            }
+            uint4 pk;
+            uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(fmaxf(acc[2 * q], 0.f), fmaxf(acc[2 * q + 1], 0.f));
+                pw[q] = *reinterpret_cast<const uint32_t *>(&h2);
+            }
+            *reinterpret_cast<uint4 *>(h1 + (((size_t)b * L + y) * L + x) * kCh + o0) = pk;
+        }
     }
 }
 
+// Rows per CTA item of the 32-channel convolutions: enough rows that all 8
+// warps get a 16-position tile (L = 64: 2 rows, L = 32: 4).
+__host__ __device__ __forceinline__ int conv_rows(int L)
+{
+    const int nw = (L + 15) / 16;
+    return nw >= 8 ? 1 : 8 / nw;
+}
+
 // 32 -> 32 masked convolution on the tensor cores (forward): out =
-// ReLU(conv(in) + bias).  One CTA row item (sample b, row y) at a time; warp w
-// computes positions 16 w .. 16 w + 15 for all 32 output channels: K = 13 taps
-// x 32 input channels in 26 k16 steps.
+// ReLU(conv(in) + bias).  One CTA item = R = conv_rows(L) consecutive rows of
+// one sample (rows y0-2 .. y0+R-1 staged); warp w computes row y0 + w / NW,
+// positions 16 (w % NW) .. +15, for all 32 output channels: K = 13 taps x 32
+// input channels in 26 k16 steps.
 __global__ void __launch_bounds__(256) k_conv32(const bf16 *__restrict__ in, bf16 *__restrict__ out,
                                                 const bf16 *__restrict__ W, const float *__restrict__ bias, int n,
                                                 int L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     bf16 *Ws = reinterpret_cast<bf16 *>(smem);      // [13][32 o][40]
-    bf16 *Xs = Ws + kTapsB * kCh * kRowStride;       // [3][PX][40]
-    const int NW = (L + 15) / 16, PX = NW * 16 + 4;
+    bf16 *Xs = Ws + kTapsB * kCh * kRowStride;       // [R + 2][PX][40]
+    const int NW = (L + 15) / 16, PX = NW * 16 + 4, R = conv_rows(L), YB = (L + R - 1) / R;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rr = warp / NW, pt = warp - rr * NW; // this warp's row within the item and position tile
     for (int i = tid; i < kTapsB * kCh * kCh; i += blockDim.x) {
         const int t = i / (kCh * kCh), r = (i / kCh) % kCh, q = i % kCh; // W[t][o = r][c = q]
         Ws[(t * kCh + r) * kRowStride + q] = W[i];
     }
-    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
-        const int b = item / L, y = item % L;
+    for (int item = blockIdx.x; item < n * YB; item += gridDim.x) {
+        const int b = item / YB, y0 = (item - b * YB) * R, y = y0 + rr;
         __syncthreads(); // weights ready / previous item's reads done
-        for (int i = tid; i < 3 * PX * 4; i += blockDim.x) {
+        for (int i = tid; i < (R + 2) * PX * 4; i += blockDim.x) {
             const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
-            const int yy = y - 2 + r, xx = xi - 2;
+            const int yy = y0 - 2 + r, xx = xi - 2;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (yy >= 0 && xx >= 0 && xx < L)
+            if (yy >= 0 && yy < L && xx >= 0 && xx < L)
                 v = *reinterpret_cast<const uint4 *>(in + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8);
             *reinterpret_cast<uint4 *>(Xs + (r * PX + xi) * kRowStride + ch * 8) = v;
         }
         __syncthreads();
-        if (warp < NW) {
+        if (rr < R && y < L) {
             float acc[4][4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-            const int x0 = warp * 16;
+            const int x0 = pt * 16;
             const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
             const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
 #pragma unroll 1
             for (int t = 0; t < kTapsB; ++t) {
-                const int r = tap_dy(t) + 2, xoff = tap_dx(t);
+                const int r = tap_dy(t) + 2 + rr, xoff = tap_dx(t);
 #pragma unroll
                 for (int kc = 0; kc < 2; ++kc) {
                     uint32_t a0, a1, a2, a3;
@@ -209,21 +249,22 @@ __global__ void __launch_bounds__(256) k_conv32_bwd(const float *__restrict__ dz
                                                     int n, int L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int NW = (L + 15) / 16, PX = NW * 16 + 4;
+    const int NW = (L + 15) / 16, PX = NW * 16 + 4, R = conv_rows(L), YB = (L + R - 1) / R;
     bf16 *Ws = reinterpret_cast<bf16 *>(smem);      // [13][32 c][40]  (W transposed)
-    bf16 *Xh = Ws + kTapsB * kCh * kRowStride;       // [3][PX][40] hi
-    bf16 *Xl = Xh + 3 * PX * kRowStride;             // [3][PX][40] lo
+    bf16 *Xh = Ws + kTapsB * kCh * kRowStride;       // [R + 2][PX][40] hi
+    bf16 *Xl = Xh + (R + 2) * PX * kRowStride;       // [R + 2][PX][40] lo
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rr = warp / NW, pt = warp - rr * NW;
     for (int i = tid; i < kTapsB * kCh * kCh; i += blockDim.x) {
         const int t = i / (kCh * kCh), r = (i / kCh) % kCh, q = i % kCh; // W[t][o = r][c = q]
         Ws[(t * kCh + q) * kRowStride + r] = W[i];
     }
-    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
-        const int b = item / L, y = item % L;
+    for (int item = blockIdx.x; item < n * YB; item += gridDim.x) {
+        const int b = item / YB, y0 = (item - b * YB) * R, y = y0 + rr;
         __syncthreads();
-        for (int i = tid; i < 3 * PX * 4; i += blockDim.x) {
+        for (int i = tid; i < (R + 2) * PX * 4; i += blockDim.x) {
             const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
-            const int yy = y + r, xx = xi - 2;
+            const int yy = y0 + r, xx = xi - 2;
             const bool ok = yy < L && xx >= 0 && xx < L;
             bf16 hi[8], lo[8];
             stage_split(dz + (((size_t)b * L + (ok ? yy : 0)) * L + (ok ? xx : 0)) * kCh + ch * 8, ok, hi, lo);
@@ -231,17 +272,17 @@ __global__ void __launch_bounds__(256) k_conv32_bwd(const float *__restrict__ dz
             *reinterpret_cast<uint4 *>(Xl + (r * PX + xi) * kRowStride + ch * 8) = *reinterpret_cast<uint4 *>(lo);
         }
         __syncthreads();
-        if (warp < NW) {
+        if (rr < R && y < L) {
             float acc[4][4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-            const int x0 = warp * 16;
+            const int x0 = pt * 16;
             const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
             const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
 #pragma unroll 1
             for (int t = 0; t < kTapsB; ++t) {
-                const int r = -tap_dy(t), xoff = -tap_dx(t);
+                const int r = -tap_dy(t) + rr, xoff = -tap_dx(t);
 #pragma unroll
                 for (int kc = 0; kc < 2; ++kc) {
                     const int aoff = (r * PX + x0 + arow + xoff + 2) * kRowStride + kc * 16 + acol;
@@ -278,32 +319,61 @@ __global__ void __launch_bounds__(256) k_conv32_bwd(const float *__restrict__ dz
     }
 }
 
-// Last layer (32 -> 1, mask B): logit f, and per position log p(s_k | s_<k) =
-// log sigmoid(s f) and (training) dF = -(1/n) s sigmoid(-s f).
-__global__ void k_layerD_fwd(const bf16 *hD, const float *wD, const float *bD, const int8_t *spins, int negate,
-                             float *f, float *ll, float *dF, float inv_n, int n, int L)
+// Stage rows y-2..y of a [n][L][L][32] BF16 activation into smem rows of L+4
+// positions (x offset 2, zero padded), 16-byte chunks.
+__device__ __forceinline__ void stage_rows3(bf16 (*H)[(kMaxL + 4) * kCh], const bf16 *src, int b, int y, int L)
 {
-    const size_t total = (size_t)n * L * L;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(p % L), y = (int)((p / L) % L);
-        const size_t b = p / ((size_t)L * L);
-        float acc = bD[0];
-        for (int t = 0; t < kTapsB; ++t) {
-            const int yy = y + tap_dy(t), xx = x + tap_dx(t);
-            if (yy < 0 || xx < 0 || xx >= L)
-                continue;
-            const bf16 *h = hD + ((b * L + yy) * L + xx) * kCh;
+    for (int i = threadIdx.x; i < 3 * (L + 4) * 4; i += blockDim.x) {
+        const int r = i / ((L + 4) * 4), rem = i - r * (L + 4) * 4, xx = rem / 4 - 2, ch = rem & 3, yy = y - 2 + r;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (yy >= 0 && xx >= 0 && xx < L)
+            v = *reinterpret_cast<const uint4 *>(src + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8);
+        *reinterpret_cast<uint4 *>(&H[r][(xx + 2) * kCh + ch * 8]) = v;
+    }
+}
+
+// Last layer (32 -> 1, mask B): logit f, and per position log p(s_k | s_<k) =
+// log sigmoid(s f) and (training) dF = -(1/n) s sigmoid(-s f).  One CTA item =
+// one row; 4 threads per position (8 channels each), partials summed in smem.
+__global__ void __launch_bounds__(256) k_layerD_fwd(const bf16 *hD, const float *wD, const float *bD,
+                                                    const int8_t *spins, int negate, float *f, float *ll, float *dF,
+                                                    float inv_n, int n, int L)
+{
+    __shared__ float W[kTapsB * kCh];
+    __shared__ __align__(16) bf16 H[3][(kMaxL + 4) * kCh];
+    __shared__ float part[kMaxL * 4];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kTapsB * kCh; i += blockDim.x)
+        W[i] = wD[i];
+    const float b0 = bD[0];
+    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
+        const int b = item / L, y = item - b * L;
+        __syncthreads();
+        stage_rows3(H, hD, b, y, L);
+        __syncthreads();
+        for (int j = tid; j < L * 4; j += blockDim.x) {
+            const int x = j >> 2, c0 = (j & 3) * 8;
+            float acc = 0.f;
 #pragma unroll
-            for (int c = 0; c < kCh; c += 2) {
-                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(h + c);
-                acc += wD[t * kCh + c] * bf(v.x) + wD[t * kCh + c + 1] * bf(v.y);
+            for (int t = 0; t < kTapsB; ++t) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(&H[tap_dy(t) + 2][(x + tap_dx(t) + 2) * kCh + c0]);
+                const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    acc += W[t * kCh + c0 + 2 * q] * bf(h2[q].x) + W[t * kCh + c0 + 2 * q + 1] * bf(h2[q].y);
             }
+            part[j] = acc;
         }
-        const float s = negate ? -(float)spins[p] : (float)spins[p];
-        f[p] = acc;
-        ll[p] = log_sigmoid(s * acc);
-        if (dF)
-            dF[p] = -inv_n * s * sigmoid(-s * acc);
+        __syncthreads();
+        for (int x = tid; x < L; x += blockDim.x) {
+            const float acc = b0 + ((part[4 * x] + part[4 * x + 1]) + (part[4 * x + 2] + part[4 * x + 3]));
+            const size_t p = ((size_t)b * L + y) * L + x;
+            const float sv = negate ? -(float)spins[p] : (float)spins[p];
+            f[p] = acc;
+            ll[p] = log_sigmoid(sv * acc);
+            if (dF)
+                dF[p] = -inv_n * sv * sigmoid(-sv * acc);
+        }
     }
 }
 
@@ -330,59 +400,113 @@ __global__ void k_logq(const float *ll, double *logq, int L)
 }
 
 // ------------------------------------------------------------------ backward
-// Last layer: dZ_{D-1} = (sum_t wD[t] dF(p - d_t)) * [h_{D-1} > 0], one thread
-// per (position, channel).
-__global__ void k_layerD_bwd_data(const float *dF, const float *wD, const bf16 *hD, float *dZ, int n, int L)
+// Last layer: dZ_{D-1}(p)[c] = (sum_t wD[t][c] dF(p - d_t)) * [h_{D-1}(p)[c] > 0]
+// (the forward read h at q + d_t for output q).  One CTA item = one row: dF of
+// rows y..y+2 staged in smem (zero padded); 4 threads per position.
+__global__ void __launch_bounds__(256) k_layerD_bwd_data(const float *dF, const float *wD, const bf16 *hD, float *dZ,
+                                                         int n, int L)
 {
-    const size_t total = (size_t)n * L * L * kCh;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % kCh);
-        const size_t p = i / kCh;
-        const int x = (int)(p % L), y = (int)((p / L) % L);
-        const size_t b = p / ((size_t)L * L);
-        float acc = 0.f;
-        for (int t = 0; t < kTapsB; ++t) {
-            const int yy = y - tap_dy(t), xx = x - tap_dx(t);
-            if (yy < L && xx >= 0 && xx < L)
-                acc += wD[t * kCh + c] * dF[(b * L + yy) * L + xx];
+    __shared__ float W[kTapsB * kCh];
+    __shared__ float G[3][kMaxL + 4];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kTapsB * kCh; i += blockDim.x)
+        W[i] = wD[i];
+    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
+        const int b = item / L, y = item - b * L;
+        __syncthreads();
+        for (int i = tid; i < 3 * (L + 4); i += blockDim.x) {
+            const int r = i / (L + 4), xx = i - r * (L + 4) - 2, yy = y + r;
+            G[r][xx + 2] = (yy < L && xx >= 0 && xx < L) ? dF[((size_t)b * L + yy) * L + xx] : 0.f;
         }
-        dZ[i] = bf(hD[i]) > 0.f ? acc : 0.f;
+        __syncthreads();
+        for (int j = tid; j < L * 4; j += blockDim.x) {
+            const int x = j >> 2, c0 = (j & 3) * 8;
+            float acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                acc[q] = 0.f;
+#pragma unroll
+            for (int t = 0; t < kTapsB; ++t) {
+                const float gv = G[-tap_dy(t)][x - tap_dx(t) + 2];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    acc[q] += W[t * kCh + c0 + q] * gv;
+            }
+            const size_t p = ((size_t)b * L + y) * L + x;
+            const uint4 hv = *reinterpret_cast<const uint4 *>(hD + p * kCh + c0);
+            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&hv);
+            float4 o0, o1;
+            o0.x = bf(h2[0].x) > 0.f ? acc[0] : 0.f;
+            o0.y = bf(h2[0].y) > 0.f ? acc[1] : 0.f;
+            o0.z = bf(h2[1].x) > 0.f ? acc[2] : 0.f;
+            o0.w = bf(h2[1].y) > 0.f ? acc[3] : 0.f;
+            o1.x = bf(h2[2].x) > 0.f ? acc[4] : 0.f;
+            o1.y = bf(h2[2].y) > 0.f ? acc[5] : 0.f;
+            o1.z = bf(h2[3].x) > 0.f ? acc[6] : 0.f;
+            o1.w = bf(h2[3].y) > 0.f ? acc[7] : 0.f;
+            float4 *dst = reinterpret_cast<float4 *>(dZ + p * kCh + c0);
+            dst[0] = o0;
+            dst[1] = o1;
+        }
     }
 }
 
-// Last-layer weight and bias gradients: gW[t][c] = sum_p dF(p) h(p + d_t)[c].
-// Thread (t, c) accumulates over the CTA's rows; one atomic per thread.
-__global__ void k_layerD_bwd_w(const float *dF, const bf16 *hD, float *g, DevParams P, int n, int L)
+// Last-layer weight and bias gradients: gW[t][c] = sum_p dF(p) h(p + d_t)[c],
+// gb = sum_p dF(p).  One CTA item = one row, staged in smem; thread i owns
+// outputs i and i + 256 of the 13 x 32 + 1; one atomic per output per CTA.
+__global__ void __launch_bounds__(256) k_layerD_bwd_w(const float *dF, const bf16 *hD, float *g, DevParams P, int n,
+                                                      int L)
 {
-    const int tid = threadIdx.x; // kTapsB * kCh + 1 threads
-    const int t = tid / kCh, c = tid % kCh;
-    float acc = 0.f;
+    __shared__ float Gs[kMaxL];
+    __shared__ __align__(16) bf16 H[3][(kMaxL + 4) * kCh];
+    constexpr int NO = kTapsB * kCh + 1;
+    const int tid = threadIdx.x;
+    float acc[2] = {0.f, 0.f};
     for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
-        const int b = item / L, y = item % L;
-        for (int x = 0; x < L; ++x) {
-            const float d = dF[((size_t)b * L + y) * L + x];
+        const int b = item / L, y = item - b * L;
+        __syncthreads();
+        stage_rows3(H, hD, b, y, L);
+        for (int x = tid; x < L; x += blockDim.x)
+            Gs[x] = dF[((size_t)b * L + y) * L + x];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int o = tid + k * 256;
+            if (o >= NO)
+                continue;
+            const int t = o / kCh, c = o - t * kCh;
+            float a = 0.f;
             if (t < kTapsB) {
-                const int yy = y + tap_dy(t), xx = x + tap_dx(t);
-                if (yy >= 0 && xx >= 0 && xx < L)
-                    acc += d * bf(hD[(((size_t)b * L + yy) * L + xx) * kCh + c]);
+                const bf16 *hr = &H[tap_dy(t) + 2][(tap_dx(t) + 2) * kCh + c];
+                for (int x = 0; x < L; ++x)
+                    a += Gs[x] * bf(hr[x * kCh]);
             } else {
-                acc += d;
+                for (int x = 0; x < L; ++x)
+                    a += Gs[x];
             }
+            acc[k] += a;
         }
     }
     const int D = P.D;
-    if (t < kTapsB)
-        atomicAdd(&g[canon_w(P, D - 1, 0, c, tap_dy(t), tap_dx(t))], acc);
-    else if (c == 0)
-        atomicAdd(&g[P.b_off[D - 1]], acc);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int o = tid + k * 256;
+        if (o >= NO)
+            continue;
+        const int t = o / kCh, c = o - t * kCh;
+        if (t < kTapsB)
+            atomicAdd(&g[canon_w(P, D - 1, 0, c, tap_dy(t), tap_dx(t))], acc[k]);
+        else
+            atomicAdd(&g[P.b_off[D - 1]], acc[k]);
+    }
 }
 
 // Hidden-layer weight and bias gradients on the tensor cores (dZ as a BF16
 // hi + lo pair, activations exactly as the forward used them):
 // gW[t][o][c] = sum_p dZ(p)[o] X(p + d_t)[c] -- a 32 x 32 GEMM per tap with the
 // positions as the reduction dimension.  Warp w owns taps w and w + 8.
-__global__ void __launch_bounds__(256) k_dw32(const float *__restrict__ dZ, const bf16 *__restrict__ X, float *g,
-                                              DevParams P, int layer, int n, int L)
+__global__ void __launch_bounds__(256) k_dw32(const float *__restrict__ dZ, const bf16 *__restrict__ X,
+                                              float *__restrict__ part, int n, int L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int NW = (L + 15) / 16, PX = NW * 16 + 4, PZ = NW * 16;
@@ -419,9 +543,8 @@ __global__ void __launch_bounds__(256) k_dw32(const float *__restrict__ dZ, cons
             *reinterpret_cast<uint4 *>(Xs + (r * PX + xi) * kRowStride + ch * 8) = v;
         }
         __syncthreads();
-        if (tid < kCh)
-            for (int x = 0; x < L; ++x)
-                bsum += bf(Zs[x * kRowStride + tid]) + bf(Zl[x * kRowStride + tid]);
+        for (int x = warp; x < L; x += 8) // bias: thread (warp, lane) sums channel lane over x = warp mod 8
+            bsum += bf(Zs[x * kRowStride + lane]) + bf(Zl[x * kRowStride + lane]);
         for (int j = 0; j < NW; ++j) {
             const int x0 = 16 * j;
             // A = dZ^T (rows o, k = positions): 8x8 blocks (p0, o0) transposed
@@ -458,6 +581,8 @@ __global__ void __launch_bounds__(256) k_dw32(const float *__restrict__ dZ, cons
             }
         }
     }
+    // this CTA's partial sums, [t][o][c] then 32 bias values, reduced in fixed order by k_dw_reduce
+    float *mine = part + (size_t)blockIdx.x * kDwPart;
     const int gq = lane >> 2, t4 = lane & 3;
     for (int tt = 0; tt < ntap; ++tt) {
         const int t = warp + 8 * tt;
@@ -465,37 +590,91 @@ __global__ void __launch_bounds__(256) k_dw32(const float *__restrict__ dZ, cons
             for (int j = 0; j < 4; ++j)
                 for (int h = 0; h < 2; ++h) {
                     const int o = 16 * mt + gq + 8 * h, c = 8 * j + 2 * t4;
-                    atomicAdd(&g[canon_w(P, layer, o, c, tap_dy(t), tap_dx(t))], acc[tt][mt][j][2 * h]);
-                    atomicAdd(&g[canon_w(P, layer, o, c + 1, tap_dy(t), tap_dx(t))], acc[tt][mt][j][2 * h + 1]);
+                    *reinterpret_cast<float2 *>(mine + (t * kCh + o) * kCh + c) =
+                        make_float2(acc[tt][mt][j][2 * h], acc[tt][mt][j][2 * h + 1]);
                 }
     }
-    if (tid < kCh)
-        atomicAdd(&g[P.b_off[layer] + tid], bsum);
+    __shared__ float bs[8][kCh];
+    bs[warp][lane] = bsum;
+    __syncthreads();
+    if (tid < kCh) {
+        float v = 0.f;
+        for (int w = 0; w < 8; ++w)
+            v += bs[w][tid];
+        mine[kTapsB * kCh * kCh + tid] = v;
+    }
 }
 
-// Layer-1 weight and bias gradients: gW1[o][t] = sum_p dZ1(p)[o] s(p + d_t).
-__global__ void k_layer1_bwd_w(const float *dZ1, const int8_t *spins, float *g, DevParams P, int n, int L)
+// Sum the per-CTA partials of k_dw32 in CTA order (deterministic) into the
+// canonical gradient of hidden layer `layer`.
+__global__ void k_dw_reduce(const float *__restrict__ part, int nparts, float *g, DevParams P, int layer)
 {
-    const int tid = threadIdx.x; // kCh * (kTapsA + 1) threads
-    const int o = tid / (kTapsA + 1), t = tid % (kTapsA + 1);
-    float acc = 0.f;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kDwPart)
+        return;
+    float v = 0.f;
+    for (int k = 0; k < nparts; ++k)
+        v += part[(size_t)k * kDwPart + i];
+    if (i < kTapsB * kCh * kCh) {
+        const int t = i / (kCh * kCh), o = (i / kCh) % kCh, c = i % kCh;
+        g[canon_w(P, layer, o, c, tap_dy(t), tap_dx(t))] += v;
+    } else {
+        g[P.b_off[layer] + (i - kTapsB * kCh * kCh)] += v;
+    }
+}
+
+// Layer-1 weight and bias gradients: gW1[o][t] = sum_p dZ1(p)[o] s(p + d_t),
+// gb1[o] = sum_p dZ1(p)[o].  One CTA item = one row: spins of rows y-2..y and
+// dZ1 of row y staged in smem; thread i owns outputs i and i + 256 of the
+// 32 x (12 + 1); one atomic per output per CTA.
+__global__ void __launch_bounds__(256) k_layer1_bwd_w(const float *dZ1, const int8_t *spins, float *g, DevParams P,
+                                                      int n, int L)
+{
+    __shared__ float S[3][kMaxL + 4];
+    __shared__ __align__(16) float Z[kMaxL * kCh];
+    constexpr int NO = kCh * (kTapsA + 1);
+    const int tid = threadIdx.x;
+    float acc[2] = {0.f, 0.f};
     for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
-        const int b = item / L, y = item % L;
-        for (int x = 0; x < L; ++x) {
-            const float d = dZ1[(((size_t)b * L + y) * L + x) * kCh + o];
+        const int b = item / L, y = item - b * L;
+        __syncthreads();
+        for (int i = tid; i < 3 * (L + 4); i += blockDim.x) {
+            const int r = i / (L + 4), xx = i - r * (L + 4) - 2, yy = y - 2 + r;
+            S[r][xx + 2] = (yy >= 0 && xx >= 0 && xx < L) ? (float)spins[((size_t)b * L + yy) * L + xx] : 0.f;
+        }
+        const float4 *zr = reinterpret_cast<const float4 *>(dZ1 + ((size_t)b * L + y) * L * kCh);
+        for (int i = tid; i < L * kCh / 4; i += blockDim.x)
+            reinterpret_cast<float4 *>(Z)[i] = zr[i];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int idx = tid + k * 256;
+            if (idx >= NO)
+                continue;
+            const int o = idx / (kTapsA + 1), t = idx - o * (kTapsA + 1);
+            float a = 0.f;
             if (t < kTapsA) {
-                const int yy = y + tap_dy(t), xx = x + tap_dx(t);
-                if (yy >= 0 && xx >= 0 && xx < L)
-                    acc += d * (float)spins[((size_t)b * L + yy) * L + xx];
+                const float *sr = &S[tap_dy(t) + 2][tap_dx(t) + 2];
+                for (int x = 0; x < L; ++x)
+                    a += Z[x * kCh + o] * sr[x];
             } else {
-                acc += d;
+                for (int x = 0; x < L; ++x)
+                    a += Z[x * kCh + o];
             }
+            acc[k] += a;
         }
     }
-    if (t < kTapsA)
-        atomicAdd(&g[canon_w(P, 0, o, 0, tap_dy(t), tap_dx(t))], acc);
-    else
-        atomicAdd(&g[P.b_off[0] + o], acc);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int idx = tid + k * 256;
+        if (idx >= NO)
+            continue;
+        const int o = idx / (kTapsA + 1), t = idx - o * (kTapsA + 1);
+        if (t < kTapsA)
+            atomicAdd(&g[canon_w(P, 0, o, 0, tap_dy(t), tap_dx(t))], acc[k]);
+        else
+            atomicAdd(&g[P.b_off[0] + o], acc[k]);
+    }
 }
 
 __global__ void k_adam(float *p, float *m, float *v, const float *g, size_t n, float lr, float b1, float b2, float eps,
@@ -773,6 +952,7 @@ struct mc_van {
     long long *E1 = nullptr, *E2 = nullptr;
     int *acc = nullptr;
     bf16 *hist = nullptr;
+    float *dwpart = nullptr; // per-CTA partial gradients of k_dw32
     int sms = 0;
     bool weights_ready = false;
 };
@@ -787,7 +967,7 @@ mc_status vfail(mc_status s, const std::string &m)
 
 struct VanLayout {
     size_t p, m, v, g, wh, w1, wD, bias, H, dZa, dZb, f, ll, dF, spins, prop, lq, lq2, lq3, lq4, lr, E1, E2, acc, hist,
-        total;
+        dwpart, total;
 };
 
 VanLayout van_layout(int L, int nmax, int D)
@@ -806,6 +986,7 @@ VanLayout van_layout(int L, int nmax, int D)
     o.v = take(P.total * 4);
     o.g = take(P.total * 4);
     o.wh = take((size_t)(D - 2) * kTapsB * kCh * kCh * 2);
+    o.dwpart = take((size_t)kMaxDwBlocks * kDwPart * 4);
     o.w1 = take((size_t)kCh * kTapsA * 4);
     o.wD = take((size_t)kTapsB * kCh * 4);
     o.bias = take((size_t)((D - 1) * kCh + 1) * 4);
@@ -832,10 +1013,13 @@ VanLayout van_layout(int L, int nmax, int D)
 
 unsigned grid_for(size_t n, int threads, int sms) { return (unsigned)std::min<size_t>((n + threads - 1) / threads, (size_t)sms * 16); }
 
-size_t conv_smem(int L) { return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)3 * (((L + 15) / 16) * 16 + 4) * kRowStride * 2; }
+size_t conv_smem(int L)
+{
+    return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)(conv_rows(L) + 2) * (((L + 15) / 16) * 16 + 4) * kRowStride * 2;
+}
 size_t conv_bwd_smem(int L)
 {
-    return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)6 * (((L + 15) / 16) * 16 + 4) * kRowStride * 2;
+    return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)2 * (conv_rows(L) + 2) * (((L + 15) / 16) * 16 + 4) * kRowStride * 2;
 }
 size_t dw_smem(int L)
 {
@@ -865,15 +1049,15 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
             return e;
     }
     const int L = w->L, D = w->D;
-    const size_t pos = (size_t)n * L * L, layer = (size_t)w->nmax * L * L * kCh;
-    k_layer1_fwd<<<grid_for(pos * kCh, 256, w->sms), 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n,
-                                                                           L);
+    const size_t layer = (size_t)w->nmax * L * L * kCh;
+    const unsigned rows = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 8);
+    k_layer1_fwd<<<rows, 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n, L);
     const unsigned cg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 3);
     for (int l = 1; l <= D - 2; ++l)
         k_conv32<<<cg, 256, conv_smem(L), w->stream>>>(w->H + (l - 1) * layer, w->H + l * layer,
                                                        w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
                                                        w->bias + l * kCh, n, L);
-    k_layerD_fwd<<<grid_for(pos, 256, w->sms), 256, 0, w->stream>>>(w->H + (D - 2) * layer, w->wD,
+    k_layerD_fwd<<<rows, 256, 0, w->stream>>>(w->H + (D - 2) * layer, w->wD,
                                                                     w->bias + (D - 1) * kCh, w->spins, negate, w->f,
                                                                     w->ll, dF, 1.0f / n, n, L);
     k_logq<<<n, 256, 0, w->stream>>>(w->ll, logq, L);
@@ -883,23 +1067,27 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
 cudaError_t backward(mc_van *w, int n)
 {
     const int L = w->L, D = w->D;
-    const size_t pos = (size_t)n * L * L, layer = (size_t)w->nmax * L * L * kCh;
+    const size_t layer = (size_t)w->nmax * L * L * kCh;
     cudaError_t e = cudaMemsetAsync(w->g, 0, w->P.total * 4, w->stream);
     if (e != cudaSuccess)
         return e;
     const bf16 *hD = w->H + (D - 2) * layer;
-    k_layerD_bwd_data<<<grid_for(pos * kCh, 256, w->sms), 256, 0, w->stream>>>(w->dF, w->wD, hD, w->dZa, n, L);
-    const unsigned rg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 4);
-    k_layerD_bwd_w<<<rg, kTapsB * kCh + 1, 0, w->stream>>>(w->dF, hD, w->g, w->dp, n, L);
+    const unsigned rows = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 8);
+    const unsigned rg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 12);
+    k_layerD_bwd_data<<<rows, 256, 0, w->stream>>>(w->dF, w->wD, hD, w->dZa, n, L);
+    k_layerD_bwd_w<<<rg, 256, 0, w->stream>>>(w->dF, hD, w->g, w->dp, n, L);
     float *dz = w->dZa, *dzn = w->dZb;
     const unsigned cg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 3);
+    // k_dw32 holds 124 registers x 256 threads: two CTAs per SM, one wave
+    const unsigned dwg = (unsigned)std::min<size_t>(std::min<size_t>((size_t)n * L, (size_t)w->sms * 2), kMaxDwBlocks);
     for (int l = D - 2; l >= 1; --l) { // hidden layer l: input H[l-1], output H[l], grad dz wrt its pre-activation
-        k_dw32<<<cg, 256, dw_smem(L), w->stream>>>(dz, w->H + (l - 1) * layer, w->g, w->dp, l, n, L);
+        k_dw32<<<dwg, 256, dw_smem(L), w->stream>>>(dz, w->H + (l - 1) * layer, w->dwpart, n, L);
+        k_dw_reduce<<<(kDwPart + 255) / 256, 256, 0, w->stream>>>(w->dwpart, (int)dwg, w->g, w->dp, l);
         k_conv32_bwd<<<cg, 256, conv_bwd_smem(L), w->stream>>>(dz, dzn, w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
                                                                w->H + (l - 1) * layer, n, L);
         std::swap(dz, dzn);
     }
-    k_layer1_bwd_w<<<rg, kCh * (kTapsA + 1), 0, w->stream>>>(dz, w->spins, w->g, w->dp, n, L);
+    k_layer1_bwd_w<<<rg, 256, 0, w->stream>>>(dz, w->spins, w->g, w->dp, n, L);
     return cudaGetLastError();
 }
 
@@ -958,6 +1146,7 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     w->v = reinterpret_cast<float *>(b + o.v);
     w->g = reinterpret_cast<float *>(b + o.g);
     w->wh = reinterpret_cast<bf16 *>(b + o.wh);
+    w->dwpart = reinterpret_cast<float *>(b + o.dwpart);
     w->w1 = reinterpret_cast<float *>(b + o.w1);
     w->wD = reinterpret_cast<float *>(b + o.wD);
     w->bias = reinterpret_cast<float *>(b + o.bias);

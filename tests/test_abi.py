@@ -74,3 +74,27 @@ def test_null_and_bad_arguments_rejected(mc):
     buf = ctypes.create_string_buffer(1 << 20)
     st = L.mc_batch_init(ctypes.byref(out), 1, arr, 0, 16, ctypes.c_void_p(ctypes.addressof(buf) + 0), 1 << 20, None)
     assert st != 0
+
+
+@pytest.mark.parametrize("case,msg", [
+    ("empty", "n_chains"),
+    ("zero_extent", "even and >= 2"),
+    ("su2_odd", "even and >= 2"),
+    ("nan_beta", "finite"),
+    ("too_big", "2\\^31"),
+    ("no_ring", "series_capacity"),
+])
+def test_degenerate_inputs_rejected_on_the_host(mc, case, msg):
+    """Empty batches, zero or odd extents, a NaN coupling, lattices past the
+    32-bit site index and an empty ring are refused before anything reaches a
+    GPU."""
+    args = {
+        "empty": ([], 0, 16),
+        "zero_extent": ([mc.ising((0, 64), 0.4, 1)], 0, 16),
+        "su2_odd": ([mc.su2((4, 4, 4, 3), 2.0, 1)], 0, 16),
+        "nan_beta": ([mc.ising(64, float("nan"), 1)], 0, 16),
+        "too_big": ([mc.ising(1 << 17, 0.4, 1)], 1, 16),
+        "no_ring": ([mc.ising(64, 0.4, 1)], 0, 0),
+    }[case]
+    with pytest.raises(mc.MCError, match=msg):
+        mc.mc_workspace_bytes(*args)

@@ -51,10 +51,13 @@ def _cuda_time(fn):
     return e0.elapsed_time(e1) / 1e3
 
 
-def plain_rate(L: int, beta: float, chains: int, therm: int, sweeps: int, every: int, seed: int = 1) -> dict:
-    """Plain Metropolis: chain-sweeps per second and tau of |M| in sweeps."""
+def plain_rate(L: int, beta: float, chains: int, therm: int, sweeps: int, every: int, seed: int = 1,
+               layout: int | None = None) -> dict:
+    """Plain Metropolis: chain-sweeps per second and tau of |M| in sweeps
+    (int8 layout by default; the 32-spin words where L allows)."""
     from . import mc
-    b = mc.Batch([mc.ising(L, beta, seed, chain_id=k) for k in range(chains)], layout=mc.MC_LAYOUT_INT8,
+    layout = mc.MC_LAYOUT_INT8 if layout is None else layout
+    b = mc.Batch([mc.ising(L, beta, seed, chain_id=k) for k in range(chains)], layout=layout,
                  series_capacity=sweeps // every + 4)
     b.sweep(therm)
     b.sweep(every, every)  # graph warm-up
@@ -65,7 +68,8 @@ def plain_rate(L: int, beta: float, chains: int, therm: int, sweeps: int, every:
     b.close()
     rate = chains * sweeps / secs
     return {"chain_sweeps_per_s": rate, "tau_absM_sweeps": tau, "ess_per_s": rate / (2.0 * tau), "seconds": secs,
-            "chains": chains, "sweeps": sweeps, "mean_absm": float(absm.mean())}
+            "chains": chains, "sweeps": sweeps, "mean_absm": float(absm.mean()),
+            "layout": "msc32" if layout == mc.MC_LAYOUT_MSC32 else "int8"}
 
 
 def learned_rate(L: int, beta: float, chains: int, therm: int, data_snapshots: int, data_spacing: int,

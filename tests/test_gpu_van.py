@@ -188,3 +188,39 @@ def test_training_lowers_loss_and_raises_acceptance():
     assert last < first - 1.0, (first, last)
     acc1 = sum(net.mh_round(b) for _ in range(3)) / 3
     assert acc1 > 2 * max(acc0, 1), (acc0, acc1)
+
+
+def test_full_size_L64_sampler_log_prob_and_gradients():
+    """The benchmark's configuration, L = 64 with 4096 proposals: the sampler's
+    FP64 log q equals the forward network's on what it sampled, and both equal
+    the BF16-activation oracle on sampled configurations; one training step's
+    loss and gradients at L = 64 (batch 32) match the oracle.  The gradient
+    tolerance is looser than at L = 8: each weight gradient is a sum over
+    32 x 4096 positions whose terms carry the 2^-16 relative error of the
+    BF16 hi + lo split of dZ, and the sum cancels to ~1/100 of the sum of
+    magnitudes, so 1e-2 relative (cos > 1 - 1e-5) is the arithmetic's bound."""
+    L, n = 64, 4096
+    p = bf16_params(seed=7, bias=0.2)
+    net = mc.VAN(L, batch=n, depth=6, seed=3)
+    net.set_params(mc.mc.van_pack(p))
+    s, lq = net.sample(n, 0)
+    lp = net.log_prob(s).cpu().numpy()
+    lqs = lq.cpu().numpy()
+    assert np.max(np.abs(lqs - lp) / np.abs(lp)) < 1e-5
+    idx = [0, 1, 2047, n - 1]
+    ob = van.log_prob(p, s[idx].cpu().numpy().astype(np.float64), act="bf16")
+    assert np.max(np.abs(lp[idx] - ob) / np.abs(ob)) < 1e-4, (lp[idx], ob)
+    # gradients on 32 of the sampled configurations
+    sub = s[:32].contiguous()
+    loss_g = net.train_step(sub, lr=0.0, apply=False)
+    _, gflat = net.get_params(grads=True)
+    gg = mc.mc.van_unpack(gflat)
+    loss_o, go = van.loss_and_grad(p, sub.cpu().numpy().astype(np.float64), act="bf16")
+    assert abs(loss_g - loss_o) / abs(loss_o) < 1e-5
+    for l, ((gW, gb), (oW, ob_)) in enumerate(zip(gg, go)):
+        a = np.concatenate([gW.ravel(), gb.ravel()])
+        b = np.concatenate([oW.ravel(), ob_.ravel()])
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert cos > 1 - 1e-5 and rel < 1e-2, (l, cos, rel)
+    net.close()

@@ -121,6 +121,8 @@ def learned_rate(L: int, beta: float, chains: int, therm: int, data_snapshots: i
     secs = _cuda_time(run)
     absm = np.abs(b.read_series()["M"].astype(np.float64)) / (L * L)
     tau = tau_int(absm)
+    # the sequential sampler alone: L^2 dependent steps through every layer
+    t_sample = _cuda_time(lambda: net.sample(chains, 0x7FFFFFFF))
     net.close()
     b.close()
     rate = chains * rounds / secs
@@ -129,7 +131,8 @@ def learned_rate(L: int, beta: float, chains: int, therm: int, data_snapshots: i
             "local_sweeps_per_round": local_sweeps, "chains": chains, "rounds": rounds,
             "train_seconds": t_train, "data_seconds": t_data, "train_configs": int(data.shape[0]),
             "train_steps": train_steps, "loss_first": losses[0], "loss_last": losses[-1],
-            "mean_absm": float(absm.mean())}
+            "mean_absm": float(absm.mean()), "sample_ms": t_sample * 1e3,
+            "sample_us_per_position": t_sample * 1e6 / (L * L)}
 
 
 def _init_flat(depth: int, channels: int, seed: int, scale: float) -> np.ndarray:

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "tc_dev.cuh"
 #include "van_dev.cuh"
 
 using bf16 = __nv_bfloat16;
@@ -141,78 +142,163 @@ __host__ __device__ __forceinline__ int conv_rows(int L)
     return nw >= 8 ? 1 : 8 / nw;
 }
 
-// 32 -> 32 masked convolution on the tensor cores (forward): out =
-// ReLU(conv(in) + bias).  One CTA item = R = conv_rows(L) consecutive rows of
-// one sample (rows y0-2 .. y0+R-1 staged); warp w computes row y0 + w / NW,
-// positions 16 (w % NW) .. +15, for all 32 output channels: K = 13 taps x 32
-// input channels in 26 k16 steps.
-__global__ void __launch_bounds__(256) k_conv32(const bf16 *__restrict__ in, bf16 *__restrict__ out,
-                                                const bf16 *__restrict__ W, const float *__restrict__ bias, int n,
-                                                int L)
+// 32 -> 32 masked convolution (forward) on the fifth-generation tensor cores:
+// out = ReLU(conv(in) + bias), an implicit GEMM D[q][o] = sum_{t,c} A_t[q][c] W[t][o][c]
+// with tcgen05.mma (M = 128 positions, N = 32 channels, K = 16, BF16 in,
+// FP32 accumulator in tensor memory).
+//
+// Positions are indexed on a padded grid, q = r P + xp with P = L + 4 and
+// xp = x + 2, so that every tap (dy, dx) of output q reads input index
+// q + (dy + 2) P + dx of the staged rows y0-2 .. y0+R-1 -- a shifted view of
+// the same shared-memory planes (see tc_dev.cuh), zero halo columns giving the
+// zero padding.  Outputs on halo columns or past the last row are computed and
+// discarded.  One CTA item = R rows of one sample, staged with cp.async into 4
+// chunk planes (8 channels each); the item is cut into 128-position tiles,
+// issued 3 at a time by one thread into one of two tensor-memory buffers
+// (26 MMAs per tile: 13 taps x 2 k-steps) while the 4 warps drain the other
+// buffer (tcgen05.ld, bias, ReLU, BF16, 64-byte stores).  Two CTAs per SM.
+struct TcConvGeom {
+    int L, P, R, YB, Qpad, tiles, PL;
+    uint32_t plane_bytes, smem_bytes;
+};
+constexpr uint32_t kTcB = kTapsB * 4 * kCh * 16; // B planes: [tap][chunk][out channel] x 16 bytes
+constexpr int kTcGroup = 3;                       // tiles per commit
+constexpr uint32_t kTcCols = 256;                 // 2 buffers x 3 tiles x 32 columns, rounded to a power of 2
+constexpr int kTcMaxPolls = 1 << 22;              // bounded completion wait
+
+TcConvGeom tc_conv_geom(int L)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    bf16 *Ws = reinterpret_cast<bf16 *>(smem);      // [13][32 o][40]
-    bf16 *Xs = Ws + kTapsB * kCh * kRowStride;       // [R + 2][PX][40]
-    const int NW = (L + 15) / 16, PX = NW * 16 + 4, R = conv_rows(L), YB = (L + R - 1) / R;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int rr = warp / NW, pt = warp - rr * NW; // this warp's row within the item and position tile
-    for (int i = tid; i < kTapsB * kCh * kCh; i += blockDim.x) {
-        const int t = i / (kCh * kCh), r = (i / kCh) % kCh, q = i % kCh; // W[t][o = r][c = q]
-        Ws[(t * kCh + r) * kRowStride + q] = W[i];
+    TcConvGeom g{};
+    g.L = L;
+    g.P = L + 4;
+    for (int R : {16, 8, 4, 2, 1}) { // most rows whose planes fit two CTAs per SM
+        g.R = R < L ? R : L;
+        g.Qpad = (g.R * g.P + 127) / 128 * 128;
+        g.PL = (g.Qpad + 2 * g.P + 4 + 7) / 8 * 8; // 2-entry guard each side of every tap's view
+        g.plane_bytes = (uint32_t)g.PL * 16;
+        g.smem_bytes = 4 * g.plane_bytes + kTcB + 32;
+        if (g.smem_bytes <= 110u * 1024)
+            break;
     }
-    for (int item = blockIdx.x; item < n * YB; item += gridDim.x) {
-        const int b = item / YB, y0 = (item - b * YB) * R, y = y0 + rr;
-        __syncthreads(); // weights ready / previous item's reads done
-        for (int i = tid; i < (R + 2) * PX * 4; i += blockDim.x) {
-            const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
-            const int yy = y0 - 2 + r, xx = xi - 2;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (yy >= 0 && yy < L && xx >= 0 && xx < L)
-                v = *reinterpret_cast<const uint4 *>(in + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8);
-            *reinterpret_cast<uint4 *>(Xs + (r * PX + xi) * kRowStride + ch * 8) = v;
+    g.YB = (L + g.R - 1) / g.R;
+    g.tiles = g.Qpad / 128;
+    return g;
+}
+
+__global__ void __launch_bounds__(128, 2) k_conv32_tc(const bf16 *__restrict__ in, bf16 *__restrict__ out,
+                                                      const bf16 *__restrict__ W, const float *__restrict__ bias,
+                                                      int n, TcConvGeom g, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t sb = smem_u32(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t buf_bytes = 4 * g.plane_bytes;
+    const uint32_t boff = buf_bytes, bar0 = sb + boff + kTcB, tslot_off = boff + kTcB + 16;
+    for (uint32_t i = tid; i < buf_bytes / 16; i += blockDim.x) // halo columns and guards stay zero
+        reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < kTapsB * kCh * 4; i += blockDim.x) {
+        const int t = i / (kCh * 4), o = (i / 4) % kCh, c8 = i % 4;
+        *reinterpret_cast<uint4 *>(smem + boff + ((t * 4 + c8) * kCh + o) * 16) =
+            *reinterpret_cast<const uint4 *>(W + ((size_t)(t * kCh + o) * kCh + c8 * 8));
+    }
+    if (warp == 0)
+        tc::tmem_alloc(sb + tslot_off, kTcCols);
+    if (tid == 0) {
+        tc::mbar_init(bar0, 1);
+        tc::mbar_init(bar0 + 8, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *reinterpret_cast<volatile uint32_t *>(smem + tslot_off);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, kCh);
+    float bv[kCh];
+#pragma unroll
+    for (int c = 0; c < kCh; ++c)
+        bv[c] = __ldg(&bias[c]);
+    // descriptors of tap t, k-step kc for tile 0; tile m adds 128 m positions to the start
+    // address (its 14-bit field holds addr >> 4 of a shared address below 256 KB: no carry)
+    uint64_t adesc[kTapsB * 2], bdesc[kTapsB * 2];
+    if (tid == 0)
+        for (int t = 0; t < kTapsB; ++t)
+            for (int kc = 0; kc < 2; ++kc) {
+                adesc[t * 2 + kc] = tc::smem_desc(sb + (uint32_t)(2 * kc) * g.plane_bytes +
+                                                      (uint32_t)(2 + (tap_dy(t) + 2) * g.P + tap_dx(t)) * 16u,
+                                                  g.plane_bytes, 128);
+                bdesc[t * 2 + kc] = tc::smem_desc(sb + boff + (uint32_t)(t * 4 + 2 * kc) * (kCh * 16), kCh * 16, 128);
+            }
+    const int rounds = (g.tiles + kTcGroup - 1) / kTcGroup;
+    auto issue = [&](int rd) {
+        const int m0 = rd * kTcGroup, m1 = m0 + kTcGroup < g.tiles ? m0 + kTcGroup : g.tiles;
+        for (int m = m0; m < m1; ++m) {
+            const uint32_t d = tbase + (uint32_t)((rd & 1) * kTcGroup + (m - m0)) * kCh;
+            const uint64_t off = (uint64_t)((uint32_t)m * 128u);
+#pragma unroll
+            for (int j = 0; j < kTapsB * 2; ++j)
+                tc::mma_bf16(d, adesc[j] + off, bdesc[j], idesc, j != 0);
         }
+        tc::commit(bar0 + 8u * (uint32_t)(rd & 1));
+    };
+    uint32_t uses[2] = {0u, 0u};
+    int ok = 1;
+    for (int it = blockIdx.x; ok && it < n * g.YB; it += gridDim.x) {
+        const int b = it / g.YB, y0 = (it - b * g.YB) * g.R;
+        for (int i = tid; i < (g.R + 2) * g.L * 4; i += blockDim.x) {
+            const int rho = i / (g.L * 4), rem = i - rho * g.L * 4, x = rem >> 2, c8 = rem & 3, yy = y0 - 2 + rho;
+            const bool inside = yy >= 0 && yy < g.L; // rows outside the lattice: zero fill
+            const bf16 *src = in + (((size_t)b * g.L + (inside ? yy : 0)) * g.L + x) * kCh + c8 * 8;
+            const uint32_t dst = sb + (uint32_t)c8 * g.plane_bytes + (uint32_t)(4 + rho * g.P + x) * 16u;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(inside ? 16 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        tc::fence_smem_for_async();
+        tc::fence_before_sync();
         __syncthreads();
-        if (rr < R && y < L) {
-            float acc[4][4];
+        tc::fence_after_sync();
+        if (tid == 0)
+            issue(0);
+        for (int rd = 0; rd < rounds; ++rd) {
+            if (tid == 0 && rd + 1 < rounds)
+                issue(rd + 1); // the other buffer was drained before the barrier that ended round rd - 1
+            const int s = rd & 1;
+            const bool got = tc::mbar_wait(bar0 + 8u * s, uses[s] & 1u, kTcMaxPolls);
+            ++uses[s];
+            tc::fence_after_sync();
+            const int m0 = rd * kTcGroup, m1 = m0 + kTcGroup < g.tiles ? m0 + kTcGroup : g.tiles;
+            for (int m = m0; m < m1; ++m) {
+                float v[kCh];
+                tc::ld_32x32b_x32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(s * kTcGroup + (m - m0)) * kCh, v);
+                const int q = m * 128 + 32 * warp + lane, r = q / g.P, xp = q - r * g.P;
+                if (got && r < g.R && y0 + r < g.L && xp >= 2 && xp < g.L + 2) {
+                    uint4 pk[4];
+                    uint32_t *pw = reinterpret_cast<uint32_t *>(pk);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-            const int x0 = pt * 16;
-            const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
-            const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
-#pragma unroll 1
-            for (int t = 0; t < kTapsB; ++t) {
-                const int r = tap_dy(t) + 2 + rr, xoff = tap_dx(t);
-#pragma unroll
-                for (int kc = 0; kc < 2; ++kc) {
-                    uint32_t a0, a1, a2, a3;
-                    ldsm_x4(smem_u32(Xs + (r * PX + x0 + arow + xoff + 2) * kRowStride + kc * 16 + acol), a0, a1, a2,
-                            a3);
-#pragma unroll
-                    for (int np = 0; np < 2; ++np) {
-                        uint32_t b0, b1, b2, b3;
-                        ldsm_x4(smem_u32(Ws + (t * kCh + np * 16 + brow) * kRowStride + kc * 16 + bcol), b0, b1, b2,
-                                b3);
-                        mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
-                        mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+                    for (int c = 0; c < kCh; c += 2) {
+                        const __nv_bfloat162 h =
+                            __floats2bfloat162_rn(fmaxf(v[c] + bv[c], 0.f), fmaxf(v[c + 1] + bv[c + 1], 0.f));
+                        pw[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
                     }
+                    uint4 *dst = reinterpret_cast<uint4 *>(out + (((size_t)b * g.L + y0 + r) * g.L + (xp - 2)) * kCh);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        dst[k] = pk[k];
                 }
             }
-            const int g = lane >> 2, t4 = lane & 3;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int x = x0 + g + 8 * h;
-                    if (x >= L)
-                        continue;
-                    const int c = 8 * j + 2 * t4;
-                    const size_t o = (((size_t)b * L + y) * L + x) * kCh + c;
-                    *reinterpret_cast<__nv_bfloat162 *>(out + o) = __floats2bfloat162_rn(
-                        fmaxf(acc[j][2 * h] + bias[c], 0.f), fmaxf(acc[j][2 * h + 1] + bias[c + 1], 0.f));
-                }
+            tc::fence_before_sync();
+            ok = __syncthreads_and(ok && got);
+            tc::fence_after_sync();
+            if (!ok)
+                break;
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (!ok && tid == 0)
+        atomicExch(err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        tc::tmem_free(tbase, kTcCols);
 }
 
 // Split an FP32 value into BF16 hi + lo (hi + lo carries ~16 mantissa bits).
@@ -953,6 +1039,7 @@ struct mc_van {
     int *acc = nullptr;
     bf16 *hist = nullptr;
     float *dwpart = nullptr; // per-CTA partial gradients of k_dw32
+    int *err = nullptr;      // device fault latch (tensor-core completion wait gave up)
     int sms = 0;
     bool weights_ready = false;
 };
@@ -965,9 +1052,26 @@ mc_status vfail(mc_status s, const std::string &m)
     return s;
 }
 
+// After the stream was synchronised: report (and clear) a fault a kernel
+// latched -- a tensor-core completion wait that gave up.
+mc_status check_err(mc_van *w, const char *where)
+{
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, w->err, sizeof v, cudaMemcpyDeviceToHost, w->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    if (v != 0) {
+        cudaMemsetAsync(w->err, 0, sizeof v, w->stream);
+        return vfail(MC_ETIMEOUT, std::string(where) + ": a tensor-core completion wait timed out");
+    }
+    return MC_OK;
+}
+
 struct VanLayout {
     size_t p, m, v, g, wh, w1, wD, bias, H, dZa, dZb, f, ll, dF, spins, prop, lq, lq2, lq3, lq4, lr, E1, E2, acc, hist,
-        dwpart, total;
+        dwpart, err, total;
 };
 
 VanLayout van_layout(int L, int nmax, int D)
@@ -987,6 +1091,7 @@ VanLayout van_layout(int L, int nmax, int D)
     o.g = take(P.total * 4);
     o.wh = take((size_t)(D - 2) * kTapsB * kCh * kCh * 2);
     o.dwpart = take((size_t)kMaxDwBlocks * kDwPart * 4);
+    o.err = take(16);
     o.w1 = take((size_t)kCh * kTapsA * 4);
     o.wD = take((size_t)kTapsB * kCh * 4);
     o.bias = take((size_t)((D - 1) * kCh + 1) * 4);
@@ -1013,10 +1118,6 @@ VanLayout van_layout(int L, int nmax, int D)
 
 unsigned grid_for(size_t n, int threads, int sms) { return (unsigned)std::min<size_t>((n + threads - 1) / threads, (size_t)sms * 16); }
 
-size_t conv_smem(int L)
-{
-    return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)(conv_rows(L) + 2) * (((L + 15) / 16) * 16 + 4) * kRowStride * 2;
-}
 size_t conv_bwd_smem(int L)
 {
     return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)2 * (conv_rows(L) + 2) * (((L + 15) / 16) * 16 + 4) * kRowStride * 2;
@@ -1052,11 +1153,12 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
     const size_t layer = (size_t)w->nmax * L * L * kCh;
     const unsigned rows = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 8);
     k_layer1_fwd<<<rows, 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n, L);
-    const unsigned cg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 3);
+    const TcConvGeom tg = tc_conv_geom(L);
+    const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tg.YB, (size_t)w->sms * 2);
     for (int l = 1; l <= D - 2; ++l)
-        k_conv32<<<cg, 256, conv_smem(L), w->stream>>>(w->H + (l - 1) * layer, w->H + l * layer,
-                                                       w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
-                                                       w->bias + l * kCh, n, L);
+        k_conv32_tc<<<tcg, 128, tg.smem_bytes, w->stream>>>(w->H + (l - 1) * layer, w->H + l * layer,
+                                                           w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
+                                                           w->bias + l * kCh, n, tg, w->err);
     k_layerD_fwd<<<rows, 256, 0, w->stream>>>(w->H + (D - 2) * layer, w->wD,
                                                                     w->bias + (D - 1) * kCh, w->spins, negate, w->f,
                                                                     w->ll, dF, 1.0f / n, n, L);
@@ -1147,6 +1249,7 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     w->g = reinterpret_cast<float *>(b + o.g);
     w->wh = reinterpret_cast<bf16 *>(b + o.wh);
     w->dwpart = reinterpret_cast<float *>(b + o.dwpart);
+    w->err = reinterpret_cast<int *>(b + o.err);
     w->w1 = reinterpret_cast<float *>(b + o.w1);
     w->wD = reinterpret_cast<float *>(b + o.wD);
     w->bias = reinterpret_cast<float *>(b + o.bias);
@@ -1172,7 +1275,8 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(w->ws, 0, o.hist, w->stream); // params, Adam state, buffers
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem(L));
+        e = cudaFuncSetAttribute(k_conv32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_conv_geom(L).smem_bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_conv32_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_bwd_smem(L));
     if (e == cudaSuccess)
@@ -1263,7 +1367,7 @@ mc_status mc_van_train_step(mc_van *w, const int8_t *dev_spins, int32_t n, float
     }
     if (e != cudaSuccess)
         return vfail(MC_ECUDA, std::string("mc_van_train_step: ") + cudaGetErrorString(e));
-    return MC_OK;
+    return host_loss ? check_err(w, "mc_van_train_step") : MC_OK;
 }
 
 mc_status mc_van_sample(mc_van *w, int32_t n, uint32_t round, const uint32_t *dev_ids, int8_t *dev_out,
@@ -1353,7 +1457,7 @@ mc_status mc_van_mh_round(mc_van *w, mc_ctx *c, int32_t *host_accepted)
     }
     if (e != cudaSuccess)
         return vfail(MC_ECUDA, std::string("mc_van_mh_round: ") + cudaGetErrorString(e));
-    return MC_OK;
+    return host_accepted ? check_err(w, "mc_van_mh_round") : MC_OK;
 }
 
 mc_status mc_van_set_round(mc_van *w, uint32_t round)

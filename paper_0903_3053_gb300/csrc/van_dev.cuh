@@ -10,8 +10,9 @@
 // centre), each followed by bias and ReLU; layer D is 5x5, 32 -> 1, mask B,
 // giving the logit f_k with p(s_k = +1 | s_<k) = sigmoid(f_k).
 // Activations are BF16, channels innermost ([n][y][x][32]); the 32 -> 32
-// layers run on the tensor cores (mma.sync m16n8k16, BF16 in, FP32
-// accumulate); log q is accumulated in FP64.
+// layers run on the tensor cores (forward: tcgen05.mma with a tensor-memory
+// accumulator; gradients and the sampler's 32-sample tiles: mma.sync
+// m16n8k16), BF16 in, FP32 accumulate; log q is accumulated in FP64.
 #pragma once
 #include <cuda_bf16.h>
 

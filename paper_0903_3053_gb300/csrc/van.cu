@@ -134,14 +134,6 @@ __global__ void __launch_bounds__(256) k_layer1_fwd(const int8_t *spins, int neg
     }
 }
 
-// Rows per CTA item of the 32-channel convolutions: enough rows that all 8
-// warps get a 16-position tile (L = 64: 2 rows, L = 32: 4).
-__host__ __device__ __forceinline__ int conv_rows(int L)
-{
-    const int nw = (L + 15) / 16;
-    return nw >= 8 ? 1 : 8 / nw;
-}
-
 // 32 -> 32 masked convolution (forward) on the fifth-generation tensor cores:
 // out = ReLU(conv(in) + bias), an implicit GEMM D[q][o] = sum_{t,c} A_t[q][c] W[t][o][c]
 // with tcgen05.mma (M = 128 positions, N = 32 channels, K = 16, BF16 in,
@@ -166,30 +158,39 @@ constexpr int kTcGroup = 3;                       // tiles per commit
 constexpr uint32_t kTcCols = 256;                 // 2 buffers x 3 tiles x 32 columns, rounded to a power of 2
 constexpr int kTcMaxPolls = 1 << 22;              // bounded completion wait
 
-TcConvGeom tc_conv_geom(int L)
+// Rows per CTA item: the R <= 16 whose `nplanes` planes (plus the weights)
+// fit two CTAs per SM and that needs the fewest 128-position tiles per sample.
+TcConvGeom tc_conv_geom(int L, int nplanes)
 {
-    TcConvGeom g{};
-    g.L = L;
-    g.P = L + 4;
-    for (int R : {16, 8, 4, 2, 1}) { // most rows whose planes fit two CTAs per SM
-        g.R = R < L ? R : L;
-        g.Qpad = (g.R * g.P + 127) / 128 * 128;
+    TcConvGeom best{};
+    long best_tiles = -1;
+    for (int R = 1; R <= 16 && R <= L; ++R) {
+        TcConvGeom g{};
+        g.L = L;
+        g.P = L + 4;
+        g.R = R;
+        g.Qpad = (R * g.P + 127) / 128 * 128;
         g.PL = (g.Qpad + 2 * g.P + 4 + 7) / 8 * 8; // 2-entry guard each side of every tap's view
         g.plane_bytes = (uint32_t)g.PL * 16;
-        g.smem_bytes = 4 * g.plane_bytes + kTcB + 32;
-        if (g.smem_bytes <= 110u * 1024)
-            break;
+        g.smem_bytes = (uint32_t)nplanes * g.plane_bytes + kTcB + 32;
+        g.YB = (L + R - 1) / R;
+        g.tiles = g.Qpad / 128;
+        if (g.smem_bytes > 110u * 1024)
+            continue;
+        const long t = (long)g.YB * g.tiles;
+        if (best_tiles < 0 || t < best_tiles || (t == best_tiles && R > best.R)) {
+            best = g;
+            best_tiles = t;
+        }
     }
-    g.YB = (L + g.R - 1) / g.R;
-    g.tiles = g.Qpad / 128;
-    return g;
+    return best;
 }
 
 __global__ void __launch_bounds__(128, 2) k_conv32_tc(const bf16 *__restrict__ in, bf16 *__restrict__ out,
                                                       const bf16 *__restrict__ W, const float *__restrict__ bias,
                                                       int n, TcConvGeom g, int *err)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t sb = smem_u32(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t buf_bytes = 4 * g.plane_bytes;
@@ -301,108 +302,150 @@ __global__ void __launch_bounds__(128, 2) k_conv32_tc(const bf16 *__restrict__ i
         tc::tmem_free(tbase, kTcCols);
 }
 
-// Split an FP32 value into BF16 hi + lo (hi + lo carries ~16 mantissa bits).
-__device__ __forceinline__ void split_bf16(float v, bf16 &hi, bf16 &lo)
+// Gradients travel between the backward kernels as a BF16 hi + lo pair
+// (hi = bf16(v), lo = bf16(v - hi), ~16 mantissa bits): two [n][L][L][32] BF16
+// arrays in the space of one FP32 array, which the tensor cores read directly.
+__device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo)
 {
-    hi = __float2bfloat16(v);
-    lo = __float2bfloat16(v - bf(hi));
-}
-
-// Stage FP32 rows into two BF16 tiles (hi, lo): 8 values per call.
-__device__ __forceinline__ void stage_split(const float *src, bool valid, bf16 *hi, bf16 *lo)
-{
-    float v[8];
-    if (valid) {
-        const float4 p = *reinterpret_cast<const float4 *>(src), q = *reinterpret_cast<const float4 *>(src + 4);
-        v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w; v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
-    } else {
+    bf16 h[8], l[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            v[i] = 0.f;
+    for (int k = 0; k < 8; ++k) {
+        h[k] = __float2bfloat16(v[k]);
+        l[k] = __float2bfloat16(v[k] - bf(h[k]));
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        split_bf16(v[i], hi[i], lo[i]);
+    hi = *reinterpret_cast<uint4 *>(h);
+    lo = *reinterpret_cast<uint4 *>(l);
 }
 
 // Gradient with respect to a 32 -> 32 layer's input, masked by the previous
-// layer's ReLU: out = (conv^T dZ) * [mask_src > 0], taps at (-dy, -dx) and
-// transposed weights.  dZ arrives in FP32 and enters the tensor cores as a
-// BF16 hi + lo pair (two MMAs per k step), so the gradient keeps ~16 mantissa
-// bits; the weights are exactly the BF16 values the forward used.  FP32 out.
-__global__ void __launch_bounds__(256) k_conv32_bwd(const float *__restrict__ dz, float *__restrict__ out,
-                                                    const bf16 *__restrict__ W, const bf16 *__restrict__ mask_src,
-                                                    int n, int L)
+// layer's ReLU, on the fifth-generation tensor cores:
+//   out(p)[c] = [mask(p)[c] > 0] sum_t sum_o W[t][o][c] dz(p - d_t)[o].
+// Same padded-position implicit GEMM as k_conv32_tc with the taps negated
+// (rows y0 .. y0+R+1 staged) and the weights transposed into the B planes;
+// dz arrives as hi + lo (8 A planes) and each k step issues two MMAs into
+// the same FP32 accumulator; the masked result leaves as hi + lo.
+constexpr int kTcBwdGroup = 2;
+constexpr uint32_t kTcBwdCols = 128;
+
+__global__ void __launch_bounds__(128, 2) k_conv32_bwd_tc(const bf16 *__restrict__ dzh, const bf16 *__restrict__ dzl,
+                                                          bf16 *__restrict__ outh, bf16 *__restrict__ outl,
+                                                          const bf16 *__restrict__ W, const bf16 *__restrict__ mask,
+                                                          int n, TcConvGeom g, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int NW = (L + 15) / 16, PX = NW * 16 + 4, R = conv_rows(L), YB = (L + R - 1) / R;
-    bf16 *Ws = reinterpret_cast<bf16 *>(smem);      // [13][32 c][40]  (W transposed)
-    bf16 *Xh = Ws + kTapsB * kCh * kRowStride;       // [R + 2][PX][40] hi
-    bf16 *Xl = Xh + (R + 2) * PX * kRowStride;       // [R + 2][PX][40] lo
+    const uint32_t sb = smem_u32(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int rr = warp / NW, pt = warp - rr * NW;
-    for (int i = tid; i < kTapsB * kCh * kCh; i += blockDim.x) {
-        const int t = i / (kCh * kCh), r = (i / kCh) % kCh, q = i % kCh; // W[t][o = r][c = q]
-        Ws[(t * kCh + q) * kRowStride + r] = W[i];
+    const uint32_t abytes = 8 * g.plane_bytes; // planes 0-3: hi, 4-7: lo
+    const uint32_t boff = abytes, bar0 = sb + boff + kTcB, tslot_off = boff + kTcB + 16;
+    for (uint32_t i = tid; i < abytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < kTapsB * 4 * kCh; i += blockDim.x) { // B planes [t][o8][c] = W[t][8 o8 .. +7][c]
+        const int t = i / (4 * kCh), o8 = (i / kCh) % 4, c = i % kCh;
+        bf16 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            v[k] = W[((size_t)t * kCh + o8 * 8 + k) * kCh + c];
+        *reinterpret_cast<uint4 *>(smem + boff + ((t * 4 + o8) * kCh + c) * 16) = *reinterpret_cast<uint4 *>(v);
     }
-    for (int item = blockIdx.x; item < n * YB; item += gridDim.x) {
-        const int b = item / YB, y0 = (item - b * YB) * R, y = y0 + rr;
-        __syncthreads();
-        for (int i = tid; i < (R + 2) * PX * 4; i += blockDim.x) {
-            const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
-            const int yy = y0 + r, xx = xi - 2;
-            const bool ok = yy < L && xx >= 0 && xx < L;
-            bf16 hi[8], lo[8];
-            stage_split(dz + (((size_t)b * L + (ok ? yy : 0)) * L + (ok ? xx : 0)) * kCh + ch * 8, ok, hi, lo);
-            *reinterpret_cast<uint4 *>(Xh + (r * PX + xi) * kRowStride + ch * 8) = *reinterpret_cast<uint4 *>(hi);
-            *reinterpret_cast<uint4 *>(Xl + (r * PX + xi) * kRowStride + ch * 8) = *reinterpret_cast<uint4 *>(lo);
+    if (warp == 0)
+        tc::tmem_alloc(sb + tslot_off, kTcBwdCols);
+    if (tid == 0) {
+        tc::mbar_init(bar0, 1);
+        tc::mbar_init(bar0 + 8, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *reinterpret_cast<volatile uint32_t *>(smem + tslot_off);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, kCh);
+    uint64_t adesc[kTapsB * 2], bdesc[kTapsB * 2];
+    if (tid == 0)
+        for (int t = 0; t < kTapsB; ++t)
+            for (int kc = 0; kc < 2; ++kc) {
+                adesc[t * 2 + kc] = tc::smem_desc(sb + (uint32_t)(2 * kc) * g.plane_bytes +
+                                                      (uint32_t)(2 - tap_dy(t) * g.P - tap_dx(t)) * 16u,
+                                                  g.plane_bytes, 128);
+                bdesc[t * 2 + kc] = tc::smem_desc(sb + boff + (uint32_t)(t * 4 + 2 * kc) * (kCh * 16), kCh * 16, 128);
+            }
+    const uint64_t lo_off = (uint64_t)((4u * g.plane_bytes) >> 4);
+    const int rounds = (g.tiles + kTcBwdGroup - 1) / kTcBwdGroup;
+    auto issue = [&](int rd) {
+        const int m0 = rd * kTcBwdGroup, m1 = m0 + kTcBwdGroup < g.tiles ? m0 + kTcBwdGroup : g.tiles;
+        for (int m = m0; m < m1; ++m) {
+            const uint32_t d = tbase + (uint32_t)((rd & 1) * kTcBwdGroup + (m - m0)) * kCh;
+            const uint64_t off = (uint64_t)((uint32_t)m * 128u);
+#pragma unroll
+            for (int j = 0; j < kTapsB * 2; ++j) {
+                tc::mma_bf16(d, adesc[j] + off, bdesc[j], idesc, j != 0);
+                tc::mma_bf16(d, adesc[j] + off + lo_off, bdesc[j], idesc, 1u);
+            }
         }
+        tc::commit(bar0 + 8u * (uint32_t)(rd & 1));
+    };
+    uint32_t uses[2] = {0u, 0u};
+    int ok = 1;
+    for (int it = blockIdx.x; ok && it < n * g.YB; it += gridDim.x) {
+        const int b = it / g.YB, y0 = (it - b * g.YB) * g.R;
+        for (int i = tid; i < (g.R + 2) * g.L * 8; i += blockDim.x) { // rows y0 .. y0+R+1, hi and lo
+            const int rho = i / (g.L * 8), rem = i - rho * g.L * 8, x = rem >> 3, pl = rem & 7, yy = y0 + rho;
+            const bool inside = yy < g.L;
+            const bf16 *src = (pl < 4 ? dzh : dzl) + (((size_t)b * g.L + (inside ? yy : 0)) * g.L + x) * kCh + (pl & 3) * 8;
+            const uint32_t dst = sb + (uint32_t)pl * g.plane_bytes + (uint32_t)(4 + rho * g.P + x) * 16u;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(inside ? 16 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        tc::fence_smem_for_async();
+        tc::fence_before_sync();
         __syncthreads();
-        if (rr < R && y < L) {
-            float acc[4][4];
+        tc::fence_after_sync();
+        if (tid == 0)
+            issue(0);
+        for (int rd = 0; rd < rounds; ++rd) {
+            if (tid == 0 && rd + 1 < rounds)
+                issue(rd + 1);
+            const int s = rd & 1;
+            const bool got = tc::mbar_wait(bar0 + 8u * s, uses[s] & 1u, kTcMaxPolls);
+            ++uses[s];
+            tc::fence_after_sync();
+            const int m0 = rd * kTcBwdGroup, m1 = m0 + kTcBwdGroup < g.tiles ? m0 + kTcBwdGroup : g.tiles;
+            for (int m = m0; m < m1; ++m) {
+                float v[kCh];
+                tc::ld_32x32b_x32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(s * kTcBwdGroup + (m - m0)) * kCh,
+                                  v);
+                const int q = m * 128 + 32 * warp + lane, r = q / g.P, xp = q - r * g.P;
+                if (got && r < g.R && y0 + r < g.L && xp >= 2 && xp < g.L + 2) {
+                    const size_t p = ((size_t)b * g.L + y0 + r) * g.L + (xp - 2);
+                    const uint4 *mk = reinterpret_cast<const uint4 *>(mask + p * kCh);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-            const int x0 = pt * 16;
-            const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
-            const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
-#pragma unroll 1
-            for (int t = 0; t < kTapsB; ++t) {
-                const int r = -tap_dy(t) + rr, xoff = -tap_dx(t);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint4 mv = mk[k];
+                        const bf16 *m8 = reinterpret_cast<const bf16 *>(&mv);
+                        float o[8];
 #pragma unroll
-                for (int kc = 0; kc < 2; ++kc) {
-                    const int aoff = (r * PX + x0 + arow + xoff + 2) * kRowStride + kc * 16 + acol;
-                    uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
-                    ldsm_x4(smem_u32(Xh + aoff), h0, h1, h2, h3);
-                    ldsm_x4(smem_u32(Xl + aoff), l0, l1, l2, l3);
-#pragma unroll
-                    for (int np = 0; np < 2; ++np) {
-                        uint32_t b0, b1, b2, b3;
-                        ldsm_x4(smem_u32(Ws + (t * kCh + np * 16 + brow) * kRowStride + kc * 16 + bcol), b0, b1, b2,
-                                b3);
-                        mma_bf16(acc[2 * np], h0, h1, h2, h3, b0, b1);
-                        mma_bf16(acc[2 * np], l0, l1, l2, l3, b0, b1);
-                        mma_bf16(acc[2 * np + 1], h0, h1, h2, h3, b2, b3);
-                        mma_bf16(acc[2 * np + 1], l0, l1, l2, l3, b2, b3);
+                        for (int j = 0; j < 8; ++j)
+                            o[j] = bf(m8[j]) > 0.f ? v[8 * k + j] : 0.f;
+                        uint4 hi, lo;
+                        split8(o, hi, lo);
+                        reinterpret_cast<uint4 *>(outh + p * kCh)[k] = hi;
+                        reinterpret_cast<uint4 *>(outl + p * kCh)[k] = lo;
                     }
                 }
             }
-            const int g = lane >> 2, t4 = lane & 3;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int x = x0 + g + 8 * h;
-                    if (x >= L)
-                        continue;
-                    const int c = 8 * j + 2 * t4;
-                    const size_t o = (((size_t)b * L + y) * L + x) * kCh + c;
-                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(mask_src + o);
-                    *reinterpret_cast<float2 *>(out + o) =
-                        make_float2(bf(m.x) > 0.f ? acc[j][2 * h] : 0.f, bf(m.y) > 0.f ? acc[j][2 * h + 1] : 0.f);
-                }
+            tc::fence_before_sync();
+            ok = __syncthreads_and(ok && got);
+            tc::fence_after_sync();
+            if (!ok)
+                break;
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (!ok && tid == 0)
+        atomicExch(err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        tc::tmem_free(tbase, kTcBwdCols);
 }
 
 // Stage rows y-2..y of a [n][L][L][32] BF16 activation into smem rows of L+4
@@ -489,8 +532,8 @@ __global__ void k_logq(const float *ll, double *logq, int L)
 // Last layer: dZ_{D-1}(p)[c] = (sum_t wD[t][c] dF(p - d_t)) * [h_{D-1}(p)[c] > 0]
 // (the forward read h at q + d_t for output q).  One CTA item = one row: dF of
 // rows y..y+2 staged in smem (zero padded); 4 threads per position.
-__global__ void __launch_bounds__(256) k_layerD_bwd_data(const float *dF, const float *wD, const bf16 *hD, float *dZ,
-                                                         int n, int L)
+__global__ void __launch_bounds__(256) k_layerD_bwd_data(const float *dF, const float *wD, const bf16 *hD,
+                                                         bf16 *dzh, bf16 *dzl, int n, int L)
 {
     __shared__ float W[kTapsB * kCh];
     __shared__ float G[3][kMaxL + 4];
@@ -521,18 +564,16 @@ __global__ void __launch_bounds__(256) k_layerD_bwd_data(const float *dF, const 
             const size_t p = ((size_t)b * L + y) * L + x;
             const uint4 hv = *reinterpret_cast<const uint4 *>(hD + p * kCh + c0);
             const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&hv);
-            float4 o0, o1;
-            o0.x = bf(h2[0].x) > 0.f ? acc[0] : 0.f;
-            o0.y = bf(h2[0].y) > 0.f ? acc[1] : 0.f;
-            o0.z = bf(h2[1].x) > 0.f ? acc[2] : 0.f;
-            o0.w = bf(h2[1].y) > 0.f ? acc[3] : 0.f;
-            o1.x = bf(h2[2].x) > 0.f ? acc[4] : 0.f;
-            o1.y = bf(h2[2].y) > 0.f ? acc[5] : 0.f;
-            o1.z = bf(h2[3].x) > 0.f ? acc[6] : 0.f;
-            o1.w = bf(h2[3].y) > 0.f ? acc[7] : 0.f;
-            float4 *dst = reinterpret_cast<float4 *>(dZ + p * kCh + c0);
-            dst[0] = o0;
-            dst[1] = o1;
+            float o[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                o[2 * q] = bf(h2[q].x) > 0.f ? acc[2 * q] : 0.f;
+                o[2 * q + 1] = bf(h2[q].y) > 0.f ? acc[2 * q + 1] : 0.f;
+            }
+            uint4 hi, lo;
+            split8(o, hi, lo);
+            *reinterpret_cast<uint4 *>(dzh + p * kCh + c0) = hi;
+            *reinterpret_cast<uint4 *>(dzl + p * kCh + c0) = lo;
         }
     }
 }
@@ -591,8 +632,8 @@ __global__ void __launch_bounds__(256) k_layerD_bwd_w(const float *dF, const bf1
 // hi + lo pair, activations exactly as the forward used them):
 // gW[t][o][c] = sum_p dZ(p)[o] X(p + d_t)[c] -- a 32 x 32 GEMM per tap with the
 // positions as the reduction dimension.  Warp w owns taps w and w + 8.
-__global__ void __launch_bounds__(256) k_dw32(const float *__restrict__ dZ, const bf16 *__restrict__ X,
-                                              float *__restrict__ part, int n, int L)
+__global__ void __launch_bounds__(256) k_dw32(const bf16 *__restrict__ dzh, const bf16 *__restrict__ dzl,
+                                              const bf16 *__restrict__ X, float *__restrict__ part, int n, int L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int NW = (L + 15) / 16, PX = NW * 16 + 4, PZ = NW * 16;
@@ -615,10 +656,14 @@ __global__ void __launch_bounds__(256) k_dw32(const float *__restrict__ dZ, cons
         __syncthreads();
         for (int i = tid; i < PZ * 4; i += blockDim.x) {
             const int xi = i / 4, ch = i % 4;
-            bf16 hi[8], lo[8];
-            stage_split(dZ + (((size_t)b * L + y) * L + (xi < L ? xi : 0)) * kCh + ch * 8, xi < L, hi, lo);
-            *reinterpret_cast<uint4 *>(Zs + xi * kRowStride + ch * 8) = *reinterpret_cast<uint4 *>(hi);
-            *reinterpret_cast<uint4 *>(Zl + xi * kRowStride + ch * 8) = *reinterpret_cast<uint4 *>(lo);
+            uint4 hi = make_uint4(0u, 0u, 0u, 0u), lo = hi;
+            if (xi < L) {
+                const size_t off = (((size_t)b * L + y) * L + xi) * kCh + ch * 8;
+                hi = *reinterpret_cast<const uint4 *>(dzh + off);
+                lo = *reinterpret_cast<const uint4 *>(dzl + off);
+            }
+            *reinterpret_cast<uint4 *>(Zs + xi * kRowStride + ch * 8) = hi;
+            *reinterpret_cast<uint4 *>(Zl + xi * kRowStride + ch * 8) = lo;
         }
         for (int i = tid; i < 3 * PX * 4; i += blockDim.x) {
             const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
@@ -713,8 +758,8 @@ __global__ void k_dw_reduce(const float *__restrict__ part, int nparts, float *g
 // gb1[o] = sum_p dZ1(p)[o].  One CTA item = one row: spins of rows y-2..y and
 // dZ1 of row y staged in smem; thread i owns outputs i and i + 256 of the
 // 32 x (12 + 1); one atomic per output per CTA.
-__global__ void __launch_bounds__(256) k_layer1_bwd_w(const float *dZ1, const int8_t *spins, float *g, DevParams P,
-                                                      int n, int L)
+__global__ void __launch_bounds__(256) k_layer1_bwd_w(const bf16 *dzh, const bf16 *dzl, const int8_t *spins, float *g,
+                                                      DevParams P, int n, int L)
 {
     __shared__ float S[3][kMaxL + 4];
     __shared__ __align__(16) float Z[kMaxL * kCh];
@@ -728,9 +773,15 @@ __global__ void __launch_bounds__(256) k_layer1_bwd_w(const float *dZ1, const in
             const int r = i / (L + 4), xx = i - r * (L + 4) - 2, yy = y - 2 + r;
             S[r][xx + 2] = (yy >= 0 && xx >= 0 && xx < L) ? (float)spins[((size_t)b * L + yy) * L + xx] : 0.f;
         }
-        const float4 *zr = reinterpret_cast<const float4 *>(dZ1 + ((size_t)b * L + y) * L * kCh);
-        for (int i = tid; i < L * kCh / 4; i += blockDim.x)
-            reinterpret_cast<float4 *>(Z)[i] = zr[i];
+        const uint4 *zh = reinterpret_cast<const uint4 *>(dzh + ((size_t)b * L + y) * L * kCh);
+        const uint4 *zl = reinterpret_cast<const uint4 *>(dzl + ((size_t)b * L + y) * L * kCh);
+        for (int i = tid; i < L * kCh / 8; i += blockDim.x) { // value = hi + lo
+            const uint4 h = zh[i], l = zl[i];
+            const bf16 *h8 = reinterpret_cast<const bf16 *>(&h), *l8 = reinterpret_cast<const bf16 *>(&l);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                Z[8 * i + k] = bf(h8[k]) + bf(l8[k]);
+        }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -1118,10 +1169,6 @@ VanLayout van_layout(int L, int nmax, int D)
 
 unsigned grid_for(size_t n, int threads, int sms) { return (unsigned)std::min<size_t>((n + threads - 1) / threads, (size_t)sms * 16); }
 
-size_t conv_bwd_smem(int L)
-{
-    return (size_t)kTapsB * kCh * kRowStride * 2 + (size_t)2 * (conv_rows(L) + 2) * (((L + 15) / 16) * 16 + 4) * kRowStride * 2;
-}
 size_t dw_smem(int L)
 {
     const int PZ = ((L + 15) / 16) * 16;
@@ -1153,7 +1200,7 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
     const size_t layer = (size_t)w->nmax * L * L * kCh;
     const unsigned rows = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 8);
     k_layer1_fwd<<<rows, 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n, L);
-    const TcConvGeom tg = tc_conv_geom(L);
+    const TcConvGeom tg = tc_conv_geom(L, 4);
     const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tg.YB, (size_t)w->sms * 2);
     for (int l = 1; l <= D - 2; ++l)
         k_conv32_tc<<<tcg, 128, tg.smem_bytes, w->stream>>>(w->H + (l - 1) * layer, w->H + l * layer,
@@ -1176,20 +1223,26 @@ cudaError_t backward(mc_van *w, int n)
     const bf16 *hD = w->H + (D - 2) * layer;
     const unsigned rows = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 8);
     const unsigned rg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 12);
-    k_layerD_bwd_data<<<rows, 256, 0, w->stream>>>(w->dF, w->wD, hD, w->dZa, n, L);
+    // gradients as BF16 hi + lo pairs, each pair in the space of one FP32 buffer
+    const size_t cap = (size_t)w->nmax * L * L * kCh;
+    bf16 *dzh = reinterpret_cast<bf16 *>(w->dZa), *dzl = dzh + cap;
+    bf16 *nxh = reinterpret_cast<bf16 *>(w->dZb), *nxl = nxh + cap;
+    k_layerD_bwd_data<<<rows, 256, 0, w->stream>>>(w->dF, w->wD, hD, dzh, dzl, n, L);
     k_layerD_bwd_w<<<rg, 256, 0, w->stream>>>(w->dF, hD, w->g, w->dp, n, L);
-    float *dz = w->dZa, *dzn = w->dZb;
-    const unsigned cg = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 3);
+    const TcConvGeom tgb = tc_conv_geom(L, 8);
+    const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tgb.YB, (size_t)w->sms * 2);
     // k_dw32 holds 124 registers x 256 threads: two CTAs per SM, one wave
     const unsigned dwg = (unsigned)std::min<size_t>(std::min<size_t>((size_t)n * L, (size_t)w->sms * 2), kMaxDwBlocks);
     for (int l = D - 2; l >= 1; --l) { // hidden layer l: input H[l-1], output H[l], grad dz wrt its pre-activation
-        k_dw32<<<dwg, 256, dw_smem(L), w->stream>>>(dz, w->H + (l - 1) * layer, w->dwpart, n, L);
+        k_dw32<<<dwg, 256, dw_smem(L), w->stream>>>(dzh, dzl, w->H + (l - 1) * layer, w->dwpart, n, L);
         k_dw_reduce<<<(kDwPart + 255) / 256, 256, 0, w->stream>>>(w->dwpart, (int)dwg, w->g, w->dp, l);
-        k_conv32_bwd<<<cg, 256, conv_bwd_smem(L), w->stream>>>(dz, dzn, w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
-                                                               w->H + (l - 1) * layer, n, L);
-        std::swap(dz, dzn);
+        k_conv32_bwd_tc<<<tcg, 128, tgb.smem_bytes, w->stream>>>(dzh, dzl, nxh, nxl,
+                                                                 w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
+                                                                 w->H + (l - 1) * layer, n, tgb, w->err);
+        std::swap(dzh, nxh);
+        std::swap(dzl, nxl);
     }
-    k_layer1_bwd_w<<<rg, 256, 0, w->stream>>>(dz, w->spins, w->g, w->dp, n, L);
+    k_layer1_bwd_w<<<rg, 256, 0, w->stream>>>(dzh, dzl, w->spins, w->g, w->dp, n, L);
     return cudaGetLastError();
 }
 
@@ -1276,9 +1329,10 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     cudaError_t e = cudaMemsetAsync(w->ws, 0, o.hist, w->stream); // params, Adam state, buffers
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_conv32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc_conv_geom(L).smem_bytes);
+                                 (int)tc_conv_geom(L, 4).smem_bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv32_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_bwd_smem(L));
+        e = cudaFuncSetAttribute(k_conv32_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_conv_geom(L, 8).smem_bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dw32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(L));
     if (e == cudaSuccess)

@@ -224,3 +224,23 @@ def test_full_size_L64_sampler_log_prob_and_gradients():
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         assert cos > 1 - 1e-5 and rel < 1e-2, (l, cos, rel)
     net.close()
+
+
+@pytest.mark.parametrize("L", [2, 6, 128])
+def test_log_prob_extreme_lattice_sides(L):
+    """The smallest lattices (one padded tile, rows past the lattice) and the
+    largest side the network supports (several rows per tile item): log q of a
+    few configurations against the BF16-activation oracle, and the gradient
+    path runs."""
+    n = 3
+    p = bf16_params(seed=11, bias=0.2)
+    net = mc.VAN(L, batch=n, depth=6, seed=0)
+    net.set_params(mc.mc.van_pack(p))
+    rng = np.random.default_rng(12)
+    s = np.where(rng.random((n, L, L)) < 0.5, 1, -1).astype(np.int8)
+    g = net.log_prob(torch.from_numpy(s).cuda()).cpu().numpy()
+    ob = van.log_prob(p, s.astype(np.float64), act="bf16")
+    assert np.max(np.abs(g - ob) / np.abs(ob)) < 1e-4, (g, ob)
+    loss = net.train_step(torch.from_numpy(s).cuda(), lr=0.0, apply=False)
+    assert np.isfinite(loss)
+    net.close()

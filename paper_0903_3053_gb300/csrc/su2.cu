@@ -29,10 +29,10 @@
 namespace mc {
 namespace {
 
-// 256 threads, at least 6 blocks per SM (40 registers, no spills): the phase
-// is bound by the latency of the 18 neighbour-link loads, and 48 resident warps
-// hide it better than the 40 an unconstrained build allows (+14% measured on
-// 4 x 32^4).
+// 256 threads, at least 6 blocks per SM (40 registers; ptxas spills 12-48
+// bytes per thread, about 1% of the kernel's load requests): the phase is bound
+// by the latency of the 18 neighbour-link loads, and 48 resident warps hide it
+// better than the 40 an unconstrained build allows (+14% measured on 4 x 32^4).
 template <int P, int MU, bool REC>
 __global__ void __launch_bounds__(256, 6) k_phase(SweepArgs a)
 {

@@ -152,7 +152,7 @@ Plan make_plan(int32_t n, const mc_chain_desc *chains, int32_t layout, int64_t c
         } else {
             const size_t sites = (size_t)d.L[0] * d.L[1] * d.L[2] * d.L[3];
             staging = std::max(staging, sites * 4 * 16);
-            meas_blocks += (sites + 255) / 256;
+            meas_blocks += (sites / 2 + kPlaqThreads - 1) / kPlaqThreads;
         }
     }
     p.partial_count = 2 * meas_blocks;

@@ -80,6 +80,11 @@ __device__ __forceinline__ void latch_error(DevState *st, int code, int info)
 // kernel, whose later phases read what earlier phases (possibly on other SMs
 // of the cluster) wrote, loads through L2, the device's point of coherence.
 constexpr int kLdReadOnly = 0, kLdPlain = 1, kLdCoherent = 2;
+
+// Threads per block of the SU(2) plaquette measurement; each thread measures
+// one x1 pair of sites, so a chain of N sites has ceil(N / (2 kPlaqThreads))
+// partial-sum blocks.
+constexpr int kPlaqThreads = 128;
 template <int LD, typename T>
 __device__ __forceinline__ T lat_load(const T *p)
 {

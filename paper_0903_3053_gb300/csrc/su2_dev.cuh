@@ -300,19 +300,47 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Spatial and temporal sums of (1/2) Tr U_munu(x) (Eq. (3)) over the six
-// plaquettes with corner at canonical site s; FP32 products.
-template <int LD>
-__device__ __forceinline__ void su2_site_plaquettes(const float4 *U, const Su2Chain &ch, uint32_t s, float &fs,
-                                                    float &ft)
+// (1/2) Tr U_munu(x) of Eq. (3) for the six planes at a site, from its own
+// links Ux[mu] and the forward links Uf[mu][nu] = U_nu(x + mu); spatial planes
+// summed into fs, temporal (mu = 0) into ft, in a fixed order.
+__device__ __forceinline__ void plaquettes_of(const float4 (&Ux)[4], const float4 (&Uf)[4][4], float &fs, float &ft)
 {
-    Site x;
+    fs = 0.f;
+    ft = 0.f;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int nu = mu + 1; nu < 4; ++nu) {
+            // (1/2) Tr[U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+] = A . B
+            const float4 A = qmul(Ux[mu], Uf[mu][nu]);
+            const float4 B = qmul(Ux[nu], Uf[nu][mu]);
+            const float h = qdot(A, B);
+            if (mu == 0)
+                ft += h;
+            else
+                fs += h;
+        }
+}
+
+__device__ __forceinline__ Site site_of_canonical(const Su2Chain &ch, uint32_t s)
+{
     uint32_t q1, q2, c[4];
     fast_divmod(s, ch.div1, q1, c[1]);
     fast_divmod(q1, ch.div2, q2, c[2]);
     fast_divmod(q2, ch.div3, c[0], c[3]);
+    Site x;
     for (int m = 0; m < 4; ++m)
         x.x[m] = (int)c[m];
+    return x;
+}
+
+// Spatial and temporal sums of (1/2) Tr U_munu(x) over the six plaquettes with
+// corner at canonical site s; FP32 products.
+template <int LD>
+__device__ __forceinline__ void su2_site_plaquettes(const float4 *U, const Su2Chain &ch, uint32_t s, float &fs,
+                                                    float &ft)
+{
+    const Site x = site_of_canonical(ch, s);
     const int p = (x.x[0] + x.x[1] + x.x[2] + x.x[3]) & 1, q = 1 - p;
     const uint32_t e = s >> 1;
     float4 Ux[4], Uf[4][4]; // Uf[mu][nu] = U_nu(x + mu)
@@ -332,21 +360,48 @@ __device__ __forceinline__ void su2_site_plaquettes(const float4 *U, const Su2Ch
             if (nu != mu)
                 Uf[mu][nu] = load_link<LD>(U, ch.nh, q, nu, ef);
     }
-    fs = 0.f;
-    ft = 0.f;
+    plaquettes_of(Ux, Uf, fs, ft);
+}
+
+// The same sums for the two sites of an x1 pair, canonical 2j and 2j + 1 (L1 is
+// even, so both lie in one row and have opposite parities; both have index j
+// within their parity).  The second site's own links are the first site's
+// forward links along x1, so the pair takes 29 link loads instead of 32, and
+// one thread carries two independent products chains.
+template <int LD>
+__device__ __forceinline__ void su2_pair_plaquettes(const float4 *U, const Su2Chain &ch, uint32_t j, float &fs0,
+                                                    float &ft0, float &fs1, float &ft1)
+{
+    const Site x = site_of_canonical(ch, 2 * j);
+    Site y = x;
+    y.x[1] += 1;
+    const int p0 = (x.x[0] + x.x[1] + x.x[2] + x.x[3]) & 1, p1 = 1 - p0;
+    const uint32_t nh = ch.nh;
+    float4 U0[4], U1[4], F0[4][4], F1[4][4]; // F0[mu][nu] = U_nu(x + mu), F1[mu][nu] = U_nu(y + mu)
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu)
+    for (int mu = 0; mu < 4; ++mu) {
+        U0[mu] = load_link<LD>(U, nh, p0, mu, j);
+        U1[mu] = load_link<LD>(U, nh, p1, mu, j);
+    }
 #pragma unroll
-        for (int nu = mu + 1; nu < 4; ++nu) {
-            // (1/2) Tr[U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+] = A . B
-            const float4 A = qmul(Ux[mu], Uf[mu][nu]);
-            const float4 B = qmul(Ux[nu], Uf[nu][mu]);
-            const float h = qdot(A, B);
-            if (mu == 0)
-                ft += h;
-            else
-                fs += h;
-        }
+    for (int nu = 0; nu < 4; ++nu)
+        F0[1][nu] = U1[nu];
+    const uint32_t e00 = canonical(ch, step<0>(ch, x, +1)) >> 1, e02 = canonical(ch, step<2>(ch, x, +1)) >> 1,
+                   e03 = canonical(ch, step<3>(ch, x, +1)) >> 1;
+    const uint32_t e10 = canonical(ch, step<0>(ch, y, +1)) >> 1, e11 = canonical(ch, step<1>(ch, y, +1)) >> 1,
+                   e12 = canonical(ch, step<2>(ch, y, +1)) >> 1, e13 = canonical(ch, step<3>(ch, y, +1)) >> 1;
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu != 0) F0[0][nu] = load_link<LD>(U, nh, p1, nu, e00);
+        if (nu != 2) F0[2][nu] = load_link<LD>(U, nh, p1, nu, e02);
+        if (nu != 3) F0[3][nu] = load_link<LD>(U, nh, p1, nu, e03);
+        if (nu != 0) F1[0][nu] = load_link<LD>(U, nh, p0, nu, e10);
+        if (nu != 1) F1[1][nu] = load_link<LD>(U, nh, p0, nu, e11);
+        if (nu != 2) F1[2][nu] = load_link<LD>(U, nh, p0, nu, e12);
+        if (nu != 3) F1[3][nu] = load_link<LD>(U, nh, p0, nu, e13);
+    }
+    plaquettes_of(U0, F0, fs0, ft0);
+    plaquettes_of(U1, F1, fs1, ft1);
 }
 
 }  // namespace

@@ -146,8 +146,12 @@ MC_API mc_status mc_read_series(mc_ctx *ctx, mc_record *host_dst, int64_t max_pe
 
 /* Canonical configuration of one chain, to/from host or device memory
  * (dst_is_device / src_is_device).  Ising: MC_FMT_INT8 or MC_FMT_BITS;
- * SU(2): MC_FMT_F32.  mc_get_config is synchronous; mc_set_config is async but
- * the source may be reused as soon as it returns when it is host memory. */
+ * SU(2): MC_FMT_F32.  Page-locked host memory (allocated or registered through
+ * CUDA) is read or written in place by the layout-conversion kernel; other host
+ * memory passes through the context's staging region with a copy.
+ * mc_get_config is synchronous.  mc_set_config is asynchronous on the context's
+ * stream: a device or page-locked source must stay unchanged until the next
+ * synchronising call; other host memory may be reused when the call returns. */
 MC_API mc_status mc_get_config(mc_ctx *ctx, int32_t chain, int32_t fmt, void *dst, int32_t dst_is_device);
 MC_API mc_status mc_set_config(mc_ctx *ctx, int32_t chain, int32_t fmt, const void *src, int32_t src_is_device);
 MC_API size_t mc_config_bytes(const mc_ctx *ctx, int32_t chain, int32_t fmt); /* 0 if invalid */

@@ -662,6 +662,21 @@ size_t mc_config_bytes(const mc_ctx *c, int32_t chain, int32_t fmt)
     return fmt == MC_FMT_F32 ? su2_config_bytes(c->su2[chain]) : 0;
 }
 
+// Device address of a host buffer the GPU can read and write in place
+// (page-locked memory, allocated or registered through CUDA), else nullptr.
+static void *device_view_of_host(void *host)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError(); // clear the non-sticky error of an unknown pointer
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Host buffers: page-locked memory is read or written by the conversion kernel
+// directly (one pass over the interconnect); other host memory goes through
+// the staging region with a copy.
 static mc_status config_io(mc_ctx *c, int32_t chain, int32_t fmt, void *buf, int32_t is_device, bool to_lattice)
 {
     if (!c || !buf)
@@ -672,14 +687,22 @@ static mc_status config_io(mc_ctx *c, int32_t chain, int32_t fmt, void *buf, int
     if (bytes == 0)
         return fail(MC_EINVAL, "format not valid for this chain (Ising: MC_FMT_INT8, or MC_FMT_BITS with Lx % 32 == 0; "
                                "SU(2): MC_FMT_F32)");
-    void *dev = is_device ? buf : c->d_staging;
+    void *dev = buf;
+    bool staged = false;
+    if (!is_device) {
+        dev = device_view_of_host(buf);
+        if (!dev) {
+            dev = c->d_staging;
+            staged = true;
+        }
+    }
     cudaError_t e = cudaSuccess;
-    if (to_lattice && !is_device)
+    if (to_lattice && staged)
         e = cudaMemcpyAsync(dev, buf, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = c->kind == MC_KIND_ISING ? ising_config_io(c, chain, fmt, dev, to_lattice)
                                      : su2_config_io(c, chain, dev, to_lattice);
-    if (e == cudaSuccess && !to_lattice && !is_device)
+    if (e == cudaSuccess && !to_lattice && staged)
         e = cudaMemcpyAsync(buf, dev, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "configuration copy");

@@ -280,38 +280,55 @@ __global__ void k_msc_to_int8(IsingChain ch, const uint32_t *src, int8_t *dst)
 }
 
 // Canonical bit rows (bit b of word v of row y = site x = 32 v + b) <-> MSC.
+// Even bits of x to its low half and odd bits to its high half (the outer
+// perfect unshuffle written as four delta swaps; Warren, "Hacker's Delight",
+// Sec. 7-2), and the inverse shuffle.
+__device__ __forceinline__ uint32_t bit_unshuffle(uint32_t x)
+{
+    uint32_t t;
+    t = (x ^ (x >> 1)) & 0x22222222u; x ^= t ^ (t << 1);
+    t = (x ^ (x >> 2)) & 0x0C0C0C0Cu; x ^= t ^ (t << 2);
+    t = (x ^ (x >> 4)) & 0x00F000F0u; x ^= t ^ (t << 4);
+    t = (x ^ (x >> 8)) & 0x0000FF00u; x ^= t ^ (t << 8);
+    return x;
+}
+__device__ __forceinline__ uint32_t bit_shuffle(uint32_t x)
+{
+    uint32_t t;
+    t = (x ^ (x >> 8)) & 0x0000FF00u; x ^= t ^ (t << 8);
+    t = (x ^ (x >> 4)) & 0x00F000F0u; x ^= t ^ (t << 4);
+    t = (x ^ (x >> 2)) & 0x0C0C0C0Cu; x ^= t ^ (t << 2);
+    t = (x ^ (x >> 1)) & 0x22222222u; x ^= t ^ (t << 1);
+    return x;
+}
+
+// Canonical bit rows <-> the two colour planes.  One thread per 64-site chunk u
+// = y W + w of a row (canonical words 2u, 2u + 1, read or written once, 8
+// contiguous bytes per thread, so that a page-locked host buffer can be read
+// or written by the kernel directly): its even-x sites are word u of plane
+// y & 1, its odd-x sites word u of the other plane.
 __global__ void k_msc_from_bits(IsingChain ch, const uint32_t *src, uint32_t *dst)
 {
-    const uint32_t nw = ch.Ly * ch.W, rw = ch.Lx >> 5;
+    const uint32_t nw = ch.Ly * ch.W;
     const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= 2 * nw)
+    if (u >= nw)
         return;
-    const uint32_t c = u / nw, t = u - c * nw, y = t / ch.W, w = t - y * ch.W;
-    const uint32_t o = (y + c) & 1u;
-    uint32_t word = 0;
-    for (int b = 0; b < 32; ++b) {
-        const uint32_t x = 64 * w + 2 * b + o;
-        word |= ((src[y * rw + (x >> 5)] >> (x & 31u)) & 1u) << b;
-    }
-    dst[u] = word;
+    const uint32_t y = u / ch.W;
+    const uint32_t a = bit_unshuffle(src[2 * u]), b = bit_unshuffle(src[2 * u + 1]);
+    dst[(y & 1u) * nw + u] = (a & 0xFFFFu) | (b << 16);          // x even
+    dst[((y + 1u) & 1u) * nw + u] = (a >> 16) | (b & 0xFFFF0000u); // x odd
 }
 
 __global__ void k_msc_to_bits(IsingChain ch, const uint32_t *src, uint32_t *dst)
 {
-    // one thread per canonical word; gathers from both planes
-    const uint32_t rw = ch.Lx >> 5, nw = ch.Ly * ch.W;
-    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= ch.Ly * rw)
+    const uint32_t nw = ch.Ly * ch.W;
+    const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nw)
         return;
-    const uint32_t y = v / rw, vw = v - y * rw;
-    uint32_t word = 0;
-    for (int b = 0; b < 32; ++b) {
-        const uint32_t x = 32 * vw + b;
-        const uint32_t c = (x + y) & 1u, j = x >> 1;
-        const uint32_t msc = src[c * nw + y * ch.W + (j >> 5)];
-        word |= ((msc >> (j & 31u)) & 1u) << b;
-    }
-    dst[v] = word;
+    const uint32_t y = u / ch.W;
+    const uint32_t even = src[(y & 1u) * nw + u], odd = src[((y + 1u) & 1u) * nw + u];
+    dst[2 * u] = bit_shuffle((even & 0xFFFFu) | (odd << 16));
+    dst[2 * u + 1] = bit_shuffle((even >> 16) | (odd & 0xFFFF0000u));
 }
 
 __global__ void k_int8_from_bits(IsingChain ch, const uint32_t *src, int8_t *dst)
@@ -507,9 +524,9 @@ cudaError_t ising_config_io(mc_ctx *c, int chain, int fmt, void *buf, bool to_la
     char *lat = c->d_lattice + ch.spin_off;
     const size_t n = (size_t)ch.Lx * ch.Ly;
     if (c->layout == MC_LAYOUT_INT8) {
-        if (fmt == MC_FMT_INT8)
-            return to_lattice ? cudaMemcpyAsync(lat, buf, n, cudaMemcpyDeviceToDevice, c->ls)
-                              : cudaMemcpyAsync(buf, lat, n, cudaMemcpyDeviceToDevice, c->ls);
+        if (fmt == MC_FMT_INT8) // buf: device memory or page-locked host memory
+            return to_lattice ? cudaMemcpyAsync(lat, buf, n, cudaMemcpyDefault, c->ls)
+                              : cudaMemcpyAsync(buf, lat, n, cudaMemcpyDefault, c->ls);
         if (to_lattice)
             k_int8_from_bits<<<blocks_for(n, 256), 256, 0, c->ls>>>(ch, static_cast<const uint32_t *>(buf),
                                                                         reinterpret_cast<int8_t *>(lat));
@@ -527,9 +544,9 @@ cudaError_t ising_config_io(mc_ctx *c, int chain, int fmt, void *buf, bool to_la
             k_msc_to_int8<<<blocks_for(words, 256), 256, 0, c->ls>>>(ch, msc, static_cast<int8_t *>(buf));
     } else {
         if (to_lattice)
-            k_msc_from_bits<<<blocks_for(words, 256), 256, 0, c->ls>>>(ch, static_cast<const uint32_t *>(buf), msc);
+            k_msc_from_bits<<<blocks_for(words / 2, 256), 256, 0, c->ls>>>(ch, static_cast<const uint32_t *>(buf), msc);
         else
-            k_msc_to_bits<<<blocks_for(n / 32, 256), 256, 0, c->ls>>>(ch, msc, static_cast<uint32_t *>(buf));
+            k_msc_to_bits<<<blocks_for(words / 2, 256), 256, 0, c->ls>>>(ch, msc, static_cast<uint32_t *>(buf));
     }
     return cudaGetLastError();
 }

@@ -250,6 +250,12 @@ class Batch:
         n = int(np.prod(c.L))
         return (n, 4, 4), np.float32
 
+    def _check_tensor(self, chain: int, fmt: int, t):
+        shape, dt = self._shape(chain, fmt)
+        need = int(np.prod(shape)) * np.dtype(dt).itemsize
+        if not t.is_contiguous() or t.numel() * t.element_size() < need:
+            raise ValueError(f"tensor must be contiguous and hold at least {need} bytes")
+
     def get_config(self, chain: int = 0, fmt: int | None = None) -> np.ndarray:
         fmt = self._default_fmt() if fmt is None else fmt
         shape, dt = self._shape(chain, fmt)
@@ -266,17 +272,27 @@ class Batch:
 
     def get_config_device(self, chain: int, out_tensor, fmt: int | None = None):
         fmt = self._default_fmt() if fmt is None else fmt
+        self._check_tensor(chain, fmt, out_tensor)
         _check(load().mc_get_config(self._ctx, int(chain), int(fmt), ctypes.c_void_p(out_tensor.data_ptr()), 1))
 
     def set_config_device(self, chain: int, tensor, fmt: int | None = None):
         fmt = self._default_fmt() if fmt is None else fmt
+        self._check_tensor(chain, fmt, tensor)
         _check(load().mc_set_config(self._ctx, int(chain), int(fmt), ctypes.c_void_p(tensor.data_ptr()), 1))
 
     def set_config_host_async(self, chain: int, host_tensor, fmt: int | None = None):
         """Asynchronous upload from a page-locked host tensor (keep it unchanged
         until the next synchronising call)."""
         fmt = self._default_fmt() if fmt is None else fmt
+        self._check_tensor(chain, fmt, host_tensor)
         _check(load().mc_set_config(self._ctx, int(chain), int(fmt), ctypes.c_void_p(host_tensor.data_ptr()), 0))
+
+    def get_config_host(self, chain: int, host_tensor, fmt: int | None = None):
+        """Synchronous download into a caller-owned host tensor (page-locked
+        memory is written in place by the conversion kernel)."""
+        fmt = self._default_fmt() if fmt is None else fmt
+        self._check_tensor(chain, fmt, host_tensor)
+        _check(load().mc_get_config(self._ctx, int(chain), int(fmt), ctypes.c_void_p(host_tensor.data_ptr()), 0))
 
     def _default_fmt(self):
         return MC_FMT_INT8 if self.kind == MC_KIND_ISING else MC_FMT_F32

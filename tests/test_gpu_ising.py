@@ -126,6 +126,32 @@ def test_config_roundtrip_and_formats():
         b.close()
 
 
+def test_config_through_page_locked_host_memory():
+    """Page-locked host buffers are read and written in place by the layout
+    conversion kernels (no staging copy); results equal the staged path's."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    s = np.where(rng.random((64, 192)) < 0.5, 1, -1).astype(np.int8)
+    bits = np.packbits((s > 0).astype(np.uint8), axis=1, bitorder="little").view(np.uint32)
+    for layout in (mc.MC_LAYOUT_INT8, mc.MC_LAYOUT_MSC32):
+        b = mc.Batch([mc.ising((192, 64), 0.4, seed=1)], layout=layout)
+        b.set_config_host_async(0, torch.from_numpy(s.copy()).pin_memory())
+        b.sync()
+        np.testing.assert_array_equal(b.get_config(0), s)
+        b.set_config(0, -s)
+        hb = torch.from_numpy(bits.view(np.int32).copy()).pin_memory()
+        b.set_config_host_async(0, hb, mc.MC_FMT_BITS)
+        b.sync()
+        np.testing.assert_array_equal(b.get_config(0), s)
+        out_bits = torch.zeros(bits.shape, dtype=torch.int32).pin_memory()
+        b.get_config_host(0, out_bits, mc.MC_FMT_BITS)
+        np.testing.assert_array_equal(out_bits.numpy().view(np.uint32), bits)
+        out8 = torch.zeros(s.shape, dtype=torch.int8).pin_memory()
+        b.get_config_host(0, out8)
+        np.testing.assert_array_equal(out8.numpy(), s)
+        b.close()
+
+
 def test_resume_is_bit_exact():
     """Checkpoint = configuration + sweep counter (counter-based stream)."""
     c = mc.ising(128, BC, seed=11)

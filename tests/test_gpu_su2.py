@@ -73,12 +73,18 @@ def test_multi_sweep_trajectory_follows_oracle():
         q = g.copy()  # continue from the GPU's own FP32 state
 
 
-def test_plaquette_on_fixed_configuration():
-    L = (8, 6, 4, 6)
-    rng = np.random.default_rng(1)
+def _random_links(L, seed):
+    rng = np.random.default_rng(seed)
     q = rng.normal(size=(int(np.prod(L)), 4, 4))
     q /= np.linalg.norm(q, axis=2, keepdims=True)
-    q = f32_roundtrip(q)
+    return f32_roundtrip(q)
+
+
+# L1 = 2 makes the x1 pair of the measuring thread wrap onto itself; 8x6x4x6
+# has 576 pairs, a ragged last block of the 128-pair measurement blocks.
+@pytest.mark.parametrize("L", [(8, 6, 4, 6), (2, 2, 2, 2), (4, 2, 6, 2), (6, 10, 2, 4)])
+def test_plaquette_on_fixed_configuration(L):
+    q = _random_links(L, 1)
     b = mc.Batch([mc.su2(L, 2.0, seed=1)])
     b.set_config(0, q.astype(np.float32))
     m = b.measure(0)
@@ -86,6 +92,35 @@ def test_plaquette_on_fixed_configuration():
     assert abs(m["P"] - want[0]) < 1e-6
     assert abs(m["Ps"] - want[1]) < 1e-6
     assert abs(m["Pt"] - want[2]) < 1e-6
+    b.close()
+
+
+def test_config_through_page_locked_host_memory():
+    torch = pytest.importorskip("torch")
+    L = (4, 6, 2, 4)
+    q = _random_links(L, 3).astype(np.float32)
+    b = mc.Batch([mc.su2(L, 2.0, seed=1)])
+    b.set_config_host_async(0, torch.from_numpy(q.copy()).pin_memory())
+    b.sync()
+    np.testing.assert_array_equal(b.get_config(0), q)
+    out = torch.zeros(q.shape, dtype=torch.float32).pin_memory()
+    b.get_config_host(0, out)
+    np.testing.assert_array_equal(out.numpy(), q)
+    b.close()
+
+
+def test_plaquette_of_a_batch_of_shapes():
+    """Several chains of different shapes in one measurement launch (per-chain
+    block table of the pair kernel)."""
+    shapes = [(4, 4, 4, 4), (2, 6, 2, 8), (6, 2, 4, 2), (8, 8, 6, 4)]
+    qs = [_random_links(L, 10 + i) for i, L in enumerate(shapes)]
+    b = mc.Batch([mc.su2(L, 2.0, seed=1, chain_id=i) for i, L in enumerate(shapes)], series_capacity=4)
+    for i, q in enumerate(qs):
+        b.set_config(i, q.astype(np.float32))
+    for i, (L, q) in enumerate(zip(shapes, qs)):
+        m = b.measure(i)
+        want = oracle.su2_plaquette(q, L)
+        assert abs(m["P"] - want[0]) < 1e-6 and abs(m["Ps"] - want[1]) < 1e-6 and abs(m["Pt"] - want[2]) < 1e-6
     b.close()
 
 

@@ -22,8 +22,9 @@
 // (e, sweep, TAG_HB | p<<12 | mu<<8 | t, chain); the direction uses
 // (e, sweep, TAG_DIR | p<<12 | mu<<8, chain).  Uniforms are ((r>>8)+1) 2^-24.
 // FP32 throughout (logf/cospif/sincospif/expm1f/log1pf, not the fast
-// intrinsics: __cosf/__logf moved single links by more than 1e-5), FP64 only
-// in the plaquette sums.  Site coordinates come from magic-number divisions.
+// intrinsics: __cosf/__logf moved single links by more than 1e-5); lattice-wide
+// plaquette and Polyakov sums in exact int64 fixed point, FP64 only for the
+// final averages.  Site coordinates come from magic-number divisions.
 #include "su2_dev.cuh"
 
 namespace mc {

@@ -292,14 +292,6 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // (1/2) Tr U_munu(x) of Eq. (3) for the six planes at a site, from its own
 // links Ux[mu] and the forward links Uf[mu][nu] = U_nu(x + mu); spatial planes
 // summed into fs, temporal (mu = 0) into ft, in a fixed order.

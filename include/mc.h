@@ -219,7 +219,9 @@ typedef struct mc_group mc_group; /* opaque, owned by the library */
 MC_API size_t mc_group_workspace_bytes(int32_t n_ctx, mc_ctx *const *ctxs);
 MC_API mc_status mc_group_create(mc_group **out, int32_t n_ctx, mc_ctx *const *ctxs, void *workspace,
                                  size_t workspace_bytes, void *cuda_stream);
-/* cluster_size in {1, 2, 4, 8} (0 = keep; default 4); threads_per_block a
+/* cluster_size in {1, 2, 4, 8, 16} (0 = keep; default 4; 16 is a non-portable
+ * cluster size: a device that cannot co-schedule it fails the next
+ * mc_group_sweep with MC_ECUDA); threads_per_block a
  * multiple of 32 in [64, 256] (0 = keep; default 256); a chain whose estimated
  * cost (MSC spin-flip units per sweep: Ising int8 2 per site, MSC 1 per site,
  * SU(2) 60 per link) is at least split_cost is shared by a whole cluster

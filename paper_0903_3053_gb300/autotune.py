@@ -65,7 +65,7 @@ def _time(fn, reps: int) -> float:
 
 
 def group_candidates():
-    for C in (1, 2, 4, 8):
+    for C in (1, 2, 4, 8, 16):
         for threads in (128, 256):
             for split in (-1.0, 0.0):
                 if C == 1 and split == 0.0:
@@ -85,7 +85,12 @@ def tune_group(group: "mc.Group", n_sweeps: int = 4, reps: int = 3, use_cache: b
     results = []
     for C, threads, split in group_candidates():
         group.configure(C, threads, split)
-        ms = _time(lambda: group.sweep(n_sweeps), reps) / n_sweeps
+        try:
+            ms = _time(lambda: group.sweep(n_sweeps), reps) / n_sweeps
+        except mc.MCError as err:  # e.g. a cluster size the device cannot co-schedule
+            if verbose:
+                print(f"  cluster {C} threads {threads} split {split}: unavailable ({err})", flush=True)
+            continue
         results.append((ms, C, threads, split))
         if verbose:
             print(f"  cluster {C} threads {threads} split {split}: {ms:.3f} ms/sweep", flush=True)

@@ -31,7 +31,7 @@ struct mc_group;
 namespace mc {
 namespace {
 
-constexpr int kMaxCluster = 8;
+constexpr int kMaxCluster = 16; // 16 is a non-portable cluster size (opted into at group creation)
 constexpr int kMaxMembers = 16;
 
 struct GroupMember {
@@ -519,6 +519,8 @@ mc_status mc_group_create(mc_group **out, int32_t n_ctx, mc_ctx *const *ctxs, vo
         e = cudaEventCreateWithFlags(&g->fence_in, cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&g->fence_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) // allow clusters of 16 CTAs
+        e = cudaFuncSetAttribute(k_group, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     g->hm = hm;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->d_members, g->hm.data(), hm.size() * sizeof(GroupMember), cudaMemcpyHostToDevice, st);
@@ -538,8 +540,9 @@ mc_status mc_group_configure(mc_group *g, int32_t cluster_size, int32_t threads_
 {
     if (!g)
         return gfail(MC_EINVAL, "group is NULL");
-    if (cluster_size != 0 && cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8)
-        return gfail(MC_EINVAL, "cluster_size must be 1, 2, 4 or 8");
+    if (cluster_size != 0 && cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 &&
+        cluster_size != 16)
+        return gfail(MC_EINVAL, "cluster_size must be 1, 2, 4, 8 or 16");
     if (threads_per_block != 0 && (threads_per_block < 64 || threads_per_block > 256 || threads_per_block % 32))
         return gfail(MC_EINVAL, "threads_per_block must be a multiple of 32 in [64, 256]");
     if (cluster_size)

@@ -171,37 +171,40 @@ __device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, 
 // INLINE_FAIL: count a failed update with an inlined atomic (the persistent
 // batch kernel, where the out-of-line call costs a stack frame) instead of
 // count_heatbath_failure.
-template <int P, int MU, int LD, bool REC, bool INLINE_FAIL = false>
-__device__ __forceinline__ void su2_update_link(float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
-                                                uint32_t sweep, uint8_t *tries, DevState *state)
+// Staple of the link U_MU(x) at site e of parity P (Eq. (6)) as V = W / |W| and
+// alpha = beta |W| (V = 1 for a vanishing staple); sc = canonical site index.
+template <int P, int MU, int LD>
+__device__ __forceinline__ void su2_link_staple(const float4 *U, const Su2Chain &ch, uint32_t e, float4 &V,
+                                                float &alpha, uint32_t &sc)
 {
-    float4 V = make_float4(1.f, 0.f, 0.f, 0.f);
-    float alpha;
-    uint32_t s = 0;
-    {
-        const Site x = site_from_parity_index(ch, P, e);
-        const uint32_t sc = canonical(ch, x);
-        if (REC)
-            s = sc;
-        const float4 W = staple<MU, P, LD>(U, ch, x, sc, e);
-        const float kn = sqrtf(qdot(W, W));
-        if (kn > 0.f) {
-            const float inv = 1.0f / kn;
-            V = make_float4(W.x * inv, W.y * inv, W.z * inv, W.w * inv);
-        }
-        alpha = ch.beta * kn;
+    const Site x = site_from_parity_index(ch, P, e);
+    sc = canonical(ch, x);
+    const float4 W = staple<MU, P, LD>(U, ch, x, sc, e);
+    const float kn = sqrtf(qdot(W, W));
+    V = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (kn > 0.f) {
+        const float inv = 1.0f / kn;
+        V = make_float4(W.x * inv, W.y * inv, W.z * inv, W.w * inv);
     }
+    alpha = ch.beta * kn;
+}
+
+// Heat-bath draw and store for a link whose staple is (V, alpha): a0 by
+// Kennedy-Pendleton / Creutz, direction on S^2, U = X V, reprojection
+// (Eqs. (5), (7)).  Returns the try taken (kFailed: link unchanged, counted).
+template <int P, int MU, bool INLINE_FAIL>
+__device__ __forceinline__ int su2_link_draw(float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
+                                             uint32_t sweep, float4 V, float alpha, DevState *state)
+{
     const uint32_t sel = ((uint32_t)P << 12) | ((uint32_t)MU << 8);
     float a0 = 0.f;
     const int t = draw_a0(alpha, e, sweep, sel, ch, ks, a0);
-    if (REC)
-        tries[ch.tries_off + (size_t)s * 4 + MU] = (uint8_t)t;
     if (t == kFailed) {
         if (INLINE_FAIL)
             atomicAdd(&state->hb_failures, 1ull);
         else
             count_heatbath_failure(state);
-        return;
+        return t;
     }
     const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ks);
     const float ct = 2.0f * uniform_open0(r.x) - 1.0f;
@@ -214,6 +217,28 @@ __device__ __forceinline__ void su2_update_link(float4 *U, const Su2Chain &ch, c
     const float nrm = rsqrtf(qdot(Un, Un));
     Un = make_float4(Un.x * nrm, Un.y * nrm, Un.z * nrm, Un.w * nrm);
     U[(size_t)(P * 4 + MU) * ch.nh + e] = Un;
+    return t;
+}
+
+// Heat-bath update of the link U_MU(x) at site e of parity P (Eqs. (5)-(7)):
+// staple, a0 by Kennedy-Pendleton / Creutz, direction on S^2, U = X V,
+// reprojection.  REC: store the try taken at tries[2 e + b][MU] (canonical
+// site 2 e + b, b the parity bit of x1); a separate instantiation so that the
+// sweeps that do not record keep no extra state live across the heat-bath loop.
+// INLINE_FAIL: count a failed update with an inlined atomic (the persistent
+// batch kernel, where the out-of-line call costs a stack frame) instead of
+// count_heatbath_failure.
+template <int P, int MU, int LD, bool REC, bool INLINE_FAIL = false>
+__device__ __forceinline__ void su2_update_link(float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
+                                                uint32_t sweep, uint8_t *tries, DevState *state)
+{
+    float4 V;
+    float alpha;
+    uint32_t sc;
+    su2_link_staple<P, MU, LD>(U, ch, e, V, alpha, sc);
+    const int t = su2_link_draw<P, MU, INLINE_FAIL>(U, ch, ks, e, sweep, V, alpha, state);
+    if (REC)
+        tries[ch.tries_off + (size_t)sc * 4 + MU] = (uint8_t)t;
 }
 
 // Overrelaxation of the link U_MU(x) at site e of parity P (the

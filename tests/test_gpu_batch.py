@@ -48,7 +48,7 @@ def reference():
 
 
 @pytest.mark.parametrize("C,threads,split", [(1, 256, -1.0), (2, 128, -1.0), (4, 256, -1.0), (8, 256, 0.0),
-                                             (4, 64, 1e300), (8, 128, -1.0)])
+                                             (4, 64, 1e300), (8, 128, -1.0), (16, 256, 0.0), (16, 128, -1.0)])
 def test_group_matches_context_sweeps(reference, C, threads, split):
     bs = mixed_batches()
     g = mc.Group(bs)

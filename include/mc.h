@@ -89,7 +89,8 @@ typedef struct {
     int64_t sweep; /* global index of the sweep after which it was taken (0-based) */
     int64_t E;     /* Ising: H of Eq. (1), exact */
     int64_t M;     /* Ising: sum of spins, exact */
-    double P;      /* SU(2): plaquette (1/6N) sum_x sum_{mu<nu} (1/2) Tr U_munu(x), Eq. (3); FP64 sum */
+    double P;      /* SU(2): plaquette (1/6N) sum_x sum_{mu<nu} (1/2) Tr U_munu(x), Eq. (3); FP32 per-site
+                      values, summed exactly in int64 fixed point (2^-29), averaged in FP64 */
     double Ps;     /* SU(2): spatial plaquettes only (mu, nu in 1..3) */
     double Pt;     /* SU(2): temporal plaquettes only (one index 0) */
 } mc_record;

@@ -840,12 +840,41 @@ constexpr uint32_t kTagVanMH = 0x22000000u;     // accept uniform and global fli
 constexpr int kSampleTile = 32;                 // samples per sampler CTA (two m16 tiles)
 constexpr int kAStride = kTapsB * kCh + 8;      // 424 bf16 per sample row of the gathered A tile
 
+// A tile [32 samples][13 taps][32 channels] of one layer's input at position
+// (y, x): the 12 earlier-position taps from the ring `h` (hist of that layer,
+// `ring` elements per sample) by cp.async, zero-filled outside the lattice or
+// beyond the n samples, and the current position's value from Hc.  The caller
+// synchronises the block before the tile is read.
+__device__ __forceinline__ void gather_taps(bf16 *As, const bf16 *Hc, const bf16 *h, size_t ring, int s0, int n,
+                                            int L, int y, int x)
+{
+    for (int i = threadIdx.x; i < kSampleTile * kTapsB * 4; i += blockDim.x) {
+        const int s = i / (kTapsB * 4), t = (i / 4) % kTapsB, ch = i % 4, gs = s0 + s;
+        bf16 *dst = As + s * kAStride + t * kCh + ch * 8;
+        if (t == kTapsB - 1) {
+            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(Hc + s * kRowStride + ch * 8);
+        } else {
+            const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+            const bool inside = gs < n && yy >= 0 && xx >= 0 && xx < L;
+            const bf16 *src = inside ? h + (size_t)gs * ring + ((size_t)(yy % 3) * L + xx) * kCh + ch * 8 : h;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                         "r"(inside ? 16 : 0)
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Autoregressive sampling, one position k = y L + x at a time in raster order.
 // Each CTA owns 32 samples.  At step k every layer is evaluated at position k
 // only: its 13 taps come from the ring hist[l][sample][row % 3][x][c] of that
 // layer's earlier outputs (rows y-2..y) and from the value just computed at k.
 // s_k = +1 iff u < sigmoid(f_k), u from Philox (k >> 2, round, TAG_SAMPLE, id)
-// word k & 3; log q accumulates log sigmoid(s_k f_k) in FP64.
+// word k & 3; log q accumulates log sigmoid(s_k f_k) in FP64.  The step is a
+// chain of dependent layers, so its time is latency: the first layer reads
+// the sampled spins from a 3-row ring in shared memory, and each later layer
+// gathers its 12 earlier-position taps of all 32 samples with one burst of
+// cp.async copies (zero-filled outside the lattice), one round trip per layer.
 __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, const float *__restrict__ w1,
                                                 const float *__restrict__ wD, const float *__restrict__ bias, int D,
                                                 int L, int n, bf16 *hist, int8_t *out, double *logq, PhiloxKey key,
@@ -860,6 +889,7 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
     float *WD = W1 + kCh * kTapsA;                                 // [13][32]
     float *Bs = WD + kTapsB * kCh;                                 // [(D-1) 32 + 1]
     float *Fs = Bs + (D - 1) * kCh + 1;                            // [32] logits
+    int8_t *Sr = reinterpret_cast<int8_t *>(Fs + kSampleTile);     // [32][3][L] spins of rows y-2..y (row % 3)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int s0 = blockIdx.x * kSampleTile;
     for (int i = tid; i < nh * kTapsB * kCh * kCh; i += blockDim.x) {
@@ -888,7 +918,7 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
                 for (int t = 0; t < kTapsA; ++t) {
                     const int yy = y + tap_dy(t), xx = x + tap_dx(t);
                     if (yy >= 0 && xx >= 0 && xx < L)
-                        acc += W1[o * kTapsA + t] * (float)out[((size_t)gs * L + yy) * L + xx];
+                        acc += W1[o * kTapsA + t] * (float)Sr[(s * 3 + yy % 3) * L + xx];
                 }
             const bf16 h = __float2bfloat16(fmaxf(acc, 0.f));
             Hc[s * kRowStride + o] = h;
@@ -898,20 +928,7 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
         __syncthreads();
         // ---- hidden layers (tensor cores): M = 32 samples, N = 32, K = 13 x 32
         for (int l = 1; l <= nh; ++l) {
-            const bf16 *hprev = hist + (size_t)(l - 1) * n * ring;
-            for (int i = tid; i < kSampleTile * kTapsB * 4; i += blockDim.x) {
-                const int s = i / (kTapsB * 4), t = (i / 4) % kTapsB, ch = i % 4, gs = s0 + s;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (t == kTapsB - 1) {
-                    v = *reinterpret_cast<const uint4 *>(Hc + s * kRowStride + ch * 8);
-                } else if (gs < n) {
-                    const int yy = y + tap_dy(t), xx = x + tap_dx(t);
-                    if (yy >= 0 && xx >= 0 && xx < L)
-                        v = *reinterpret_cast<const uint4 *>(hprev + (size_t)gs * ring +
-                                                             ((size_t)(yy % 3) * L + xx) * kCh + ch * 8);
-                }
-                *reinterpret_cast<uint4 *>(As + s * kAStride + t * kCh + ch * 8) = v;
-            }
+            gather_taps(As, Hc, hist + (size_t)(l - 1) * n * ring, ring, s0, n, L, y, x);
             __syncthreads();
             const int mt = warp >> 2, nt = warp & 3; // 8 warps: 2 m-tiles x 4 n-tiles
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -942,17 +959,17 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
             __syncthreads();
         }
         // ---- output layer (CUDA cores): 8 lanes per sample, 4 channels each
+        gather_taps(As, Hc, hist + (size_t)nh * n * ring, ring, s0, n, L, y, x);
+        __syncthreads();
         {
             const int s = tid >> 3, part = tid & 7, gs = s0 + s;
-            const bf16 *hlast = hist + (size_t)nh * n * ring;
             float acc = 0.f;
             if (gs < n)
                 for (int t = 0; t < kTapsB; ++t) {
                     const int yy = y + tap_dy(t), xx = x + tap_dx(t);
                     if (yy < 0 || xx < 0 || xx >= L)
                         continue;
-                    const bf16 *hp = t == kTapsB - 1 ? Hc + s * kRowStride
-                                                     : hlast + (size_t)gs * ring + ((size_t)(yy % 3) * L + xx) * kCh;
+                    const bf16 *hp = As + s * kAStride + t * kCh;
 #pragma unroll
                     for (int c = part * 4; c < part * 4 + 4; ++c)
                         acc += WD[t * kCh + c] * bf(hp[c]);
@@ -973,6 +990,7 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
             const float sp = u < sigmoid(f) ? 1.f : -1.f;
             lq += (double)log_sigmoid(sp * f);
             out[((size_t)(s0 + tid) * L + y) * L + x] = (int8_t)sp;
+            Sr[(tid * 3 + slot) * L + x] = (int8_t)sp;
         }
         __syncthreads();
     }
@@ -1174,10 +1192,11 @@ size_t dw_smem(int L)
     const int PZ = ((L + 15) / 16) * 16;
     return (size_t)2 * PZ * kRowStride * 2 + (size_t)3 * (PZ + 4) * kRowStride * 2;
 }
-size_t sample_smem(int D)
+size_t sample_smem(int D, int L)
 {
     return (size_t)(D - 2) * kTapsB * kCh * kRowStride * 2 + (size_t)kSampleTile * kAStride * 2 +
-           (size_t)kSampleTile * kRowStride * 2 + (size_t)(kCh * kTapsA + kTapsB * kCh + (D - 1) * kCh + 1 + 32) * 4;
+           (size_t)kSampleTile * kRowStride * 2 + (size_t)(kCh * kTapsA + kTapsB * kCh + (D - 1) * kCh + 1 + 32) * 4 +
+           (size_t)kSampleTile * 3 * L;
 }
 
 cudaError_t prep(mc_van *w)
@@ -1336,7 +1355,7 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dw32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(L));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sample_smem(depth));
+        e = cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sample_smem(depth, L));
     if (e != cudaSuccess) {
         delete w;
         return vfail(MC_ECUDA, std::string("mc_van_create: ") + cudaGetErrorString(e));
@@ -1439,7 +1458,7 @@ mc_status mc_van_sample(mc_van *w, int32_t n, uint32_t round, const uint32_t *de
     cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n * w->L * w->L, w->stream);
     if (e == cudaSuccess) {
         const unsigned blocks = (unsigned)((n + kSampleTile - 1) / kSampleTile);
-        k_sample<<<blocks, 256, sample_smem(w->D), w->stream>>>(w->wh, w->w1, w->wD, w->bias, w->D, w->L, n, w->hist,
+        k_sample<<<blocks, 256, sample_smem(w->D, w->L), w->stream>>>(w->wh, w->w1, w->wD, w->bias, w->D, w->L, n, w->hist,
                                                                 out, lq, w->key, round, dev_ids);
         e = cudaGetLastError();
     }

@@ -190,12 +190,32 @@ __device__ __forceinline__ void su2_link_staple(const float4 *U, const Su2Chain 
     alpha = ch.beta * kn;
 }
 
-// Heat-bath draw and store for a link whose staple is (V, alpha): a0 by
-// Kennedy-Pendleton / Creutz, direction on S^2, U = X V, reprojection
+// Uniform direction on S^2 for the vector part of X in Eq. (5): cos theta =
+// 2 u1 - 1, phi = 2 pi u2 from the link's direction Philox block.
+struct S2Direction {
+    float ct, st, sphi, cphi;
+};
+
+template <int P, int MU>
+__device__ __forceinline__ S2Direction su2_direction(const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
+                                                     uint32_t sweep)
+{
+    const uint32_t sel = ((uint32_t)P << 12) | ((uint32_t)MU << 8);
+    const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ks);
+    S2Direction d;
+    d.ct = 2.0f * uniform_open0(r.x) - 1.0f;
+    sincospif(2.0f * uniform_open0(r.y), &d.sphi, &d.cphi);
+    d.st = sqrtf(fmaxf(0.f, 1.0f - d.ct * d.ct));
+    return d;
+}
+
+// Heat-bath draw and store for a link whose staple is (V, alpha) and whose
+// direction is d: a0 by Kennedy-Pendleton / Creutz, U = X V, reprojection
 // (Eqs. (5), (7)).  Returns the try taken (kFailed: link unchanged, counted).
 template <int P, int MU, bool INLINE_FAIL>
 __device__ __forceinline__ int su2_link_draw(float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
-                                             uint32_t sweep, float4 V, float alpha, DevState *state)
+                                             uint32_t sweep, float4 V, float alpha, const S2Direction &d,
+                                             DevState *state)
 {
     const uint32_t sel = ((uint32_t)P << 12) | ((uint32_t)MU << 8);
     float a0 = 0.f;
@@ -207,13 +227,8 @@ __device__ __forceinline__ int su2_link_draw(float4 *U, const Su2Chain &ch, cons
             count_heatbath_failure(state);
         return t;
     }
-    const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ks);
-    const float ct = 2.0f * uniform_open0(r.x) - 1.0f;
-    float sphi, cphi;
-    sincospif(2.0f * uniform_open0(r.y), &sphi, &cphi);
-    const float st = sqrtf(fmaxf(0.f, 1.0f - ct * ct));
     const float rad = sqrtf(fmaxf(0.f, 1.0f - a0 * a0));
-    const float4 X = make_float4(a0, rad * st * cphi, rad * st * sphi, rad * ct);
+    const float4 X = make_float4(a0, rad * d.st * d.cphi, rad * d.st * d.sphi, rad * d.ct);
     float4 Un = qmul(X, V);
     const float nrm = rsqrtf(qdot(Un, Un));
     Un = make_float4(Un.x * nrm, Un.y * nrm, Un.z * nrm, Un.w * nrm);
@@ -233,11 +248,15 @@ template <int P, int MU, int LD, bool REC, bool INLINE_FAIL = false>
 __device__ __forceinline__ void su2_update_link(float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
                                                 uint32_t sweep, uint8_t *tries, DevState *state)
 {
+    // The direction does not depend on the staple: drawn first, its Philox
+    // block and trigonometry fill the wait for the staple's 18 link loads
+    // (0.627 against 0.650 ms per sweep of 4 x 32^4, identical links).
+    const S2Direction d = su2_direction<P, MU>(ch, ks, e, sweep);
     float4 V;
     float alpha;
     uint32_t sc;
     su2_link_staple<P, MU, LD>(U, ch, e, V, alpha, sc);
-    const int t = su2_link_draw<P, MU, INLINE_FAIL>(U, ch, ks, e, sweep, V, alpha, state);
+    const int t = su2_link_draw<P, MU, INLINE_FAIL>(U, ch, ks, e, sweep, V, alpha, d, state);
     if (REC)
         tries[ch.tries_off + (size_t)sc * 4 + MU] = (uint8_t)t;
 }

@@ -155,14 +155,40 @@ __device__ __forceinline__ bool heatbath_try(int t, float alpha, uint32_t e, uin
     return u2 * u2 <= 1.0f - c * c;
 }
 
-// Heat-bath draw of a0: tries 0 .. kKpTries - 1 by Kennedy-Pendleton (skipped
-// when alpha = 0), then Creutz up to kKpTries + kCreutzTries - 1; returns the
-// try taken, or kFailed.  One loop over both samplers (measured ~2% faster on
-// 4 x 32^4 than a loop per sampler, identical draws).
-__device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, uint32_t sel, const Su2Chain &ch,
-                                       const PhiloxSchedule &ks, float &a0)
+// The part of Kennedy-Pendleton try 0 that does not depend on alpha:
+// q = -(log u1 + cos^2(2 pi u2) log u3), so that lambda^2 = q / (2 alpha), and
+// u4^2 for the acceptance test.  Computed before the staple, it fills the wait
+// for the staple's loads.
+struct KpFirstTry {
+    float q, u4sq;
+};
+
+__device__ __forceinline__ KpFirstTry kp_first_try(uint32_t e, uint32_t sweep, uint32_t sel, const Su2Chain &ch,
+                                                   const PhiloxSchedule &ks)
 {
-    for (int t = alpha > 0.f ? 0 : kKpTries; t < kKpTries + kCreutzTries; ++t) {
+    const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel, ch.chain_id), ks);
+    const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
+    const float u3 = uniform_open0(r.z), u4 = uniform_open0(r.w);
+    const float cs = cospif(2.0f * u2);
+    return KpFirstTry{-(logf(u1) + cs * cs * logf(u3)), u4 * u4};
+}
+
+// Heat-bath draw of a0: tries 0 .. kKpTries - 1 by Kennedy-Pendleton (skipped
+// when alpha = 0; try 0 from its precomputed part f), then Creutz up to
+// kKpTries + kCreutzTries - 1; returns the try taken, or kFailed.  One loop
+// over both samplers (measured ~2% faster on 4 x 32^4 than a loop per
+// sampler); the same draws as heatbath_try for every t.
+__device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, uint32_t sel, const Su2Chain &ch,
+                                       const PhiloxSchedule &ks, const KpFirstTry &f, float &a0)
+{
+    if (alpha > 0.f) {
+        const float lam2 = f.q * (0.5f / alpha);
+        if (f.u4sq <= 1.0f - lam2) {
+            a0 = 1.0f - 2.0f * lam2;
+            return 0;
+        }
+    }
+    for (int t = alpha > 0.f ? 1 : kKpTries; t < kKpTries + kCreutzTries; ++t) {
         float a;
         if (heatbath_try(t, alpha, e, sweep, sel, ch, ks, a)) {
             a0 = a;
@@ -215,11 +241,11 @@ __device__ __forceinline__ S2Direction su2_direction(const Su2Chain &ch, const P
 template <int P, int MU, bool INLINE_FAIL>
 __device__ __forceinline__ int su2_link_draw(float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
                                              uint32_t sweep, float4 V, float alpha, const S2Direction &d,
-                                             DevState *state)
+                                             const KpFirstTry &f, DevState *state)
 {
     const uint32_t sel = ((uint32_t)P << 12) | ((uint32_t)MU << 8);
     float a0 = 0.f;
-    const int t = draw_a0(alpha, e, sweep, sel, ch, ks, a0);
+    const int t = draw_a0(alpha, e, sweep, sel, ch, ks, f, a0);
     if (t == kFailed) {
         if (INLINE_FAIL)
             atomicAdd(&state->hb_failures, 1ull);
@@ -244,19 +270,31 @@ __device__ __forceinline__ int su2_link_draw(float4 *U, const Su2Chain &ch, cons
 // INLINE_FAIL: count a failed update with an inlined atomic (the persistent
 // batch kernel, where the out-of-line call costs a stack frame) instead of
 // count_heatbath_failure.
-template <int P, int MU, int LD, bool REC, bool INLINE_FAIL = false>
+template <int P, int MU, int LD, bool REC, bool INLINE_FAIL = false, int EARLY = 2>
 __device__ __forceinline__ void su2_update_link(float4 *U, const Su2Chain &ch, const PhiloxSchedule &ks, uint32_t e,
                                                 uint32_t sweep, uint8_t *tries, DevState *state)
 {
-    // The direction does not depend on the staple: drawn first, its Philox
-    // block and trigonometry fill the wait for the staple's 18 link loads
-    // (0.627 against 0.650 ms per sweep of 4 x 32^4, identical links).
-    const S2Direction d = su2_direction<P, MU>(ch, ks, e, sweep);
+    // The direction and the alpha-free part of the first heat-bath try do not
+    // depend on the staple: computed first (EARLY = 2), their Philox blocks,
+    // logarithms and trigonometry fill the wait for the staple's 18 link loads
+    // (0.609 against 0.650 ms per sweep of 4 x 32^4, identical links).  EARLY
+    // = 1 moves only the direction, 0 neither; the draws are the same.
+    const uint32_t sel = ((uint32_t)P << 12) | ((uint32_t)MU << 8);
+    S2Direction d;
+    KpFirstTry f;
+    if (EARLY >= 1)
+        d = su2_direction<P, MU>(ch, ks, e, sweep);
+    if (EARLY >= 2)
+        f = kp_first_try(e, sweep, sel, ch, ks);
     float4 V;
     float alpha;
     uint32_t sc;
     su2_link_staple<P, MU, LD>(U, ch, e, V, alpha, sc);
-    const int t = su2_link_draw<P, MU, INLINE_FAIL>(U, ch, ks, e, sweep, V, alpha, d, state);
+    if (EARLY < 2)
+        f = kp_first_try(e, sweep, sel, ch, ks);
+    if (EARLY < 1)
+        d = su2_direction<P, MU>(ch, ks, e, sweep);
+    const int t = su2_link_draw<P, MU, INLINE_FAIL>(U, ch, ks, e, sweep, V, alpha, d, f, state);
     if (REC)
         tries[ch.tries_off + (size_t)sc * 4 + MU] = (uint8_t)t;
 }
@@ -302,6 +340,14 @@ __device__ __forceinline__ void su2_overrelax_link_rt(int phase, float4 *U, cons
     }
 }
 
+// How much of the RNG-only work the persistent batch kernel moves ahead of the
+// staple (the EARLY argument of su2_update_link).  With its 128-register
+// budget the direction alone measured best on the batched workload: 0.459 ms
+// per sweep against 0.475-0.491 (direction and first try) and 0.487 (neither).
+#ifndef MC_GROUP_EARLY
+#define MC_GROUP_EARLY 1
+#endif
+
 // Runtime (P, MU) dispatch of su2_update_link for the persistent batch kernel
 // (no try record, inlined failure count).
 template <int LD>
@@ -309,14 +355,14 @@ __device__ __forceinline__ void su2_update_link_rt(int phase, float4 *U, const S
                                                    uint32_t e, uint32_t sweep, DevState *state)
 {
     switch (phase) { // phase = position in the sweep: (odd, mu = 0..3), then (even, mu = 0..3)
-    case 0: su2_update_link<1, 0, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 1: su2_update_link<1, 1, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 2: su2_update_link<1, 2, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 3: su2_update_link<1, 3, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 4: su2_update_link<0, 0, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 5: su2_update_link<0, 1, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
-    case 6: su2_update_link<0, 2, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
-    default: su2_update_link<0, 3, LD, false, true>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 0: su2_update_link<1, 0, LD, false, true, MC_GROUP_EARLY>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 1: su2_update_link<1, 1, LD, false, true, MC_GROUP_EARLY>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 2: su2_update_link<1, 2, LD, false, true, MC_GROUP_EARLY>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 3: su2_update_link<1, 3, LD, false, true, MC_GROUP_EARLY>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 4: su2_update_link<0, 0, LD, false, true, MC_GROUP_EARLY>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 5: su2_update_link<0, 1, LD, false, true, MC_GROUP_EARLY>(U, ch, ks, e, sweep, nullptr, state); break;
+    case 6: su2_update_link<0, 2, LD, false, true, MC_GROUP_EARLY>(U, ch, ks, e, sweep, nullptr, state); break;
+    default: su2_update_link<0, 3, LD, false, true, MC_GROUP_EARLY>(U, ch, ks, e, sweep, nullptr, state); break;
     }
 }
 

@@ -89,6 +89,30 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar_saddr, uint32_t parity, i
     return false;
 }
 
+// Arrive on an mbarrier (count 1), optionally announcing `bytes` of
+// asynchronous transfers that will complete on it.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar_saddr, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_saddr), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar_saddr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_saddr) : "memory");
+}
+
+// Tensor-map (TMA) load of one box at coordinates (c0 .. c4) into shared
+// memory, completing `bytes` on the mbarrier.  `map` is the address of a
+// __grid_constant__ CUtensorMap kernel parameter.  Coordinates outside the
+// tensor read as zero.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst_saddr, const void *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar_saddr)
+{
+    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes "
+                 "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst_saddr),
+                 "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar_saddr)
+                 : "memory");
+}
+
 // 32 consecutive FP32 columns of this thread's tensor-memory lane (the warp
 // reads lanes 32 (warp % 4) .. +31 starting at `taddr`).
 __device__ __forceinline__ void ld_32x32b_x32(uint32_t taddr, float (&v)[32])

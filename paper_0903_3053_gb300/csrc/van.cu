@@ -8,6 +8,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "tc_dev.cuh"
 #include "van_dev.cuh"
 
@@ -134,21 +137,21 @@ __global__ void __launch_bounds__(256) k_layer1_fwd(const int8_t *spins, int neg
     }
 }
 
-// 32 -> 32 masked convolution (forward) on the fifth-generation tensor cores:
-// out = ReLU(conv(in) + bias), an implicit GEMM D[q][o] = sum_{t,c} A_t[q][c] W[t][o][c]
-// with tcgen05.mma (M = 128 positions, N = 32 channels, K = 16, BF16 in,
-// FP32 accumulator in tensor memory).
+// 32 -> 32 masked convolutions on the fifth-generation tensor cores: implicit
+// GEMMs D[q][o] = sum_{t,c} A_t[q][c] W[t][o][c] with tcgen05.mma (M = 128
+// positions, N = 32 channels, K = 16, BF16 in, FP32 accumulator in tensor
+// memory).  Positions are indexed on a padded grid, q = r P + xp with
+// xp = x + 2 and a row pitch P >= L + 4, so that every tap (dy, dx) of output q
+// reads input index q + (dy + 2) P + dx of the staged rows y0-2 .. y0+R-1 -- a
+// shifted view of the same shared-memory chunk planes (see tc_dev.cuh), zero
+// halo columns giving the zero padding.  Outputs on halo columns or past the
+// last row are computed and discarded.  One CTA item = R rows of one sample,
+// cut into 128-position tiles; tiles are issued 3 at a time by one thread into
+// one of two tensor-memory buffers (26 MMAs per tile: 13 taps x 2 k-steps)
+// while 4 warps drain the other (tcgen05.ld, bias, ReLU, BF16, stores).
 //
-// Positions are indexed on a padded grid, q = r P + xp with P = L + 4 and
-// xp = x + 2, so that every tap (dy, dx) of output q reads input index
-// q + (dy + 2) P + dx of the staged rows y0-2 .. y0+R-1 -- a shifted view of
-// the same shared-memory planes (see tc_dev.cuh), zero halo columns giving the
-// zero padding.  Outputs on halo columns or past the last row are computed and
-// discarded.  One CTA item = R rows of one sample, staged with cp.async into 4
-// chunk planes (8 channels each); the item is cut into 128-position tiles,
-// issued 3 at a time by one thread into one of two tensor-memory buffers
-// (26 MMAs per tile: 13 taps x 2 k-steps) while the 4 warps drain the other
-// buffer (tcgen05.ld, bias, ReLU, BF16, 64-byte stores).  Two CTAs per SM.
+// Geometry of the gradient kernel (k_conv32_bwd_tc: P = L + 4, rows staged with
+// cp.async by the CTA's threads, `nplanes` chunk planes, two CTAs per SM).
 struct TcConvGeom {
     int L, P, R, YB, Qpad, tiles, PL;
     uint32_t plane_bytes, smem_bytes;
@@ -186,16 +189,69 @@ TcConvGeom tc_conv_geom(int L, int nplanes)
     return best;
 }
 
-__global__ void __launch_bounds__(128, 2) k_conv32_tc(const bf16 *__restrict__ in, bf16 *__restrict__ out,
-                                                      const bf16 *__restrict__ W, const float *__restrict__ bias,
-                                                      int n, TcConvGeom g, int *err)
+// ---------------------------------------------------------------- TMA-pipelined forward convolution
+// out = ReLU(conv(in) + bias).  The staging is taken off the threads and the
+// three stages of an item overlap across items: warp 4 streams the
+// input rows of the next item by TMA (one box per 8-channel chunk: R + 2 rows
+// of P positions from x = -2, everything outside the lattice arriving
+// zero-filled, so the box is the padded chunk plane) into the second of two stage
+// buffers, one thread of warp 5 issues the MMAs of the current item, and warps
+// 0-3 drain tensor memory (bias, ReLU, BF16, stores).  They hand over through
+// mbarriers: stage full (TMA bytes), stage free (MMA commit), accumulator full
+// (MMA commit) and accumulator free (epilogue arrivals); every wait is bounded
+// and a timeout latches MC_ETIMEOUT.  Every TMA destination starts on a
+// 128-byte boundary.  One CTA of 6 warps per SM.
+struct TmaConvGeom {
+    int L, P, R, YB, Qpad, tiles, PL;
+    uint32_t plane_bytes, stage_bytes, smem_bytes;
+};
+constexpr int kTmaGuard = 8;                   // positions ahead of staged row 0 (>= 4, multiple of 8)
+constexpr uint32_t kTmaMaxSmem = 200u * 1024;  // two stages + weights + barriers
+constexpr uint32_t kTmaBarBytes = 128;         // 9 mbarriers, tensor-memory slot
+
+// Rows per item: the R whose two stages fit one CTA per SM and that needs the
+// fewest 128-position tiles per sample.
+TmaConvGeom tma_conv_geom(int L)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    TmaConvGeom best{};
+    long best_tiles = -1;
+    for (int R = 1; R <= 32 && R <= L; ++R) {
+        TmaConvGeom g{};
+        g.L = L;
+        g.P = (L + 4 + 7) / 8 * 8;
+        g.R = R;
+        g.Qpad = (R * g.P + 127) / 128 * 128;
+        g.PL = (kTmaGuard + 2 * g.P + g.Qpad + 7) / 8 * 8;
+        g.plane_bytes = (uint32_t)g.PL * 16;
+        g.stage_bytes = 4 * g.plane_bytes;
+        g.smem_bytes = 2 * g.stage_bytes + kTcB + kTmaBarBytes + 128; // + alignment slack
+        g.YB = (L + R - 1) / R;
+        g.tiles = g.Qpad / 128;
+        if (g.smem_bytes > kTmaMaxSmem)
+            continue;
+        const long t = (long)g.YB * g.tiles;
+        if (best_tiles < 0 || t < best_tiles || (t == best_tiles && R > best.R)) {
+            best = g;
+            best_tiles = t;
+        }
+    }
+    return best;
+}
+
+__global__ void __launch_bounds__(192, 1) k_conv32_tma(const __grid_constant__ CUtensorMap in_map,
+                                                       bf16 *__restrict__ out, const bf16 *__restrict__ W,
+                                                       const float *__restrict__ bias, int n, TmaConvGeom g, int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // TMA destinations need 128-byte alignment: round the base up (the launch
+    // reserves 128 extra bytes)
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     const uint32_t sb = smem_u32(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t buf_bytes = 4 * g.plane_bytes;
-    const uint32_t boff = buf_bytes, bar0 = sb + boff + kTcB, tslot_off = boff + kTcB + 16;
-    for (uint32_t i = tid; i < buf_bytes / 16; i += blockDim.x) // halo columns and guards stay zero
+    const uint32_t boff = 2 * g.stage_bytes, bars = boff + kTcB;
+    const uint32_t full0 = sb + bars, empty0 = full0 + 16, tfull0 = full0 + 32, tempty0 = full0 + 48,
+                   drain = full0 + 64, tslot_off = bars + 80;
+    for (uint32_t i = tid; i < 2 * g.stage_bytes / 16; i += blockDim.x) // padding columns and guards stay zero
         reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int i = tid; i < kTapsB * kCh * 4; i += blockDim.x) {
         const int t = i / (kCh * 4), o = (i / 4) % kCh, c8 = i % 4;
@@ -205,101 +261,176 @@ __global__ void __launch_bounds__(128, 2) k_conv32_tc(const bf16 *__restrict__ i
     if (warp == 0)
         tc::tmem_alloc(sb + tslot_off, kTcCols);
     if (tid == 0) {
-        tc::mbar_init(bar0, 1);
-        tc::mbar_init(bar0 + 8, 1);
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_init(full0 + 8 * k, 1);
+            tc::mbar_init(empty0 + 8 * k, 1);
+            tc::mbar_init(tfull0 + 8 * k, 1);
+            tc::mbar_init(tempty0 + 8 * k, 4);
+        }
+        tc::mbar_init(drain, 1);
     }
+    tc::fence_smem_for_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *reinterpret_cast<volatile uint32_t *>(smem + tslot_off);
-    const uint32_t idesc = tc::idesc_bf16_f32(128, kCh);
-    float bv[kCh];
-#pragma unroll
-    for (int c = 0; c < kCh; ++c)
-        bv[c] = __ldg(&bias[c]);
-    // descriptors of tap t, k-step kc for tile 0; tile m adds 128 m positions to the start
-    // address (its 14-bit field holds addr >> 4 of a shared address below 256 KB: no carry)
-    uint64_t adesc[kTapsB * 2], bdesc[kTapsB * 2];
-    if (tid == 0)
-        for (int t = 0; t < kTapsB; ++t)
-            for (int kc = 0; kc < 2; ++kc) {
-                adesc[t * 2 + kc] = tc::smem_desc(sb + (uint32_t)(2 * kc) * g.plane_bytes +
-                                                      (uint32_t)(2 + (tap_dy(t) + 2) * g.P + tap_dx(t)) * 16u,
-                                                  g.plane_bytes, 128);
-                bdesc[t * 2 + kc] = tc::smem_desc(sb + boff + (uint32_t)(t * 4 + 2 * kc) * (kCh * 16), kCh * 16, 128);
-            }
-    const int rounds = (g.tiles + kTcGroup - 1) / kTcGroup;
-    auto issue = [&](int rd) {
-        const int m0 = rd * kTcGroup, m1 = m0 + kTcGroup < g.tiles ? m0 + kTcGroup : g.tiles;
-        for (int m = m0; m < m1; ++m) {
-            const uint32_t d = tbase + (uint32_t)((rd & 1) * kTcGroup + (m - m0)) * kCh;
-            const uint64_t off = (uint64_t)((uint32_t)m * 128u);
-#pragma unroll
-            for (int j = 0; j < kTapsB * 2; ++j)
-                tc::mma_bf16(d, adesc[j] + off, bdesc[j], idesc, j != 0);
-        }
-        tc::commit(bar0 + 8u * (uint32_t)(rd & 1));
-    };
-    uint32_t uses[2] = {0u, 0u};
+    const int total = n * g.YB, rounds = (g.tiles + kTcGroup - 1) / kTcGroup;
     int ok = 1;
-    for (int it = blockIdx.x; ok && it < n * g.YB; it += gridDim.x) {
-        const int b = it / g.YB, y0 = (it - b * g.YB) * g.R;
-        for (int i = tid; i < (g.R + 2) * g.L * 4; i += blockDim.x) {
-            const int rho = i / (g.L * 4), rem = i - rho * g.L * 4, x = rem >> 2, c8 = rem & 3, yy = y0 - 2 + rho;
-            const bool inside = yy >= 0 && yy < g.L; // rows outside the lattice: zero fill
-            const bf16 *src = in + (((size_t)b * g.L + (inside ? yy : 0)) * g.L + x) * kCh + c8 * 8;
-            const uint32_t dst = sb + (uint32_t)c8 * g.plane_bytes + (uint32_t)(4 + rho * g.P + x) * 16u;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(inside ? 16 : 0)
-                         : "memory");
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        tc::fence_smem_for_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0)
-            issue(0);
-        for (int rd = 0; rd < rounds; ++rd) {
-            if (tid == 0 && rd + 1 < rounds)
-                issue(rd + 1); // the other buffer was drained before the barrier that ended round rd - 1
-            const int s = rd & 1;
-            const bool got = tc::mbar_wait(bar0 + 8u * s, uses[s] & 1u, kTcMaxPolls);
-            ++uses[s];
-            tc::fence_after_sync();
-            const int m0 = rd * kTcGroup, m1 = m0 + kTcGroup < g.tiles ? m0 + kTcGroup : g.tiles;
-            for (int m = m0; m < m1; ++m) {
-                float v[kCh];
-                tc::ld_32x32b_x32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(s * kTcGroup + (m - m0)) * kCh, v);
-                const int q = m * 128 + 32 * warp + lane, r = q / g.P, xp = q - r * g.P;
-                if (got && r < g.R && y0 + r < g.L && xp >= 2 && xp < g.L + 2) {
-                    uint4 pk[4];
-                    uint32_t *pw = reinterpret_cast<uint32_t *>(pk);
-#pragma unroll
-                    for (int c = 0; c < kCh; c += 2) {
-                        const __nv_bfloat162 h =
-                            __floats2bfloat162_rn(fmaxf(v[c] + bv[c], 0.f), fmaxf(v[c + 1] + bv[c + 1], 0.f));
-                        pw[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
-                    }
-                    uint4 *dst = reinterpret_cast<uint4 *>(out + (((size_t)b * g.L + y0 + r) * g.L + (xp - 2)) * kCh);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        dst[k] = pk[k];
+    if (warp == 4) {
+        if (lane == 0) { // producer
+            const uint32_t bytes = (uint32_t)(g.R + 2) * 4u * (uint32_t)g.P * 16u;
+            int k = 0, armed[2] = {-1, -1};
+            for (int it = blockIdx.x; it < total; it += gridDim.x, ++k) {
+                const int s = k & 1;
+                if (k >= 2 && !tc::mbar_wait(empty0 + 8 * s, ((k >> 1) - 1) & 1, kTcMaxPolls)) {
+                    ok = 0;
+                    break;
                 }
+                const int b = it / g.YB, y0 = (it - b * g.YB) * g.R;
+                tc::mbar_arrive_expect_tx(full0 + 8 * s, bytes);
+                const uint32_t st = sb + (uint32_t)s * g.stage_bytes;
+                for (int c8 = 0; c8 < 4; ++c8) // rows y0-2 .. y0+R-1, columns -2 .. P-3 of one chunk
+                    tc::tma_load_5d(st + (uint32_t)c8 * g.plane_bytes + (uint32_t)kTmaGuard * 16u, &in_map, 0, c8,
+                                    -2, y0 - 2, b, full0 + 8 * s);
+                armed[s] = k;
             }
-            tc::fence_before_sync();
-            ok = __syncthreads_and(ok && got);
-            tc::fence_after_sync();
-            if (!ok)
-                break;
+            for (int s = 0; s < 2; ++s) // the last loads of each stage have landed before the CTA ends
+                if (armed[s] >= 0 && !tc::mbar_wait(full0 + 8 * s, (armed[s] >> 1) & 1, kTcMaxPolls))
+                    ok = 0;
+        }
+    } else if (warp == 5) {
+        if (lane == 0) { // MMA issuer
+            const uint32_t idesc = tc::idesc_bf16_f32(128, kCh);
+            uint64_t adesc[kTapsB * 2], bdesc[kTapsB * 2];
+            for (int t = 0; t < kTapsB; ++t)
+                for (int kc = 0; kc < 2; ++kc) {
+                    adesc[t * 2 + kc] =
+                        tc::smem_desc(sb + (uint32_t)(2 * kc) * g.plane_bytes +
+                                          (uint32_t)(kTmaGuard + (tap_dy(t) + 2) * g.P + tap_dx(t)) * 16u,
+                                      g.plane_bytes, 128);
+                    bdesc[t * 2 + kc] = tc::smem_desc(sb + boff + (uint32_t)(t * 4 + 2 * kc) * (kCh * 16), kCh * 16, 128);
+                }
+            uint32_t tcount = 0;
+            int k = 0;
+            for (int it = blockIdx.x; ok && it < total; it += gridDim.x, ++k) {
+                const int s = k & 1;
+                if (!tc::mbar_wait(full0 + 8 * s, (k >> 1) & 1, kTcMaxPolls)) {
+                    ok = 0;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint64_t soff = (uint64_t)(((uint32_t)s * g.stage_bytes) >> 4);
+                for (int rd = 0; rd < rounds; ++rd, ++tcount) {
+                    const uint32_t bb = tcount & 1u;
+                    if (tcount >= 2 && !tc::mbar_wait(tempty0 + 8 * bb, ((tcount >> 1) - 1) & 1u, kTcMaxPolls)) {
+                        ok = 0;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const int m0 = rd * kTcGroup, m1 = m0 + kTcGroup < g.tiles ? m0 + kTcGroup : g.tiles;
+                    for (int m = m0; m < m1; ++m) {
+                        const uint32_t d = tbase + (bb * kTcGroup + (uint32_t)(m - m0)) * kCh;
+                        const uint64_t off = soff + (uint64_t)((uint32_t)m * 128u);
+#pragma unroll
+                        for (int j = 0; j < kTapsB * 2; ++j)
+                            tc::mma_bf16(d, adesc[j] + off, bdesc[j], idesc, j != 0);
+                    }
+                    tc::commit(tfull0 + 8 * bb);
+                }
+                if (!ok)
+                    break;
+                tc::commit(empty0 + 8 * s); // stage s is free once this item's MMAs have read it
+            }
+            tc::commit(drain); // every MMA issued above has completed before the CTA ends
+            if (!tc::mbar_wait(drain, 0u, kTcMaxPolls))
+                ok = 0;
+        }
+    } else { // warps 0-3: epilogue, tensor-memory lanes 32 warp .. 32 warp + 31
+        float bv[kCh];
+#pragma unroll
+        for (int c = 0; c < kCh; ++c)
+            bv[c] = __ldg(&bias[c]);
+        uint32_t tcount = 0;
+        for (int it = blockIdx.x; ok && it < total; it += gridDim.x) {
+            const int b = it / g.YB, y0 = (it - b * g.YB) * g.R;
+            for (int rd = 0; rd < rounds; ++rd, ++tcount) {
+                const uint32_t bb = tcount & 1u;
+                const bool got =
+                    __any_sync(0xffffffffu, tc::mbar_wait(tfull0 + 8 * bb, (tcount >> 1) & 1u, kTcMaxPolls));
+                tc::fence_after_sync();
+                if (!got) {
+                    ok = 0;
+                    break;
+                }
+                const int m0 = rd * kTcGroup, m1 = m0 + kTcGroup < g.tiles ? m0 + kTcGroup : g.tiles;
+                for (int m = m0; m < m1; ++m) {
+                    float v[kCh];
+                    tc::ld_32x32b_x32(tbase + ((uint32_t)(32 * warp) << 16) + (bb * kTcGroup + (uint32_t)(m - m0)) * kCh,
+                                      v);
+                    const int q = m * 128 + 32 * warp + lane, r = q / g.P, xp = q - r * g.P;
+                    if (r < g.R && y0 + r < g.L && xp >= 2 && xp < g.L + 2) {
+                        uint4 pk[4];
+                        uint32_t *pw = reinterpret_cast<uint32_t *>(pk);
+#pragma unroll
+                        for (int c = 0; c < kCh; c += 2) {
+                            const __nv_bfloat162 h =
+                                __floats2bfloat162_rn(fmaxf(v[c] + bv[c], 0.f), fmaxf(v[c + 1] + bv[c + 1], 0.f));
+                            pw[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(out + (((size_t)b * g.L + y0 + r) * g.L + (xp - 2)) * kCh);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            dst[k] = pk[k];
+                    }
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0)
+                    tc::mbar_arrive(tempty0 + 8 * bb);
+            }
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    ok = __syncthreads_and(ok);
     if (!ok && tid == 0)
         atomicExch(err, 1);
-    tc::fence_before_sync();
-    __syncthreads();
+    tc::fence_after_sync();
     if (warp == 0)
         tc::tmem_free(tbase, kTcCols);
+}
+
+// Encoder of tensor maps, from the driver through the runtime (no link
+// dependency on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Activations [n][L][L][32] BF16 as a 5-D tensor (8 channels, 4 chunks, x, y,
+// sample); one box is one 8-channel chunk of R + 2 rows, each P positions
+// wide from x = -2: it lands in shared memory as the padded rows of one chunk
+// plane, the columns outside the lattice zero-filled.
+cudaError_t activation_map(CUtensorMap *m, const bf16 *base, int n, int L, int P, int rows)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc)
+        return cudaErrorNotSupported;
+    const cuuint64_t dims[5] = {8, 4, (cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)n};
+    const cuuint64_t strides[4] = {16, 64, (cuuint64_t)64 * L, (cuuint64_t)64 * L * L};
+    const cuuint32_t box[5] = {8, 1, (cuuint32_t)P, (cuuint32_t)rows, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // Gradients travel between the backward kernels as a BF16 hi + lo pair
@@ -320,7 +451,7 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo)
 // Gradient with respect to a 32 -> 32 layer's input, masked by the previous
 // layer's ReLU, on the fifth-generation tensor cores:
 //   out(p)[c] = [mask(p)[c] > 0] sum_t sum_o W[t][o][c] dz(p - d_t)[o].
-// Same padded-position implicit GEMM as k_conv32_tc with the taps negated
+// Same padded-position implicit GEMM as the forward kernel with the taps negated
 // (rows y0 .. y0+R+1 staged) and the weights transposed into the B planes;
 // dz arrives as hi + lo (8 A planes) and each k step issues two MMAs into
 // the same FP32 accumulator; the masked result leaves as hi + lo.
@@ -1219,12 +1350,17 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
     const size_t layer = (size_t)w->nmax * L * L * kCh;
     const unsigned rows = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 8);
     k_layer1_fwd<<<rows, 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n, L);
-    const TcConvGeom tg = tc_conv_geom(L, 4);
-    const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tg.YB, (size_t)w->sms * 2);
-    for (int l = 1; l <= D - 2; ++l)
-        k_conv32_tc<<<tcg, 128, tg.smem_bytes, w->stream>>>(w->H + (l - 1) * layer, w->H + l * layer,
-                                                           w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
-                                                           w->bias + l * kCh, n, tg, w->err);
+    const TmaConvGeom tg = tma_conv_geom(L);
+    const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tg.YB, (size_t)w->sms);
+    for (int l = 1; l <= D - 2; ++l) {
+        CUtensorMap in_map;
+        const cudaError_t e = activation_map(&in_map, w->H + (l - 1) * layer, n, L, tg.P, tg.R + 2);
+        if (e != cudaSuccess)
+            return e;
+        k_conv32_tma<<<tcg, 192, tg.smem_bytes, w->stream>>>(in_map, w->H + l * layer,
+                                                            w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
+                                                            w->bias + l * kCh, n, tg, w->err);
+    }
     k_layerD_fwd<<<rows, 256, 0, w->stream>>>(w->H + (D - 2) * layer, w->wD,
                                                                     w->bias + (D - 1) * kCh, w->spins, negate, w->f,
                                                                     w->ll, dF, 1.0f / n, n, L);
@@ -1347,8 +1483,8 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(w->ws, 0, o.hist, w->stream); // params, Adam state, buffers
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc_conv_geom(L, 4).smem_bytes);
+        e = cudaFuncSetAttribute(k_conv32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tma_conv_geom(L).smem_bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_conv32_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc_conv_geom(L, 8).smem_bytes);

@@ -711,13 +711,16 @@ __global__ void __launch_bounds__(256) k_layerD_bwd_data(const float *dF, const 
 
 // Last-layer weight and bias gradients: gW[t][c] = sum_p dF(p) h(p + d_t)[c],
 // gb = sum_p dF(p).  One CTA item = one row, staged in smem; thread i owns
-// outputs i and i + 256 of the 13 x 32 + 1; one atomic per output per CTA.
-__global__ void __launch_bounds__(256) k_layerD_bwd_w(const float *dF, const bf16 *hD, float *g, DevParams P, int n,
-                                                      int L)
+// outputs i and i + 256 of the 13 x 32 + 1 and writes the CTA's partial sums
+// to part[CTA][output] (summed in CTA order by k_edge_grad_reduce: the
+// gradient does not depend on the order the CTAs finish in).
+constexpr int kEdgeOutD = kTapsB * kCh + 1;  // last layer: 13 x 32 weights + bias
+constexpr int kEdgeOut1 = kCh * (kTapsA + 1); // first layer: 32 x (12 weights + bias)
+__global__ void __launch_bounds__(256) k_layerD_bwd_w(const float *dF, const bf16 *hD, float *part, int n, int L)
 {
     __shared__ float Gs[kMaxL];
     __shared__ __align__(16) bf16 H[3][(kMaxL + 4) * kCh];
-    constexpr int NO = kTapsB * kCh + 1;
+    constexpr int NO = kEdgeOutD;
     const int tid = threadIdx.x;
     float acc[2] = {0.f, 0.f};
     for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
@@ -745,17 +748,32 @@ __global__ void __launch_bounds__(256) k_layerD_bwd_w(const float *dF, const bf1
             acc[k] += a;
         }
     }
-    const int D = P.D;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int o = tid + k * 256;
-        if (o >= NO)
-            continue;
+        if (o < NO)
+            part[(size_t)blockIdx.x * NO + o] = acc[k];
+    }
+}
+
+// Gradient of the first (FIRST) or last layer: the CTAs' partial sums added in
+// CTA order, written to the canonical parameter order.
+template <bool FIRST>
+__global__ void k_edge_grad_reduce(const float *part, int nb, float *g, DevParams P)
+{
+    constexpr int NO = FIRST ? kEdgeOut1 : kEdgeOutD;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= NO)
+        return;
+    float v = 0.f;
+    for (int b = 0; b < nb; ++b)
+        v += part[(size_t)b * NO + o];
+    if (FIRST) {
+        const int oc = o / (kTapsA + 1), t = o - oc * (kTapsA + 1);
+        g[t < kTapsA ? canon_w(P, 0, oc, 0, tap_dy(t), tap_dx(t)) : P.b_off[0] + oc] = v;
+    } else {
         const int t = o / kCh, c = o - t * kCh;
-        if (t < kTapsB)
-            atomicAdd(&g[canon_w(P, D - 1, 0, c, tap_dy(t), tap_dx(t))], acc[k]);
-        else
-            atomicAdd(&g[P.b_off[D - 1]], acc[k]);
+        g[t < kTapsB ? canon_w(P, P.D - 1, 0, c, tap_dy(t), tap_dx(t)) : P.b_off[P.D - 1]] = v;
     }
 }
 
@@ -888,13 +906,14 @@ __global__ void k_dw_reduce(const float *__restrict__ part, int nparts, float *g
 // Layer-1 weight and bias gradients: gW1[o][t] = sum_p dZ1(p)[o] s(p + d_t),
 // gb1[o] = sum_p dZ1(p)[o].  One CTA item = one row: spins of rows y-2..y and
 // dZ1 of row y staged in smem; thread i owns outputs i and i + 256 of the
-// 32 x (12 + 1); one atomic per output per CTA.
-__global__ void __launch_bounds__(256) k_layer1_bwd_w(const bf16 *dzh, const bf16 *dzl, const int8_t *spins, float *g,
-                                                      DevParams P, int n, int L)
+// 32 x (12 + 1) and writes the CTA's partial sums to part[CTA][output]
+// (summed in CTA order by k_edge_grad_reduce).
+__global__ void __launch_bounds__(256) k_layer1_bwd_w(const bf16 *dzh, const bf16 *dzl, const int8_t *spins,
+                                                      float *part, int n, int L)
 {
     __shared__ float S[3][kMaxL + 4];
     __shared__ __align__(16) float Z[kMaxL * kCh];
-    constexpr int NO = kCh * (kTapsA + 1);
+    constexpr int NO = kEdgeOut1;
     const int tid = threadIdx.x;
     float acc[2] = {0.f, 0.f};
     for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
@@ -935,13 +954,8 @@ __global__ void __launch_bounds__(256) k_layer1_bwd_w(const bf16 *dzh, const bf1
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int idx = tid + k * 256;
-        if (idx >= NO)
-            continue;
-        const int o = idx / (kTapsA + 1), t = idx - o * (kTapsA + 1);
-        if (t < kTapsA)
-            atomicAdd(&g[canon_w(P, 0, o, 0, tap_dy(t), tap_dx(t))], acc[k]);
-        else
-            atomicAdd(&g[P.b_off[0] + o], acc[k]);
+        if (idx < NO)
+            part[(size_t)blockIdx.x * NO + idx] = acc[k];
     }
 }
 
@@ -1383,7 +1397,10 @@ cudaError_t backward(mc_van *w, int n)
     bf16 *dzh = reinterpret_cast<bf16 *>(w->dZa), *dzl = dzh + cap;
     bf16 *nxh = reinterpret_cast<bf16 *>(w->dZb), *nxl = nxh + cap;
     k_layerD_bwd_data<<<rows, 256, 0, w->stream>>>(w->dF, w->wD, hD, dzh, dzl, n, L);
-    k_layerD_bwd_w<<<rg, 256, 0, w->stream>>>(w->dF, hD, w->g, w->dp, n, L);
+    // edge-layer partial sums go to the dW partial buffer (free at these points)
+    const unsigned eg = (unsigned)std::min<size_t>(rg, (size_t)kMaxDwBlocks * kDwPart / kEdgeOutD);
+    k_layerD_bwd_w<<<eg, 256, 0, w->stream>>>(w->dF, hD, w->dwpart, n, L);
+    k_edge_grad_reduce<false><<<(kEdgeOutD + 127) / 128, 128, 0, w->stream>>>(w->dwpart, (int)eg, w->g, w->dp);
     const TcConvGeom tgb = tc_conv_geom(L, 8);
     const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tgb.YB, (size_t)w->sms * 2);
     // k_dw32 holds 124 registers x 256 threads: two CTAs per SM, one wave
@@ -1397,7 +1414,8 @@ cudaError_t backward(mc_van *w, int n)
         std::swap(dzh, nxh);
         std::swap(dzl, nxl);
     }
-    k_layer1_bwd_w<<<rg, 256, 0, w->stream>>>(dzh, dzl, w->spins, w->g, w->dp, n, L);
+    k_layer1_bwd_w<<<eg, 256, 0, w->stream>>>(dzh, dzl, w->spins, w->dwpart, n, L);
+    k_edge_grad_reduce<true><<<(kEdgeOut1 + 127) / 128, 128, 0, w->stream>>>(w->dwpart, (int)eg, w->g, w->dp);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,22 @@ def test_gradients_match_oracle():
             assert cos > cos_min and rel < rel_max, (act, l, cos, rel)
 
 
+def test_training_step_is_deterministic():
+    """Two identical training steps give bit-identical gradients: every
+    reduction (weight gradients of all layers, loss) sums in a fixed order."""
+    L, n = 16, 96
+    net = mc.VAN(L, batch=n, depth=6, seed=4)
+    net.set_params(mc.mc.van_pack(bf16_params(depth=6, seed=21)))
+    g = torch.Generator().manual_seed(5)
+    s = (torch.randint(0, 2, (n, L, L), generator=g) * 2 - 1).to(torch.int8).cuda()
+    l1 = net.train_step(s, lr=0.0, apply=False)
+    _, g1 = net.get_params(grads=True)
+    l2 = net.train_step(s, lr=0.0, apply=False)
+    _, g2 = net.get_params(grads=True)
+    assert l1 == l2
+    np.testing.assert_array_equal(g1, g2)
+
+
 def test_sampler_follows_q():
     """Samples on a 4x4 lattice follow the network's own q (chi^2 over all
     states), and the sampler's log q equals a batched forward of its samples."""

@@ -89,52 +89,91 @@ __global__ void k_prep_weights(const float *p, DevParams P, bf16 *wh, float *w1,
 }
 
 // ------------------------------------------------------------------ forward
-// Layer 1: 1 -> 32 channels, mask A, ReLU.  One thread per (position, channel).
+// Rows of one sample handled by one CTA item of the edge-layer kernels: the
+// item streams its rows through a 4-slot ring in shared memory (rows y-2, y-1,
+// y and the next row, loaded while row y is computed), so every input row is
+// read once per item instead of once per output row.
+constexpr int kSegRows = 16;
+
+// Layer 1: 1 -> 32 channels, mask A, ReLU.  4 threads per position, 8 output
+// channels each; the sampled spins of the ring rows are int8 in shared memory.
 __global__ void __launch_bounds__(256) k_layer1_fwd(const int8_t *spins, int negate, const float *w1,
                                                     const float *b1, bf16 *h1, int n, int L)
 {
-    // One CTA item = one row (sample b, row y): spins of rows y-2..y staged in
-    // shared memory, zero padded; 4 threads per position, 8 channels each.
-    __shared__ float W[kTapsA * kCh]; // [t][o]: the 4 channel groups of a warp hit different banks
+    __shared__ __align__(16) float W[kTapsA * kCh]; // [t][o], read as float4
     __shared__ float Bs[kCh];
-    __shared__ float S[3][kMaxL + 4];
+    __shared__ int8_t S[4][kMaxL + 4]; // ring slot y & 3: row y, 2 zero columns each side
     const int tid = threadIdx.x;
     for (int i = tid; i < kCh * kTapsA; i += blockDim.x)
         W[(i % kTapsA) * kCh + i / kTapsA] = w1[i]; // w1 is [o][t]
     if (tid < kCh)
         Bs[tid] = b1[tid];
-    const float sg = negate ? -1.f : 1.f;
-    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
-        const int b = item / L, y = item - b * L;
-        __syncthreads();
-        for (int i = tid; i < 3 * (L + 4); i += blockDim.x) {
-            const int r = i / (L + 4), xx = i - r * (L + 4) - 2, yy = y - 2 + r;
-            S[r][xx + 2] = (yy >= 0 && xx >= 0 && xx < L) ? sg * (float)spins[((size_t)b * L + yy) * L + xx] : 0.f;
+    const int segs = (L + kSegRows - 1) / kSegRows;
+    auto fetch = [&](int b, int yy) -> int8_t { // element tid of padded row yy: the (negated) spin, 0 outside
+        const int xx = tid - 2;
+        if (tid < L + 4 && yy >= 0 && yy < L && xx >= 0 && xx < L) {
+            const int8_t v = spins[((size_t)b * L + yy) * L + xx];
+            return negate ? (int8_t)-v : v;
         }
-        __syncthreads();
-        for (int j = tid; j < L * 4; j += blockDim.x) {
-            const int x = j >> 2, o0 = (j & 3) * 8;
-            float acc[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                acc[q] = Bs[o0 + q];
-#pragma unroll
-            for (int t = 0; t < kTapsA; ++t) {
-                const float v = S[tap_dy(t) + 2][x + tap_dx(t) + 2];
+        return (int8_t)0;
+    };
+    for (int item = blockIdx.x; item < n * segs; item += gridDim.x) {
+        const int b = item / segs, y0 = (item - b * segs) * kSegRows, y1 = min(y0 + kSegRows, L);
+        const int8_t r2 = fetch(b, y0 - 2), r1 = fetch(b, y0 - 1), r0 = fetch(b, y0);
+        __syncthreads(); // the previous item's readers are done with the ring
+        if (tid < L + 4) {
+            S[(y0 - 2) & 3][tid] = r2;
+            S[(y0 - 1) & 3][tid] = r1;
+            S[y0 & 3][tid] = r0;
+        }
+        for (int y = y0; y < y1; ++y) {
+            const int8_t nxt = fetch(b, y + 1); // row y + 1, in flight while row y is computed
+            __syncthreads();
+            for (int j = tid; j < L * 4; j += blockDim.x) {
+                const int x = j >> 2, o0 = (j & 3) * 8;
+                float acc[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    acc[q] += W[t * kCh + o0 + q] * v;
-            }
-            uint4 pk;
-            uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
+                    acc[q] = Bs[o0 + q];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(fmaxf(acc[2 * q], 0.f), fmaxf(acc[2 * q + 1], 0.f));
-                pw[q] = *reinterpret_cast<const uint32_t *>(&h2);
+                for (int t = 0; t < kTapsA; ++t) {
+                    const float v = (float)S[(y + tap_dy(t)) & 3][x + tap_dx(t) + 2];
+                    const float4 wa = *reinterpret_cast<const float4 *>(&W[t * kCh + o0]);
+                    const float4 wb = *reinterpret_cast<const float4 *>(&W[t * kCh + o0 + 4]);
+                    const float wq[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        acc[q] += wq[q] * v;
+                }
+                uint4 pk;
+                uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const __nv_bfloat162 h2 =
+                        __floats2bfloat162_rn(fmaxf(acc[2 * q], 0.f), fmaxf(acc[2 * q + 1], 0.f));
+                    pw[q] = *reinterpret_cast<const uint32_t *>(&h2);
+                }
+                *reinterpret_cast<uint4 *>(h1 + (((size_t)b * L + y) * L + x) * kCh + o0) = pk;
             }
-            *reinterpret_cast<uint4 *>(h1 + (((size_t)b * L + y) * L + x) * kCh + o0) = pk;
+            if (tid < L + 4) // slot (y + 1) & 3 held row y - 3, which row y does not read
+                S[(y + 1) & 3][tid] = nxt;
         }
     }
+}
+
+// One padded input row of a 32-channel activation (L + 4 positions, zero
+// outside the lattice) into a ring slot, by cp.async.
+__device__ __forceinline__ void stage_row_async(bf16 *slot, const bf16 *src, int b, int yy, int L)
+{
+    for (int i = threadIdx.x; i < (L + 4) * 4; i += blockDim.x) {
+        const int xx = i / 4 - 2, ch = i & 3;
+        const bool inside = yy >= 0 && yy < L && xx >= 0 && xx < L;
+        const bf16 *g = inside ? src + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8 : src;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(slot + (xx + 2) * kCh + ch * 8)),
+                     "l"(g), "r"(inside ? 16 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // 32 -> 32 masked convolutions on the fifth-generation tensor cores: implicit
@@ -593,46 +632,62 @@ __device__ __forceinline__ void stage_rows3(bf16 (*H)[(kMaxL + 4) * kCh], const 
 }
 
 // Last layer (32 -> 1, mask B): logit f, and per position log p(s_k | s_<k) =
-// log sigmoid(s f) and (training) dF = -(1/n) s sigmoid(-s f).  One CTA item =
-// one row; 4 threads per position (8 channels each), partials summed in smem.
+// log sigmoid(s f) and (training) dF = -(1/n) s sigmoid(-s f).  A CTA item is
+// a segment of rows streamed through the ring (cp.async, one row ahead); 4
+// threads per position (8 channels each), partials summed in smem.
 __global__ void __launch_bounds__(256) k_layerD_fwd(const bf16 *hD, const float *wD, const float *bD,
                                                     const int8_t *spins, int negate, float *f, float *ll, float *dF,
                                                     float inv_n, int n, int L)
 {
-    __shared__ float W[kTapsB * kCh];
-    __shared__ __align__(16) bf16 H[3][(kMaxL + 4) * kCh];
+    __shared__ __align__(16) float W[kTapsB * kCh]; // [t][c], read as float4
+    __shared__ __align__(16) bf16 H[4][(kMaxL + 4) * kCh];
     __shared__ float part[kMaxL * 4];
     const int tid = threadIdx.x;
     for (int i = tid; i < kTapsB * kCh; i += blockDim.x)
         W[i] = wD[i];
     const float b0 = bD[0];
-    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
-        const int b = item / L, y = item - b * L;
-        __syncthreads();
-        stage_rows3(H, hD, b, y, L);
-        __syncthreads();
-        for (int j = tid; j < L * 4; j += blockDim.x) {
-            const int x = j >> 2, c0 = (j & 3) * 8;
-            float acc = 0.f;
-#pragma unroll
-            for (int t = 0; t < kTapsB; ++t) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(&H[tap_dy(t) + 2][(x + tap_dx(t) + 2) * kCh + c0]);
-                const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&v);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    acc += W[t * kCh + c0 + 2 * q] * bf(h2[q].x) + W[t * kCh + c0 + 2 * q + 1] * bf(h2[q].y);
+    const int segs = (L + kSegRows - 1) / kSegRows;
+    for (int item = blockIdx.x; item < n * segs; item += gridDim.x) {
+        const int b = item / segs, y0 = (item - b * segs) * kSegRows, y1 = min(y0 + kSegRows, L);
+        __syncthreads(); // the previous item's readers are done with the ring
+        stage_row_async(H[(y0 - 2) & 3], hD, b, y0 - 2, L);
+        stage_row_async(H[(y0 - 1) & 3], hD, b, y0 - 1, L);
+        stage_row_async(H[y0 & 3], hD, b, y0, L);
+        for (int y = y0; y < y1; ++y) {
+            if (y + 1 < y1) { // slot (y + 1) & 3 held row y - 3: its last reader finished before the barrier below
+                stage_row_async(H[(y + 1) & 3], hD, b, y + 1, L);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
-            part[j] = acc;
-        }
-        __syncthreads();
-        for (int x = tid; x < L; x += blockDim.x) {
-            const float acc = b0 + ((part[4 * x] + part[4 * x + 1]) + (part[4 * x + 2] + part[4 * x + 3]));
-            const size_t p = ((size_t)b * L + y) * L + x;
-            const float sv = negate ? -(float)spins[p] : (float)spins[p];
-            f[p] = acc;
-            ll[p] = log_sigmoid(sv * acc);
-            if (dF)
-                dF[p] = -inv_n * sv * sigmoid(-sv * acc);
+            __syncthreads();
+            for (int j = tid; j < L * 4; j += blockDim.x) {
+                const int x = j >> 2, c0 = (j & 3) * 8;
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < kTapsB; ++t) {
+                    const uint4 v =
+                        *reinterpret_cast<const uint4 *>(&H[(y + tap_dy(t)) & 3][(x + tap_dx(t) + 2) * kCh + c0]);
+                    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&v);
+                    const float4 wa = *reinterpret_cast<const float4 *>(&W[t * kCh + c0]);
+                    const float4 wb = *reinterpret_cast<const float4 *>(&W[t * kCh + c0 + 4]);
+                    const float wq[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        acc += wq[2 * q] * bf(h2[q].x) + wq[2 * q + 1] * bf(h2[q].y);
+                }
+                part[j] = acc;
+            }
+            __syncthreads();
+            for (int x = tid; x < L; x += blockDim.x) {
+                const float acc = b0 + ((part[4 * x] + part[4 * x + 1]) + (part[4 * x + 2] + part[4 * x + 3]));
+                const size_t p = ((size_t)b * L + y) * L + x;
+                const float sv = negate ? -(float)spins[p] : (float)spins[p];
+                f[p] = acc;
+                ll[p] = log_sigmoid(sv * acc);
+                if (dF)
+                    dF[p] = -inv_n * sv * sigmoid(-sv * acc);
+            }
         }
     }
 }
@@ -1362,8 +1417,8 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
     }
     const int L = w->L, D = w->D;
     const size_t layer = (size_t)w->nmax * L * L * kCh;
-    const unsigned rows = (unsigned)std::min<size_t>((size_t)n * L, (size_t)w->sms * 8);
-    k_layer1_fwd<<<rows, 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n, L);
+    const unsigned segs = (unsigned)std::min<size_t>((size_t)n * ((L + kSegRows - 1) / kSegRows), (size_t)w->sms * 8);
+    k_layer1_fwd<<<segs, 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n, L);
     const TmaConvGeom tg = tma_conv_geom(L);
     const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tg.YB, (size_t)w->sms);
     for (int l = 1; l <= D - 2; ++l) {
@@ -1375,7 +1430,7 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
                                                             w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
                                                             w->bias + l * kCh, n, tg, w->err);
     }
-    k_layerD_fwd<<<rows, 256, 0, w->stream>>>(w->H + (D - 2) * layer, w->wD,
+    k_layerD_fwd<<<segs, 256, 0, w->stream>>>(w->H + (D - 2) * layer, w->wD,
                                                                     w->bias + (D - 1) * kCh, w->spins, negate, w->f,
                                                                     w->ll, dF, 1.0f / n, n, L);
     k_logq<<<n, 256, 0, w->stream>>>(w->ll, logq, L);

@@ -807,22 +807,31 @@ __global__ void __launch_bounds__(256) k_layerD_bwd_w(const float *dF, const bf1
     for (int k = 0; k < 2; ++k) {
         const int o = tid + k * 256;
         if (o < NO)
-            part[(size_t)blockIdx.x * NO + o] = acc[k];
+            part[(size_t)o * gridDim.x + blockIdx.x] = acc[k];
     }
 }
 
-// Gradient of the first (FIRST) or last layer: the CTAs' partial sums added in
-// CTA order, written to the canonical parameter order.
+// Gradient of the first (FIRST) or last layer: one CTA per output adds its
+// nb per-CTA partial sums (part[output][CTA]) in a fixed order -- strided
+// per-thread sums, then a fixed shuffle and shared-memory tree -- and writes
+// the canonical parameter.
 template <bool FIRST>
-__global__ void k_edge_grad_reduce(const float *part, int nb, float *g, DevParams P)
+__global__ void __launch_bounds__(256) k_edge_grad_reduce(const float *part, int nb, float *g, DevParams P)
 {
-    constexpr int NO = FIRST ? kEdgeOut1 : kEdgeOutD;
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= NO)
-        return;
+    __shared__ float ws[8];
+    const int o = blockIdx.x, tid = threadIdx.x;
     float v = 0.f;
-    for (int b = 0; b < nb; ++b)
-        v += part[(size_t)b * NO + o];
+    for (int b = tid; b < nb; b += blockDim.x)
+        v += part[(size_t)o * nb + b];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((tid & 31) == 0)
+        ws[tid >> 5] = v;
+    __syncthreads();
+    if (tid != 0)
+        return;
+    v = ((ws[0] + ws[1]) + (ws[2] + ws[3])) + ((ws[4] + ws[5]) + (ws[6] + ws[7]));
     if (FIRST) {
         const int oc = o / (kTapsA + 1), t = o - oc * (kTapsA + 1);
         g[t < kTapsA ? canon_w(P, 0, oc, 0, tap_dy(t), tap_dx(t)) : P.b_off[0] + oc] = v;
@@ -1010,7 +1019,7 @@ __global__ void __launch_bounds__(256) k_layer1_bwd_w(const bf16 *dzh, const bf1
     for (int k = 0; k < 2; ++k) {
         const int idx = tid + k * 256;
         if (idx < NO)
-            part[(size_t)blockIdx.x * NO + idx] = acc[k];
+            part[(size_t)idx * gridDim.x + blockIdx.x] = acc[k];
     }
 }
 
@@ -1455,7 +1464,7 @@ cudaError_t backward(mc_van *w, int n)
     // edge-layer partial sums go to the dW partial buffer (free at these points)
     const unsigned eg = (unsigned)std::min<size_t>(rg, (size_t)kMaxDwBlocks * kDwPart / kEdgeOutD);
     k_layerD_bwd_w<<<eg, 256, 0, w->stream>>>(w->dF, hD, w->dwpart, n, L);
-    k_edge_grad_reduce<false><<<(kEdgeOutD + 127) / 128, 128, 0, w->stream>>>(w->dwpart, (int)eg, w->g, w->dp);
+    k_edge_grad_reduce<false><<<kEdgeOutD, 256, 0, w->stream>>>(w->dwpart, (int)eg, w->g, w->dp);
     const TcConvGeom tgb = tc_conv_geom(L, 8);
     const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tgb.YB, (size_t)w->sms * 2);
     // k_dw32 holds 124 registers x 256 threads: two CTAs per SM, one wave
@@ -1470,7 +1479,7 @@ cudaError_t backward(mc_van *w, int n)
         std::swap(dzl, nxl);
     }
     k_layer1_bwd_w<<<eg, 256, 0, w->stream>>>(dzh, dzl, w->spins, w->dwpart, n, L);
-    k_edge_grad_reduce<true><<<(kEdgeOut1 + 127) / 128, 128, 0, w->stream>>>(w->dwpart, (int)eg, w->g, w->dp);
+    k_edge_grad_reduce<true><<<kEdgeOut1, 256, 0, w->stream>>>(w->dwpart, (int)eg, w->g, w->dp);
     return cudaGetLastError();
 }
 

@@ -969,17 +969,24 @@ __global__ void k_dw_reduce(const float *__restrict__ part, int nparts, float *g
 
 // Layer-1 weight and bias gradients: gW1[o][t] = sum_p dZ1(p)[o] s(p + d_t),
 // gb1[o] = sum_p dZ1(p)[o].  One CTA item = one row: spins of rows y-2..y and
-// dZ1 of row y staged in smem; thread i owns outputs i and i + 256 of the
-// 32 x (12 + 1) and writes the CTA's partial sums to part[CTA][output]
-// (summed in CTA order by k_edge_grad_reduce).
+// dZ1 of row y staged in smem.  Lane o of warp w accumulates the 13 outputs
+// of channel o over its segment w of every row, the 12 tap spins held in a
+// window of registers that slides along x (3 shared-memory loads per
+// position instead of one per tap and channel); at the end the 8 segment
+// warps are added in warp order and the CTA writes its partial sums to
+// part[output][CTA] (summed in a fixed order by k_edge_grad_reduce).
 __global__ void __launch_bounds__(256) k_layer1_bwd_w(const bf16 *dzh, const bf16 *dzl, const int8_t *spins,
                                                       float *part, int n, int L)
 {
     __shared__ float S[3][kMaxL + 4];
     __shared__ __align__(16) float Z[kMaxL * kCh];
-    constexpr int NO = kEdgeOut1;
-    const int tid = threadIdx.x;
-    float acc[2] = {0.f, 0.f};
+    __shared__ float R[8][kEdgeOut1];
+    const int tid = threadIdx.x, o = tid & 31, seg = tid >> 5;
+    const int seg_len = (L + 7) / 8, x0 = seg * seg_len, x1 = min(x0 + seg_len, L);
+    float acc[kTapsA + 1];
+#pragma unroll
+    for (int t = 0; t <= kTapsA; ++t)
+        acc[t] = 0.f;
     for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
         const int b = item / L, y = item - b * L;
         __syncthreads();
@@ -997,29 +1004,48 @@ __global__ void __launch_bounds__(256) k_layer1_bwd_w(const bf16 *dzh, const bf1
                 Z[8 * i + k] = bf(h8[k]) + bf(l8[k]);
         }
         __syncthreads();
+        if (x0 < x1) {
+            // taps 0-4: S[0][x + t]; 5-9: S[1][x + t - 5]; 10, 11: S[2][x + t - 10] (mask A)
+            float w0[5], w1[5], w2[2];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int idx = tid + k * 256;
-            if (idx >= NO)
-                continue;
-            const int o = idx / (kTapsA + 1), t = idx - o * (kTapsA + 1);
-            float a = 0.f;
-            if (t < kTapsA) {
-                const float *sr = &S[tap_dy(t) + 2][tap_dx(t) + 2];
-                for (int x = 0; x < L; ++x)
-                    a += Z[x * kCh + o] * sr[x];
-            } else {
-                for (int x = 0; x < L; ++x)
-                    a += Z[x * kCh + o];
+            for (int k = 0; k < 4; ++k) {
+                w0[k + 1] = S[0][x0 + k];
+                w1[k + 1] = S[1][x0 + k];
             }
-            acc[k] += a;
+            w2[1] = S[2][x0];
+            for (int x = x0; x < x1; ++x) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    w0[k] = w0[k + 1];
+                    w1[k] = w1[k + 1];
+                }
+                w0[4] = S[0][x + 4];
+                w1[4] = S[1][x + 4];
+                w2[0] = w2[1];
+                w2[1] = S[2][x + 1];
+                const float z = Z[x * kCh + o];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    acc[k] += z * w0[k];
+                    acc[5 + k] += z * w1[k];
+                }
+                acc[10] += z * w2[0];
+                acc[11] += z * w2[1];
+                acc[12] += z;
+            }
         }
     }
+    __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int idx = tid + k * 256;
-        if (idx < NO)
-            part[(size_t)idx * gridDim.x + blockIdx.x] = acc[k];
+    for (int t = 0; t <= kTapsA; ++t)
+        R[seg][o * (kTapsA + 1) + t] = acc[t];
+    __syncthreads();
+    for (int idx = tid; idx < kEdgeOut1; idx += blockDim.x) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+            v += R[w][idx];
+        part[(size_t)idx * gridDim.x + blockIdx.x] = v;
     }
 }
 

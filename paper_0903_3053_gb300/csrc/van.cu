@@ -765,9 +765,12 @@ __global__ void __launch_bounds__(256) k_layerD_bwd_data(const float *dF, const 
 }
 
 // Last-layer weight and bias gradients: gW[t][c] = sum_p dF(p) h(p + d_t)[c],
-// gb = sum_p dF(p).  One CTA item = one row, staged in smem; thread i owns
-// outputs i and i + 256 of the 13 x 32 + 1 and writes the CTA's partial sums
-// to part[CTA][output] (summed in CTA order by k_edge_grad_reduce: the
+// gb = sum_p dF(p).  One CTA item = one row, staged in smem.  Lane c of warp w
+// accumulates the 13 tap outputs of channel c (and the bias) over its segment
+// w of every row, the tap activations held in a window of registers that
+// slides along x (3 shared-memory loads per position); at the end the 8
+// segment warps are added in warp order and the CTA writes its partial sums to
+// part[output][CTA] (summed in a fixed order by k_edge_grad_reduce: the
 // gradient does not depend on the order the CTAs finish in).
 constexpr int kEdgeOutD = kTapsB * kCh + 1;  // last layer: 13 x 32 weights + bias
 constexpr int kEdgeOut1 = kCh * (kTapsA + 1); // first layer: 32 x (12 weights + bias)
@@ -775,9 +778,13 @@ __global__ void __launch_bounds__(256) k_layerD_bwd_w(const float *dF, const bf1
 {
     __shared__ float Gs[kMaxL];
     __shared__ __align__(16) bf16 H[3][(kMaxL + 4) * kCh];
-    constexpr int NO = kEdgeOutD;
-    const int tid = threadIdx.x;
-    float acc[2] = {0.f, 0.f};
+    __shared__ float R[8][kEdgeOutD];
+    const int tid = threadIdx.x, c = tid & 31, seg = tid >> 5;
+    const int seg_len = (L + 7) / 8, x0 = seg * seg_len, x1 = min(x0 + seg_len, L);
+    float acc[kTapsB + 1];
+#pragma unroll
+    for (int t = 0; t <= kTapsB; ++t)
+        acc[t] = 0.f;
     for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
         const int b = item / L, y = item - b * L;
         __syncthreads();
@@ -785,29 +792,53 @@ __global__ void __launch_bounds__(256) k_layerD_bwd_w(const float *dF, const bf1
         for (int x = tid; x < L; x += blockDim.x)
             Gs[x] = dF[((size_t)b * L + y) * L + x];
         __syncthreads();
+        if (x0 < x1) {
+            // taps 0-4: row y-2 at x - 2 .. x + 2; 5-9: row y-1; 10-12: row y at x - 2 .. x (mask B)
+            float w0[5], w1[5], w2[3];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int o = tid + k * 256;
-            if (o >= NO)
-                continue;
-            const int t = o / kCh, c = o - t * kCh;
-            float a = 0.f;
-            if (t < kTapsB) {
-                const bf16 *hr = &H[tap_dy(t) + 2][(tap_dx(t) + 2) * kCh + c];
-                for (int x = 0; x < L; ++x)
-                    a += Gs[x] * bf(hr[x * kCh]);
-            } else {
-                for (int x = 0; x < L; ++x)
-                    a += Gs[x];
+            for (int k = 0; k < 4; ++k) {
+                w0[k + 1] = bf(H[0][(x0 + k) * kCh + c]);
+                w1[k + 1] = bf(H[1][(x0 + k) * kCh + c]);
             }
-            acc[k] += a;
+            w2[1] = bf(H[2][x0 * kCh + c]);
+            w2[2] = bf(H[2][(x0 + 1) * kCh + c]);
+            for (int x = x0; x < x1; ++x) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    w0[k] = w0[k + 1];
+                    w1[k] = w1[k + 1];
+                }
+                w0[4] = bf(H[0][(x + 4) * kCh + c]);
+                w1[4] = bf(H[1][(x + 4) * kCh + c]);
+                w2[0] = w2[1];
+                w2[1] = w2[2];
+                w2[2] = bf(H[2][(x + 2) * kCh + c]);
+                const float gf = Gs[x];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    acc[k] += gf * w0[k];
+                    acc[5 + k] += gf * w1[k];
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    acc[10 + k] += gf * w2[k];
+                acc[13] += gf;
+            }
         }
     }
+    __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int o = tid + k * 256;
-        if (o < NO)
-            part[(size_t)o * gridDim.x + blockIdx.x] = acc[k];
+    for (int t = 0; t < kTapsB; ++t)
+        R[seg][t * kCh + c] = acc[t];
+    if (c == 0)
+        R[seg][kTapsB * kCh] = acc[kTapsB];
+    __syncthreads();
+    for (int o = tid; o < kEdgeOutD; o += blockDim.x) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+            v += R[w][o];
+        part[(size_t)o * gridDim.x + blockIdx.x] = v;
     }
 }
 

@@ -391,6 +391,20 @@ def run_su2(mc, torch, rank, K, world):
     ms_or = t0.elapsed_time(t1) / Kor
     batch.read_series()
     batch.close()
+    # the small lattice of the workload: 8^4 at the same four beta, plaquette every sweep, in 1000-sweep
+    # calls (one CUDA graph); 2048 links per phase and chain, so launch- and latency-bound
+    small = mc.Batch([mc.su2(8, b, seed=1, chain_id=cid(rank, i), hot=True) for i, b in enumerate(SU2_BETAS)],
+                     series_capacity=1024)
+    small.sweep(1000, 1)
+    small.read_series()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    small.sweep(1000, 1)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_small = t0.elapsed_time(t1) / 1000
+    small.read_series()
+    small.close()
     updates = len(chains) * 4 * SU2_L ** 4 * K * world
     phase_ms = kernel_ms / max(launches, 1)
     per_launch_updates = len(chains) * 4 * SU2_L ** 4 * Kp / max(launches, 1)
@@ -405,6 +419,9 @@ def run_su2(mc, torch, rank, K, world):
             "workload": f"4D SU(2) {SU2_L}^4, beta in {SU2_BETAS}, hot start, heat-bath (KP+Creutz), plaquette "
                         "every sweep", "steps": K, "ms_per_sweep": ms / K, "phase_kernel_ms": phase_ms,
             "last_plaquette": P,
+            "lattice_8x4": {"ms_per_sweep": ms_small,
+                            "link_updates_per_s": len(SU2_BETAS) * 4 * 8 ** 4 * world / (ms_small / 1e3),
+                            "bound": "launch and latency: 2048 links per phase and chain"},
             "with_overrelaxation": {"n_or": 1, "ms_per_compound_sweep": ms_or,
                                     "overrelax_link_updates_per_s": len(chains) * 4 * SU2_L ** 4 / ((ms_or - ms / K) / 1e3)
                                     if ms_or > ms / K else None},

@@ -208,6 +208,7 @@ def run_gb300(args):
     e2e = run_e2e(mc, torch, rank, min(K, args.e2e_steps), world)
 
     # ---- SU(2) and batched-chain components -------------------------------------------
+    small = run_ising_64(mc, torch, rank, world)
     su2 = run_su2(mc, torch, rank, args.su2_steps, world)
     batched = run_batched(mc, torch, rank, args.batch_steps, world)
     ess_cmp = run_ess(args) if not args.no_ess else None
@@ -252,7 +253,8 @@ def run_gb300(args):
         "e2e": e2e,
         "gpu_launches": launches + K,  # 2 half-sweeps + 1 state-advance kernel per step
         "clocks": clock_info,
-        "components": {"su2": su2, "batched": batched, "ess_beta_c": ess_cmp, "paper_protocol": paper},
+        "components": {"ising_64x64_int8": small, "su2": su2, "batched": batched, "ess_beta_c": ess_cmp,
+                       "paper_protocol": paper},
         "device": dev_props.name,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -342,6 +344,30 @@ def run_e2e(mc, torch, rank, K, world):
             "pipeline": "two contexts on two streams alternate steps; copy-engine upload of step k+1 overlaps "
                         "the sweep of step k",
             "sequential_value": flips_per_step() * K * world / dt_seq}
+
+
+def run_ising_64(mc, torch, rank, world, sweeps=1000) -> dict:
+    """The parity workload: one 64 x 64 int8 chain at beta_c, hot start, E/M
+    every sweep, 1000 sweeps per call (the resident kernel: the lattice in
+    shared memory, all sweeps in one launch).  4096 sites: latency-bound, no
+    roofline claimed."""
+    b = mc.Batch([mc.ising(64, 0.4406868, seed=1, chain_id=cid(rank, 0))], series_capacity=sweeps)
+    b.set_mode(mc.MC_MODE_AUTO)
+    b.sweep(sweeps, 1)
+    b.read_series()
+    stream = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    b.sweep(sweeps, 1)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    b.read_series()
+    b.close()
+    return {"metric": "Ising spin-flips/s", "workload": "64x64 int8, beta_c, hot start, E/M every sweep",
+            "sweeps": sweeps, "us_per_sweep": 1e3 * ms / sweeps, "value": 64 * 64 * sweeps * world / (ms / 1e3),
+            "unit": "spin-flips/s", "bound": "latency (one CTA, 4096 sites)"}
 
 
 def run_su2(mc, torch, rank, K, world):

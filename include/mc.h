@@ -128,7 +128,8 @@ MC_API mc_status mc_sweep(mc_ctx *ctx, int64_t n_sweeps, int32_t measure_every);
 /* Execution mode for later sweeps: MC_MODE_GRID (one launch per half-sweep /
  * phase over all chains), MC_MODE_RESIDENT (Ising only: one CTA per chain with
  * its lattice in shared memory, all sweeps of a call in one launch) or
- * MC_MODE_AUTO.  threads_per_block = 0 keeps the default.  Results are
+ * MC_MODE_AUTO.  threads_per_block = 0 keeps the default (256 for Ising, 128 for
+ * SU(2), at most 256 for SU(2)).  Results are
  * bit-identical in every mode. */
 MC_API mc_status mc_set_mode(mc_ctx *ctx, int32_t mode, int32_t threads_per_block);
 

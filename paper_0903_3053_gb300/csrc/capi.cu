@@ -370,6 +370,8 @@ mc_status mc_batch_init(mc_ctx **out, int32_t n_chains, const mc_chain_desc *cha
     if (!c)
         return fail(MC_ENOMEM, "host allocation of the context failed");
     c->kind = chains[0].kind;
+    if (c->kind == MC_KIND_SU2) // 128-thread blocks: same occupancy, smaller tail (0.672 vs 0.679 ms per sweep
+        c->threads = kSu2DefaultThreads; // of 4 x 32^4)
     c->layout = c->kind == MC_KIND_ISING ? layout : 0;
     c->n_chains = n_chains;
     c->cap = series_capacity;

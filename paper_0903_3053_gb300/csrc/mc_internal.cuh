@@ -18,6 +18,7 @@ namespace mc {
 
 constexpr int kMaxChains = 4096;
 constexpr int kDefaultThreads = 256;
+constexpr int kSu2DefaultThreads = 128; // SU(2) phase kernels (launch bound 256 threads)
 constexpr int kMaxOverrelax = 64;   // overrelaxation sweeps per heat-bath sweep
 constexpr size_t kAlign = 256;
 

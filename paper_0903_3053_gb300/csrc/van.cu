@@ -1217,9 +1217,7 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
                 const float bo = Bs[l * kCh + o], b1v = Bs[l * kCh + o + 1];
                 const __nv_bfloat162 v = __floats2bfloat162_rn(fmaxf(acc[2 * h] + bo, 0.f), fmaxf(acc[2 * h + 1] + b1v, 0.f));
                 *reinterpret_cast<__nv_bfloat162 *>(Hc + s * kRowStride + o) = v;
-                if (gs < n && l < nh) // the last hidden output feeds only the output layer
-                    *reinterpret_cast<__nv_bfloat162 *>(hcur + (size_t)gs * ring + ((size_t)slot * L + x) * kCh + o) = v;
-                if (gs < n && l == nh)
+                if (gs < n) // the ring of layer l feeds the taps of layer l + 1 (the output layer for l = nh)
                     *reinterpret_cast<__nv_bfloat162 *>(hcur + (size_t)gs * ring + ((size_t)slot * L + x) * kCh + o) = v;
             }
             __syncthreads();

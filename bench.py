@@ -59,7 +59,7 @@ ISSUE_PEAK = SM_COUNT * 128 * SM_MAX_MHZ * 1e6
 # ncu capture of the current kernel (profiles/k_half_sweep_msc32_ising_batch.md):
 # 179 MB read (both colour planes once) + 51.7 MB written (changed words only).
 # Set to None whenever the kernel changes until it is captured again.
-MSC_TRAFFIC_PER_LAUNCH = 230.2e6
+MSC_TRAFFIC_PER_LAUNCH = None
 
 
 def log(*a):

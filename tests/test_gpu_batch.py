@@ -63,7 +63,8 @@ def test_group_matches_context_sweeps(reference, C, threads, split):
 
 def test_group_chains_against_oracle():
     chains = [mc.ising(32, 0.4406868, seed=5, chain_id=9), mc.ising((64, 32), 0.3, seed=6, chain_id=1)]
-    msc = [mc.ising(128, 0.5, seed=7, chain_id=4)]
+    msc = [mc.ising(128, 0.5, seed=7, chain_id=4), mc.ising((128, 64), 3.0, seed=8, chain_id=2),
+           mc.ising(64, 6.0, seed=9, chain_id=3)]  # T4 = 0; T2 = T4 = 0
     b1 = mc.Batch(chains, layout=mc.MC_LAYOUT_INT8, series_capacity=8)
     b2 = mc.Batch(msc, layout=mc.MC_LAYOUT_MSC32, series_capacity=8)
     g = mc.Group([b1, b2])

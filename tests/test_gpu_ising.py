@@ -212,6 +212,25 @@ def test_full_size_sampled_sites(L, layout):
     b.close()
 
 
+@pytest.mark.parametrize("beta", [3.0, 6.0])
+@pytest.mark.parametrize("mode", [mc.MC_MODE_GRID, mc.MC_MODE_RESIDENT])
+def test_msc_thresholds_rounding_to_zero(beta, mode):
+    """Large beta: the dE = 8 threshold floor(e^{-8 beta} 2^32) is 0 at beta = 3
+    and both are 0 at beta = 6, so no site with dE > 0 may flip (the multi-spin
+    kernel treats a zero threshold apart from its carry-chain compare); the
+    configurations and E/M series still equal the oracle's."""
+    t2, t4 = (int(v) for v in oracle.ising_thresholds(beta))
+    assert t4 == 0 and (t2 == 0) == (beta == 6.0)
+    chains = [mc.ising((128, 64), beta, seed=11, chain_id=4), mc.ising((64, 128), beta, seed=12, chain_id=5)]
+    cfgs, series = run_gpu(chains, mc.MC_LAYOUT_MSC32, 6, 1, mode)
+    for k, c in enumerate(chains):
+        s = oracle.ising_init(c.L, c.seed, c.chain_id, True)
+        E, M = oracle.ising_run(s, beta, c.seed, c.chain_id, 0, 6)
+        np.testing.assert_array_equal(cfgs[k], s)
+        np.testing.assert_array_equal(series["E"][k], E)
+        np.testing.assert_array_equal(series["M"][k], M)
+
+
 def test_beta_zero_flips_everything_on_gpu():
     b = mc.Batch([mc.ising((256, 64), 0.0, seed=5)], layout=mc.MC_LAYOUT_MSC32)
     s0 = b.get_config(0)

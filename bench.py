@@ -57,9 +57,9 @@ SU2_INSTR_PER_UPDATE = 400.0
 ISSUE_PEAK = SM_COUNT * 128 * SM_MAX_MHZ * 1e6
 # DRAM bytes (read + write) per MSC half-sweep launch of this workload, from one
 # ncu capture of the current kernel (profiles/k_half_sweep_msc32_ising_batch.md):
-# 179 MB read (both colour planes once) + 51.7 MB written (changed words only).
+# 179 MB read (both colour planes once) + 50.9 MB written (changed words only).
 # Set to None whenever the kernel changes until it is captured again.
-MSC_TRAFFIC_PER_LAUNCH = None
+MSC_TRAFFIC_PER_LAUNCH = 229.9e6
 
 
 def log(*a):

@@ -1104,54 +1104,99 @@ namespace {
 constexpr uint32_t kTagVanSample = 0x21000000u; // sampler uniforms
 constexpr uint32_t kTagVanMH = 0x22000000u;     // accept uniform and global flip
 constexpr int kSampleTile = 32;                 // samples per sampler CTA (two m16 tiles)
-constexpr int kAStride = kTapsB * kCh + 8;      // 424 bf16 per sample row of the gathered A tile
+constexpr int kAStride = kTapsA * kCh + 8;      // 392 bf16 per sample row of a gathered A tile (12 earlier taps)
+constexpr int kSampleMaxBufs = 3;               // gathered A tiles in flight
+constexpr size_t kSampleSmemLimit = 232448;     // 227 KB, the opt-in maximum per block
 
-// A tile [32 samples][13 taps][32 channels] of one layer's input at position
-// (y, x): the 12 earlier-position taps from the ring `h` (hist of that layer,
-// `ring` elements per sample) by cp.async, zero-filled outside the lattice or
-// beyond the n samples, and the current position's value from Hc.  The caller
-// synchronises the block before the tile is read.
-__device__ __forceinline__ void gather_taps(bf16 *As, const bf16 *Hc, const bf16 *h, size_t ring, int s0, int n,
-                                            int L, int y, int x)
+// The copies of one gather: the 12 earlier-position taps x 4 chunks of 16
+// bytes of the 32 samples of a CTA, 1536 copies, 6 per thread of the
+// 256-thread sampler.  What a copy reads relative to the position and where it
+// lands do not change from step to step, so each thread keeps its 6 copies'
+// tap offsets, ring offsets and tile offsets in registers.
+constexpr int kSampleThreads = 256;
+constexpr int kGatherPerThread = kSampleTile * kTapsA * 4 / kSampleThreads;
+static_assert(kGatherPerThread * kSampleThreads == kSampleTile * kTapsA * 4, "gather copies per thread");
+
+struct GatherSlots {
+    uint32_t dst[kGatherPerThread]; // byte offset in the A tile
+    int dy[kGatherPerThread], dx[kGatherPerThread];
+    size_t src[kGatherPerThread];   // element offset in a layer's ring array (sample and chunk)
+};
+
+__device__ __forceinline__ GatherSlots gather_slots(int s0, int n, size_t ring)
 {
-    for (int i = threadIdx.x; i < kSampleTile * kTapsB * 4; i += blockDim.x) {
-        const int s = i / (kTapsB * 4), t = (i / 4) % kTapsB, ch = i % 4, gs = s0 + s;
-        bf16 *dst = As + s * kAStride + t * kCh + ch * 8;
-        if (t == kTapsB - 1) {
-            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(Hc + s * kRowStride + ch * 8);
-        } else {
-            const int yy = y + tap_dy(t), xx = x + tap_dx(t);
-            const bool inside = gs < n && yy >= 0 && xx >= 0 && xx < L;
-            const bf16 *src = inside ? h + (size_t)gs * ring + ((size_t)(yy % 3) * L + xx) * kCh + ch * 8 : h;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-                         "r"(inside ? 16 : 0)
-                         : "memory");
-        }
+    GatherSlots g;
+#pragma unroll
+    for (int j = 0; j < kGatherPerThread; ++j) {
+        const int i = threadIdx.x + j * kSampleThreads;
+        const int s = i / (kTapsA * 4), t = (i / 4) % kTapsA, ch = i % 4, gs = s0 + s;
+        g.dst[j] = (uint32_t)(s * kAStride + t * kCh + ch * 8) * 2u;
+        g.dy[j] = gs < n ? tap_dy(t) : -4096; // a sample past the batch reads nothing (zero fill)
+        g.dx[j] = tap_dx(t);
+        g.src[j] = (size_t)(gs < n ? gs : 0) * ring + ch * 8;
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    return g;
+}
+
+// Start one gather -- the taps of position (y, x) from the ring array h of one
+// layer into the A tile at shared address `tile` -- as one cp.async group,
+// zero-filling taps outside the lattice; the caller waits for it later.
+__device__ __forceinline__ void prefetch_taps(uint32_t tile, const bf16 *h, const GatherSlots &g, int L, int y, int x)
+{
+#pragma unroll
+    for (int j = 0; j < kGatherPerThread; ++j) {
+        const int yy = y + g.dy[j], xx = x + g.dx[j];
+        const bool inside = yy >= 0 && xx >= 0 && xx < L;
+        const bf16 *src = inside ? h + g.src[j] + ((size_t)(yy % 3) * L + xx) * kCh : h;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(tile + g.dst[j]), "l"(src),
+                     "r"(inside ? 16 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Wait until at most `pending` of this thread's most recent cp.async groups are
+// still in flight (pending < kSampleMaxBufs).
+__device__ __forceinline__ void cp_async_wait_pending(int pending)
+{
+    if (pending <= 0)
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    else if (pending == 1)
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else
+        asm volatile("cp.async.wait_group 2;" ::: "memory");
 }
 
 // Autoregressive sampling, one position k = y L + x at a time in raster order.
 // Each CTA owns 32 samples.  At step k every layer is evaluated at position k
-// only: its 13 taps come from the ring hist[l][sample][row % 3][x][c] of that
-// layer's earlier outputs (rows y-2..y) and from the value just computed at k.
+// only: its 13 taps are the 12 earlier positions, read from the ring
+// hist[l][sample][row % 3][x][c] of that layer's earlier outputs (rows
+// y-2..y), and the value just computed at k (shared memory, Hc).
 // s_k = +1 iff u < sigmoid(f_k), u from Philox (k >> 2, round, TAG_SAMPLE, id)
 // word k & 3; log q accumulates log sigmoid(s_k f_k) in FP64.  The step is a
-// chain of dependent layers, so its time is latency: the first layer reads
-// the sampled spins from a 3-row ring in shared memory, and each later layer
-// gathers its 12 earlier-position taps of all 32 samples with one burst of
-// cp.async copies (zero-filled outside the lattice), one round trip per layer.
-__global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, const float *__restrict__ w1,
+// chain of dependent layers, so its time is latency.  The first layer reads the
+// sampled spins from a 3-row ring in shared memory.  The earlier-position taps
+// of every later layer were written in earlier steps, so their gathers do not
+// wait for the layers before them.  The G = D - 1 gathers of a step (hidden
+// layers 1..nh, then the output layer) form one sequence over all steps,
+// q = k G + g - 1, filled into `nbuf` A tiles (tile q % nbuf) by cp.async
+// groups: gather q + nbuf is issued as soon as gather q's layer has released
+// its tile, so a layer waits only for its own group, issued nbuf layers
+// earlier (possibly in the previous step).  That is safe for nbuf <= G: gather
+// g of step k + 1 reads ring g - 1 at positions <= k, and the layer writing
+// ring g - 1 at k has then already run.  Hc is double buffered, since layer l
+// reads its tap 12 from the previous layer's values while writing its own.
+__global__ void __launch_bounds__(kSampleThreads) k_sample(const bf16 *__restrict__ wh, const float *__restrict__ w1,
                                                 const float *__restrict__ wD, const float *__restrict__ bias, int D,
-                                                int L, int n, bf16 *hist, int8_t *out, double *logq, PhiloxKey key,
-                                                uint32_t round, const uint32_t *ids)
+                                                int L, int n, int nbuf, bf16 *hist, int8_t *out, double *logq,
+                                                PhiloxKey key, uint32_t round, const uint32_t *ids)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int nh = D - 2;
+    const int nh = D - 2, G = nh + 1; // G gathers: hidden layers 1..nh and the output layer
     bf16 *Wh = reinterpret_cast<bf16 *>(smem);                    // [nh][13][32][40]
-    bf16 *As = Wh + (size_t)nh * kTapsB * kCh * kRowStride;       // [32][424]
-    bf16 *Hc = As + kSampleTile * kAStride;                        // [32][40] current layer at position k
-    float *W1 = reinterpret_cast<float *>(Hc + kSampleTile * kRowStride); // [32][12]
+    bf16 *As = Wh + (size_t)nh * kTapsB * kCh * kRowStride;       // nbuf x [32][392]
+    bf16 *Hc = As + (size_t)nbuf * kSampleTile * kAStride;         // 2 x [32][40] layer values at position k
+    float *W1 = reinterpret_cast<float *>(Hc + 2 * kSampleTile * kRowStride); // [12][32] (tap-major)
     float *WD = W1 + kCh * kTapsA;                                 // [13][32]
     float *Bs = WD + kTapsB * kCh;                                 // [(D-1) 32 + 1]
     float *Fs = Bs + (D - 1) * kCh + 1;                            // [32] logits
@@ -1163,7 +1208,7 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
         Wh[row * kRowStride + c] = wh[i];
     }
     for (int i = tid; i < kCh * kTapsA; i += blockDim.x)
-        W1[i] = w1[i];
+        W1[(i % kTapsA) * kCh + i / kTapsA] = w1[i]; // w1 is [o][t]
     for (int i = tid; i < kTapsB * kCh; i += blockDim.x)
         WD[i] = wD[i];
     for (int i = tid; i < (D - 1) * kCh + 1; i += blockDim.x)
@@ -1173,28 +1218,56 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
     if (tid < kSampleTile && s0 + tid < n)
         my_id = ids ? ids[s0 + tid] : (uint32_t)(s0 + tid);
     const size_t ring = (size_t)3 * L * kCh; // per sample per layer
+    const size_t abuf = (size_t)kSampleTile * kAStride;
+    const int Q = L * L * G; // gathers in all
+    const GatherSlots slots = gather_slots(s0, n, ring);
+    const uint32_t as0 = smem_u32(As);
+    // gather q = k G + g - 1 reads the ring of layer g - 1 for position k into tile q % nbuf
+    auto issue = [&](int q) {
+        if (q >= Q)
+            return;
+        const int kq = q / G, g = q - kq * G + 1, yq = kq / L;
+        prefetch_taps(as0 + (uint32_t)((q % nbuf) * abuf * 2), hist + (size_t)(g - 1) * n * ring, slots, L, yq,
+                      kq - yq * L);
+    };
     __syncthreads();
+    for (int q = 0; q < nbuf; ++q)
+        issue(q);
     for (int k = 0; k < L * L; ++k) {
         const int y = k / L, x = k % L, slot = y % 3;
-        // ---- layer 1 (CUDA cores): 32 samples x 32 channels
-        for (int i = tid; i < kSampleTile * kCh; i += blockDim.x) {
-            const int s = i / kCh, o = i % kCh, gs = s0 + s;
-            float acc = Bs[o];
+        // ---- layer 1 (CUDA cores): 32 samples x 32 channels, 4 channels of one sample per thread
+        {
+            const int s = tid >> 3, o0 = (tid & 7) * 4, gs = s0 + s;
+            float acc[4] = {Bs[o0], Bs[o0 + 1], Bs[o0 + 2], Bs[o0 + 3]};
             if (gs < n)
+#pragma unroll
                 for (int t = 0; t < kTapsA; ++t) {
                     const int yy = y + tap_dy(t), xx = x + tap_dx(t);
-                    if (yy >= 0 && xx >= 0 && xx < L)
-                        acc += W1[o * kTapsA + t] * (float)Sr[(s * 3 + yy % 3) * L + xx];
+                    if (yy >= 0 && xx >= 0 && xx < L) {
+                        const float v = (float)Sr[(s * 3 + yy % 3) * L + xx];
+                        const float4 w = *reinterpret_cast<const float4 *>(W1 + t * kCh + o0);
+                        acc[0] += w.x * v;
+                        acc[1] += w.y * v;
+                        acc[2] += w.z * v;
+                        acc[3] += w.w * v;
+                    }
                 }
-            const bf16 h = __float2bfloat16(fmaxf(acc, 0.f));
-            Hc[s * kRowStride + o] = h;
-            if (gs < n)
-                hist[((size_t)gs * ring) + ((size_t)slot * L + x) * kCh + o] = h; // layer index 0
+            const __nv_bfloat162 h01 = __floats2bfloat162_rn(fmaxf(acc[0], 0.f), fmaxf(acc[1], 0.f));
+            const __nv_bfloat162 h23 = __floats2bfloat162_rn(fmaxf(acc[2], 0.f), fmaxf(acc[3], 0.f));
+            uint2 pk;
+            pk.x = *reinterpret_cast<const uint32_t *>(&h01);
+            pk.y = *reinterpret_cast<const uint32_t *>(&h23);
+            *reinterpret_cast<uint2 *>(Hc + s * kRowStride + o0) = pk;
+            if (gs < n) // layer index 0
+                *reinterpret_cast<uint2 *>(hist + (size_t)gs * ring + ((size_t)slot * L + x) * kCh + o0) = pk;
         }
-        __syncthreads();
         // ---- hidden layers (tensor cores): M = 32 samples, N = 32, K = 13 x 32
         for (int l = 1; l <= nh; ++l) {
-            gather_taps(As, Hc, hist + (size_t)(l - 1) * n * ring, ring, s0, n, L, y, x);
+            const int q = k * G + l - 1;
+            const bf16 *At = As + (size_t)(q % nbuf) * abuf;
+            const bf16 *Hp = Hc + (size_t)((l - 1) & 1) * kSampleTile * kRowStride; // layer l - 1 at k
+            bf16 *Hn = Hc + (size_t)(l & 1) * kSampleTile * kRowStride;
+            cp_async_wait_pending(min(nbuf - 1, Q - 1 - q));
             __syncthreads();
             const int mt = warp >> 2, nt = warp & 3; // 8 warps: 2 m-tiles x 4 n-tiles
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1202,11 +1275,18 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
             const int arow = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
             const int brow = nt * 8 + (lane & 7), bcol = ((lane >> 3) & 1) * 8;
 #pragma unroll 2
-            for (int kk = 0; kk < 2 * kTapsB; ++kk) {
+            for (int kk = 0; kk < 2 * kTapsA; ++kk) {
                 uint32_t a0, a1, a2, a3, b0, b1;
-                ldsm_x4(smem_u32(As + arow * kAStride + kk * 16 + acol), a0, a1, a2, a3);
+                ldsm_x4(smem_u32(At + arow * kAStride + kk * 16 + acol), a0, a1, a2, a3);
                 const int t = kk >> 1, half = kk & 1;
                 ldsm_x2(smem_u32(Wl + (t * kCh + brow) * kRowStride + half * 16 + bcol), b0, b1);
+                mma_bf16(acc, a0, a1, a2, a3, b0, b1);
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) { // tap 12: position k itself
+                uint32_t a0, a1, a2, a3, b0, b1;
+                ldsm_x4(smem_u32(Hp + arow * kRowStride + half * 16 + acol), a0, a1, a2, a3);
+                ldsm_x2(smem_u32(Wl + (kTapsA * kCh + brow) * kRowStride + half * 16 + bcol), b0, b1);
                 mma_bf16(acc, a0, a1, a2, a3, b0, b1);
             }
             const int g = lane >> 2, t4 = lane & 3, o = nt * 8 + 2 * t4;
@@ -1216,16 +1296,20 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
                 const int s = mt * 16 + g + 8 * h, gs = s0 + s;
                 const float bo = Bs[l * kCh + o], b1v = Bs[l * kCh + o + 1];
                 const __nv_bfloat162 v = __floats2bfloat162_rn(fmaxf(acc[2 * h] + bo, 0.f), fmaxf(acc[2 * h + 1] + b1v, 0.f));
-                *reinterpret_cast<__nv_bfloat162 *>(Hc + s * kRowStride + o) = v;
+                *reinterpret_cast<__nv_bfloat162 *>(Hn + s * kRowStride + o) = v;
                 if (gs < n) // the ring of layer l feeds the taps of layer l + 1 (the output layer for l = nh)
                     *reinterpret_cast<__nv_bfloat162 *>(hcur + (size_t)gs * ring + ((size_t)slot * L + x) * kCh + o) = v;
             }
-            __syncthreads();
+            __syncthreads(); // every warp is done with tile At: refill it
+            issue(q + nbuf);
         }
         // ---- output layer (CUDA cores): 8 lanes per sample, 4 channels each
-        gather_taps(As, Hc, hist + (size_t)nh * n * ring, ring, s0, n, L, y, x);
+        const int qo = k * G + G - 1;
+        cp_async_wait_pending(min(nbuf - 1, Q - 1 - qo));
         __syncthreads();
         {
+            const bf16 *At = As + (size_t)(qo % nbuf) * abuf;
+            const bf16 *Hp = Hc + (size_t)(nh & 1) * kSampleTile * kRowStride;
             const int s = tid >> 3, part = tid & 7, gs = s0 + s;
             float acc = 0.f;
             if (gs < n)
@@ -1233,7 +1317,7 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
                     const int yy = y + tap_dy(t), xx = x + tap_dx(t);
                     if (yy < 0 || xx < 0 || xx >= L)
                         continue;
-                    const bf16 *hp = As + s * kAStride + t * kCh;
+                    const bf16 *hp = t < kTapsA ? At + s * kAStride + t * kCh : Hp + s * kRowStride;
 #pragma unroll
                     for (int c = part * 4; c < part * 4 + 4; ++c)
                         acc += WD[t * kCh + c] * bf(hp[c]);
@@ -1245,6 +1329,7 @@ __global__ void __launch_bounds__(256) k_sample(const bf16 *__restrict__ wh, con
                 Fs[s] = acc + Bs[(D - 1) * kCh];
         }
         __syncthreads();
+        issue(qo + nbuf);
         // ---- draw s_k
         if (tid < kSampleTile && s0 + tid < n) {
             const float f = Fs[tid];
@@ -1456,11 +1541,32 @@ size_t dw_smem(int L)
     const int PZ = ((L + 15) / 16) * 16;
     return (size_t)2 * PZ * kRowStride * 2 + (size_t)3 * (PZ + 4) * kRowStride * 2;
 }
-size_t sample_smem(int D, int L)
+size_t sample_smem(int D, int L, int nbuf)
 {
-    return (size_t)(D - 2) * kTapsB * kCh * kRowStride * 2 + (size_t)kSampleTile * kAStride * 2 +
-           (size_t)kSampleTile * kRowStride * 2 + (size_t)(kCh * kTapsA + kTapsB * kCh + (D - 1) * kCh + 1 + 32) * 4 +
-           (size_t)kSampleTile * 3 * L;
+    return (size_t)(D - 2) * kTapsB * kCh * kRowStride * 2 + (size_t)nbuf * kSampleTile * kAStride * 2 +
+           (size_t)2 * kSampleTile * kRowStride * 2 +
+           (size_t)(kCh * kTapsA + kTapsB * kCh + (D - 1) * kCh + 1 + 32) * 4 + (size_t)kSampleTile * 3 * L;
+}
+
+// Gathered A tiles the sampler keeps in flight: as many as fit, at most 3 and
+// at most the D - 1 gathers of one step.
+int sample_bufs(int D, int L)
+{
+    for (int b = std::min(kSampleMaxBufs, D - 1); b > 1; --b)
+        if (sample_smem(D, L, b) <= kSampleSmemLimit)
+            return b;
+    return 1;
+}
+
+// Dynamic shared memory a kernel may use: raised to what this network needs,
+// never lowered, so that creating a smaller network leaves larger ones usable.
+cudaError_t raise_smem_limit(const void *kernel, size_t bytes)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess || (int)bytes <= a.maxDynamicSharedSizeBytes)
+        return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 cudaError_t prep(mc_van *w)
@@ -1620,15 +1726,13 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(w->ws, 0, o.hist, w->stream); // params, Adam state, buffers
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tma_conv_geom(L).smem_bytes);
+        e = raise_smem_limit((const void *)k_conv32_tma, tma_conv_geom(L).smem_bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv32_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc_conv_geom(L, 8).smem_bytes);
+        e = raise_smem_limit((const void *)k_conv32_bwd_tc, tc_conv_geom(L, 8).smem_bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dw32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(L));
+        e = raise_smem_limit((const void *)k_dw32, dw_smem(L));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sample_smem(depth, L));
+        e = raise_smem_limit((const void *)k_sample, sample_smem(depth, L, sample_bufs(depth, L)));
     if (e != cudaSuccess) {
         delete w;
         return vfail(MC_ECUDA, std::string("mc_van_create: ") + cudaGetErrorString(e));
@@ -1731,8 +1835,9 @@ mc_status mc_van_sample(mc_van *w, int32_t n, uint32_t round, const uint32_t *de
     cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n * w->L * w->L, w->stream);
     if (e == cudaSuccess) {
         const unsigned blocks = (unsigned)((n + kSampleTile - 1) / kSampleTile);
-        k_sample<<<blocks, 256, sample_smem(w->D, w->L), w->stream>>>(w->wh, w->w1, w->wD, w->bias, w->D, w->L, n, w->hist,
-                                                                out, lq, w->key, round, dev_ids);
+        const int nbuf = sample_bufs(w->D, w->L);
+        k_sample<<<blocks, kSampleThreads, sample_smem(w->D, w->L, nbuf), w->stream>>>(w->wh, w->w1, w->wD, w->bias, w->D, w->L, n,
+                                                                      nbuf, w->hist, out, lq, w->key, round, dev_ids);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess)

@@ -242,6 +242,32 @@ def test_full_size_L64_sampler_log_prob_and_gradients():
     net.close()
 
 
+def test_sampler_prefetch_depths_and_coexisting_networks():
+    """The sampler keeps up to three gathered tap tiles in flight, as many as
+    shared memory allows: three at depth <= 6 (at depth 3 more than there are
+    gathers), two at depth 7 and L = 8, one at depth 7 and L = 96.  For each,
+    the sampler's FP64 log q equals the forward network's on what it sampled
+    and the BF16-activation oracle's on two of the samples.  The networks are
+    all created before any is sampled: creating a smaller network must not
+    shrink the shared memory a larger one launches with."""
+    cases = [(7, 96, 2), (3, 8, 64), (7, 8, 64), (6, 16, 64)]
+    nets = []
+    for depth, L, n in cases:
+        p = bf16_params(depth=depth, seed=20 + depth, bias=0.2)
+        net = mc.VAN(L, batch=n, depth=depth, seed=depth)
+        net.set_params(mc.mc.van_pack(p))
+        nets.append((net, p, L, n))
+    for net, p, L, n in nets:
+        s, lq = net.sample(n, round=5)
+        lp = net.log_prob(s).cpu().numpy()
+        lqs = lq.cpu().numpy()
+        assert np.max(np.abs(lqs - lp) / np.abs(lp)) < 1e-5, (L, lqs[:4], lp[:4])
+        ob = van.log_prob(p, s[[0, n - 1]].cpu().numpy().astype(np.float64), act="bf16")
+        assert np.max(np.abs(lp[[0, n - 1]] - ob) / np.abs(ob)) < 1e-4, (L, lp[[0, n - 1]], ob)
+    for net, *_ in nets:
+        net.close()
+
+
 @pytest.mark.parametrize("L", [2, 6, 128])
 def test_log_prob_extreme_lattice_sides(L):
     """The smallest lattices (one padded tile, rows past the lattice) and the

@@ -1317,10 +1317,15 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(const bf16 *__restric
                     const int yy = y + tap_dy(t), xx = x + tap_dx(t);
                     if (yy < 0 || xx < 0 || xx >= L)
                         continue;
-                    const bf16 *hp = t < kTapsA ? At + s * kAStride + t * kCh : Hp + s * kRowStride;
-#pragma unroll
-                    for (int c = part * 4; c < part * 4 + 4; ++c)
-                        acc += WD[t * kCh + c] * bf(hp[c]);
+                    const bf16 *hp = (t < kTapsA ? At + s * kAStride + t * kCh : Hp + s * kRowStride) + part * 4;
+                    const uint2 hv = *reinterpret_cast<const uint2 *>(hp); // 4 channels
+                    const float2 h01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hv.x));
+                    const float2 h23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hv.y));
+                    const float4 w = *reinterpret_cast<const float4 *>(WD + t * kCh + part * 4);
+                    acc += w.x * h01.x;
+                    acc += w.y * h01.y;
+                    acc += w.z * h23.x;
+                    acc += w.w * h23.y;
                 }
             acc += __shfl_xor_sync(0xffffffffu, acc, 1);
             acc += __shfl_xor_sync(0xffffffffu, acc, 2);

@@ -1213,7 +1213,8 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(const bf16 *__restric
         WD[i] = wD[i];
     for (int i = tid; i < (D - 1) * kCh + 1; i += blockDim.x)
         Bs[i] = bias[i];
-    double lq = 0.0; // owned by thread s (< 32)
+    double lq = 0.0;     // owned by thread s (< 32): log q of positions < k - 1
+    float lq_term = 0.f; // s_{k-1} f_{k-1}, whose log sigmoid is added at step k
     uint32_t my_id = 0;
     if (tid < kSampleTile && s0 + tid < n)
         my_id = ids ? ids[s0 + tid] : (uint32_t)(s0 + tid);
@@ -1235,6 +1236,8 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(const bf16 *__restric
         issue(q);
     for (int k = 0; k < L * L; ++k) {
         const int y = k / L, x = k % L, slot = y % 3;
+        if (k > 0 && tid < kSampleTile && s0 + tid < n)
+            lq += (double)log_sigmoid(lq_term);
         // ---- layer 1 (CUDA cores): 32 samples x 32 channels, 4 channels of one sample per thread
         {
             const int s = tid >> 3, o0 = (tid & 7) * 4, gs = s0 + s;
@@ -1339,17 +1342,16 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(const bf16 *__restric
         if (tid < kSampleTile && s0 + tid < n) {
             const float f = Fs[tid];
             const uint4 r = philox4x32_10(make_uint4((uint32_t)k >> 2, round, kTagVanSample, my_id), key);
-            const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
-            const float u = uniform_open0(rr[k & 3]);
-            const float sp = u < sigmoid(f) ? 1.f : -1.f;
-            lq += (double)log_sigmoid(sp * f);
-            out[((size_t)(s0 + tid) * L + y) * L + x] = (int8_t)sp;
+            const uint32_t rk = (k & 2) ? ((k & 1) ? r.w : r.z) : ((k & 1) ? r.y : r.x);
+            const float sp = uniform_open0(rk) < sigmoid(f) ? 1.f : -1.f;
             Sr[(tid * 3 + slot) * L + x] = (int8_t)sp;
+            out[((size_t)(s0 + tid) * L + y) * L + x] = (int8_t)sp;
+            lq_term = sp * f; // added to log q at the next step, off this step's tail
         }
         __syncthreads();
     }
     if (tid < kSampleTile && s0 + tid < n)
-        logq[s0 + tid] = lq;
+        logq[s0 + tid] = lq + (double)log_sigmoid(lq_term);
 }
 
 // Copy the int8 lattices of every chain of an int8-layout Ising context into

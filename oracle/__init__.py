@@ -53,6 +53,7 @@ def lib() -> ctypes.CDLL:
             c = ctypes
             P = c.c_void_p
             L.orc_philox4x32_10.argtypes = [P, P, P]
+            L.orc_philox_words.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_long, P]
             L.orc_ising_thresholds.argtypes = [c.c_double, P]
             L.orc_ising_init.argtypes = [P, c.c_int, c.c_int, c.c_uint64, c.c_uint32, c.c_int]
             L.orc_ising_sweep.argtypes = [P, c.c_int, c.c_int, P, c.c_uint64, c.c_uint32, c.c_uint32]
@@ -96,6 +97,21 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
+
+
+def philox_words(seed: int, c1: int, c2: int, c3: int, n: int) -> np.ndarray:
+    """n consecutive words of one stream: word j is word j & 3 of the block
+    with counter (j >> 2, c1, c2, c3), key (seed low, seed high)."""
+    out = np.zeros(n, dtype=np.uint32)
+    lib().orc_philox_words(seed & (2**64 - 1), c1 & 0xFFFFFFFF, c2 & 0xFFFFFFFF, c3 & 0xFFFFFFFF, int(n), _ptr(out))
+    return out
+
+
+def uniform01(r) -> np.ndarray:
+    """Random words -> (0, 1]: ((r >> 8) + 1) 2^-24, the paper's 24-bit
+    resolution (Sec. 2.2) shifted off zero."""
+    r = np.asarray(r, dtype=np.uint32)
+    return ((r >> 8).astype(np.float64) + 1.0) * 2.0 ** -24
 
 
 # --------------------------------------------------------------------------- Ising

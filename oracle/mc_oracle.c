@@ -63,6 +63,21 @@ ORC_API void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uin
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
+/* A run of n consecutive 32-bit words of one stream: word j is word (j & 3)
+ * of the block with counter (j >> 2, c1, c2, c3) and key (seed low, seed
+ * high) -- how every per-position draw below takes its random words. */
+ORC_API void orc_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, long n, uint32_t *out)
+{
+    for (long j = 0; j < n; j += 4) {
+        uint32_t ctr[4] = {(uint32_t)(j >> 2), c1, c2, c3};
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        for (long i = j; i < n && i < j + 4; ++i)
+            out[i] = r[i - j];
+    }
+}
+
 /* Stream layout shared (as a specification, not as code) with the GPU path.
  * key = (seed low 32 bits, seed high 32 bits); counter = (c0, c1, c2, c3) with
  * c3 = chain id and c2's top byte a tag naming what the numbers are for.    */

@@ -117,10 +117,10 @@ def log_prob(params, s: np.ndarray, act: str = "fp64") -> np.ndarray:
     return log_sigmoid(s * f).reshape(len(s), -1).sum(axis=1)
 
 
-def log_prob_sym(params, s: np.ndarray) -> np.ndarray:
+def log_prob_sym(params, s: np.ndarray, act: str = "fp64") -> np.ndarray:
     """log q_sym(s), q_sym(s) = (q(s) + q(-s)) / 2 (symmetry under the global
     spin flip, Wu-Wang-Zhang)."""
-    return np.logaddexp(log_prob(params, s), log_prob(params, -s)) - np.log(2.0)
+    return np.logaddexp(log_prob(params, s, act), log_prob(params, -s, act)) - np.log(2.0)
 
 
 def loss_and_grad(params, s: np.ndarray, act: str = "fp64"):
@@ -153,14 +153,14 @@ def loss_and_grad(params, s: np.ndarray, act: str = "fp64"):
     return float(loss), grads
 
 
-def sample(params, n: int, L: int, uniforms: np.ndarray) -> np.ndarray:
+def sample(params, n: int, L: int, uniforms: np.ndarray, act: str = "fp64") -> np.ndarray:
     """Autoregressive sampling, one position at a time in raster order:
-    s_k = +1 iff u_k < sigmoid(f_k(s_<k)).  uniforms: (n, L*L) in (0, 1).
+    s_k = +1 iff u_k < sigmoid(f_k(s_<k)).  uniforms: (n, L*L) in (0, 1].
     Slow (L^2 full forward passes): for small lattices only."""
     s = np.zeros((n, L, L))
     for k in range(L * L):
         y, x = divmod(k, L)
-        f, _ = forward(params, s)
+        f, _ = forward(params, s, act)
         p = 1.0 / (1.0 + np.exp(-f[:, y, x]))
         s[:, y, x] = np.where(uniforms[:, k] < p, 1.0, -1.0)
     return s
@@ -171,8 +171,72 @@ def ising_energy(s: np.ndarray) -> np.ndarray:
     return -(s * np.roll(s, -1, axis=-1)).sum(axis=(-2, -1)) - (s * np.roll(s, -1, axis=-2)).sum(axis=(-2, -1))
 
 
-def mh_accept_logratio(params, beta: float, s_cur: np.ndarray, s_prop: np.ndarray) -> np.ndarray:
+def mh_accept_logratio(params, beta: float, s_cur: np.ndarray, s_prop: np.ndarray,
+                       act: str = "fp64") -> np.ndarray:
     """log of the Metropolis-Hastings ratio for an independence proposal from
     q_sym: -beta (E' - E) + log q_sym(s) - log q_sym(s')."""
-    return (-beta * (ising_energy(s_prop) - ising_energy(s_cur)) + log_prob_sym(params, s_cur)
-            - log_prob_sym(params, s_prop))
+    return (-beta * (ising_energy(s_prop) - ising_energy(s_cur)) + log_prob_sym(params, s_cur, act)
+            - log_prob_sym(params, s_prop, act))
+
+
+def conditionals(params, s: np.ndarray, act: str = "fp64") -> np.ndarray:
+    """p(s_k = +1 | s_<k) at every position of each configuration, from one
+    forward pass: the probability the sampler compared its uniform with at
+    position k, given that it had drawn s_<k."""
+    f, _ = forward(params, np.asarray(s, dtype=np.float64), act)
+    return 1.0 / (1.0 + np.exp(-f))
+
+
+def grad_scale(params, s: np.ndarray, act: str = "fp64"):
+    """Per parameter, the sum of the absolute values of the terms that make
+    up its gradient through the whole backward pass: the backward of
+    loss_and_grad with |dloss/df| at the output, |W| in the products and the
+    ReLU masks kept.  If every term an implementation sums carries a relative
+    error of at most e, its gradient element errs by at most about e times
+    this scale, whatever cancellation happens inside the sum (triangle
+    inequality).  Same structure as grads of loss_and_grad."""
+    B = len(s)
+    f, cache = forward(params, s, act)
+    g = np.exp(-np.logaddexp(0.0, s * f)) / B  # |s sigmoid(-s f)| / B without overflow
+    grad_out = g[:, None, :, :]
+    out = [None] * len(params)
+    D = len(params)
+    for l in range(D - 1, -1, -1):
+        W, b = params[l]
+        x, z = cache[l]
+        dz = grad_out if l == D - 1 else grad_out * (z > 0)
+        mask = "A" if l == 0 else "B"
+        sW = np.zeros_like(W)
+        sx = np.zeros_like(x)
+        for dy, dx in taps(mask):
+            xs = np.abs(shift(x, dy, dx))
+            sW[:, :, dy + R, dx + R] = np.einsum("boxy,bixy->oi", dz, xs)
+            sx += shift(np.einsum("oi,boxy->bixy", np.abs(W[:, :, dy + R, dx + R]), dz), -dy, -dx)
+        out[l] = (sW, dz.sum(axis=(0, 2, 3)))
+        grad_out = sx
+    return out
+
+
+# Random streams of the proposal, keyed by the network's 64-bit seed (key =
+# seed low, seed high), in the counter layout of the Philox stream the local
+# sweeps use:
+#   sampler : position k of the sample with id i takes word k & 3 of the block
+#             (k >> 2, round, TAG_SAMPLE, i);
+#   MH step : chain c takes the block (0, round, TAG_MH, c); word 0 gives the
+#             accept uniform, the top bit of word 1 the global flip.
+# A uniform is ((r >> 8) + 1) 2^-24, in (0, 1].
+TAG_SAMPLE = 0x21000000
+TAG_MH = 0x22000000
+
+
+def sampler_uniforms(seed: int, rnd: int, ids, L: int) -> np.ndarray:
+    """(len(ids), L*L) uniforms of the sampler's stream."""
+    from . import philox_words, uniform01
+    return np.stack([uniform01(philox_words(seed, rnd, TAG_SAMPLE, int(i), L * L)) for i in ids])
+
+
+def mh_draws(seed: int, rnd: int, chain_ids):
+    """(accept uniform, global flip) per chain of one MH round."""
+    from . import philox_words, uniform01
+    w = np.stack([philox_words(seed, rnd, TAG_MH, int(c), 2) for c in chain_ids])
+    return uniform01(w[:, 0]), (w[:, 1] >> 31).astype(bool)

@@ -163,3 +163,67 @@ def test_bf16_activation_network_is_normalised():
     p = van.masked(van.init_params(depth=4, channels=4, seed=3, scale=2.0))
     q = np.exp(van.log_prob(p, all_states(4, 4), act="bf16"))
     assert abs(q.sum() - 1.0) < 1e-10
+
+
+def test_philox_words_are_the_pinned_blocks():
+    """The word-run helper the proposal's streams use returns, word for word,
+    the Philox4x32-10 blocks pinned by the known-answer vectors."""
+    import oracle
+    seed = 0x0123456789ABCDEF
+    w = oracle.philox_words(seed, 7, van.TAG_SAMPLE, 11, 22)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for j in range(22):
+        blk = oracle.philox4x32_10([j >> 2, 7, van.TAG_SAMPLE, 11], key)
+        assert w[j] == blk[j & 3]
+
+
+def test_proposal_streams_are_uniform_and_distinct():
+    u = van.sampler_uniforms(5, 3, range(64), 16)
+    assert u.shape == (64, 256) and u.min() > 0.0 and u.max() <= 1.0
+    assert stats.kstest(u.ravel(), "uniform").pvalue > 1e-4
+    assert np.abs(np.corrcoef(u[:32].ravel(), u[32:].ravel())[0, 1]) < 0.02
+    u2 = van.sampler_uniforms(5, 4, range(64), 16)  # another round
+    assert np.abs(np.corrcoef(u.ravel(), u2.ravel())[0, 1]) < 0.02
+    a, flip = van.mh_draws(5, 3, range(20000))
+    assert a.min() > 0.0 and a.max() <= 1.0 and stats.kstest(a, "uniform").pvalue > 1e-4
+    assert abs(flip.mean() - 0.5) < 4.0 * 0.5 / np.sqrt(len(flip))
+
+
+@pytest.mark.parametrize("act", ["fp64", "bf16"])
+def test_sample_takes_each_position_from_its_conditional(act):
+    """The defining property of the autoregressive sampler: at every position,
+    the drawn spin is +1 exactly when the position's uniform lies below
+    p(s_k = +1 | s_<k) evaluated on the drawn prefix (one forward pass of the
+    result gives every conditional at once)."""
+    L, n = 5, 40
+    p = van.masked(van.init_params(depth=4, channels=6, seed=12, scale=1.5))
+    p[0] = (p[0][0], p[0][1] + 0.3)
+    u = van.sampler_uniforms(9, 1, range(n), L)
+    s = van.sample(p, n, L, u, act=act)
+    pk = van.conditionals(p, s, act=act).reshape(n, -1)
+    want = np.where(u < pk, 1.0, -1.0)
+    np.testing.assert_array_equal(s.reshape(n, -1), want)
+    # and the draws are not trivial: both spins occur, from a spread of probabilities
+    assert 0.2 < (s > 0).mean() < 0.8 and pk.std() > 0.05
+
+
+def test_grad_scale_bounds_every_gradient_element():
+    """|gradient| <= scale element by element (triangle inequality), with
+    equality when no sum cancels (non-negative weights, all spins +1: every
+    term of every sum has the same sign)."""
+    rng = np.random.default_rng(4)
+    p = van.masked(van.init_params(depth=4, channels=5, seed=8))
+    s = np.where(rng.random((6, 6, 6)) < 0.5, 1.0, -1.0)
+    _, g = van.loss_and_grad(p, s)
+    sc = van.grad_scale(p, s)
+    for (gW, gb), (sW, sb) in zip(g, sc):
+        assert np.all(np.abs(gW) <= sW * (1 + 1e-12) + 1e-300)
+        assert np.all(np.abs(gb) <= sb * (1 + 1e-12) + 1e-300)
+        assert (sW > 2 * np.abs(gW)).any()  # with mixed signs some sums do cancel
+    pos = [(np.abs(W), b) for W, b in p]
+    ones = np.ones((3, 6, 6))
+    _, g = van.loss_and_grad(pos, ones)
+    sc = van.grad_scale(pos, ones)
+    for (gW, gb), (sW, sb) in zip(g, sc):
+        np.testing.assert_allclose(np.abs(gW), sW, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(np.abs(gb), sb, rtol=1e-12, atol=1e-300)

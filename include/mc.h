@@ -259,6 +259,13 @@ MC_API mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t d
 MC_API mc_status mc_van_set_params(mc_van *w, const float *host_params, size_t n); /* resets Adam */
 /* Parameters (and, if host_grads != NULL, the gradient of the last training step). */
 MC_API mc_status mc_van_get_params(mc_van *w, float *host_params, size_t n, float *host_grads);
+/* Hidden activations of the last forward pass (log_prob, train_step; not the
+ * sampler), for element-wise parity checks of the network: the BF16 output of
+ * layer `layer` (0 = the first 1 -> 32 layer, ..., depth - 2 = the last hidden
+ * layer), after its ReLU, for the first n configurations of that pass, as raw
+ * BF16 bit patterns uint16 [n][L][L][32] into host memory (synchronous).
+ * MC_EINVAL for a layer outside [0, depth - 2] or n outside [1, batch]. */
+MC_API mc_status mc_van_get_activations(mc_van *w, int32_t layer, int32_t n, uint16_t *host_dst);
 /* log q of n device configurations int8 [n][L][L] (or of their global flips if
  * negate) into device doubles (async). */
 MC_API mc_status mc_van_log_prob(mc_van *w, const int8_t *dev_spins, int32_t n, int32_t negate, double *dev_logq);
@@ -296,8 +303,13 @@ MC_API mc_status mc_ising_gather(mc_ctx *c, int8_t *dev_buf, int32_t back);
  * allocates nothing.  Its partial sums live in a fixed 256 KiB array inside
  * libmc.so, held on every device that loads the library until the process
  * exits; lattices of more than 4,194,304 sites are rejected with MC_EINVAL.
- * The first call on a device, made with that device current, looks up the
- * array's device address; make that first call before any stream capture.
+ * The launch and the array are those of the CURRENT device, which must be the
+ * device holding `links`, `out` and `cuda_stream`.  The first call on a
+ * device, made with that device current, looks up the array's device address
+ * and keeps it for the life of the process; make that first call before any
+ * stream capture.  A cudaDeviceReset (or anything else that destroys the
+ * device's primary context) invalidates the kept address: do not call this
+ * entry point on that device afterwards.
  * Every call uses the same array: calls that overlap on the GPU (other
  * streams, other host threads) race and give wrong results. */
 MC_API mc_status mc_su2_plaquette_noalloc(const float *links, const int32_t L[4], double *out, void *cuda_stream);

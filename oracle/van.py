@@ -123,6 +123,45 @@ def log_prob_sym(params, s: np.ndarray, act: str = "fp64") -> np.ndarray:
     return np.logaddexp(log_prob(params, s, act), log_prob(params, -s, act)) - np.log(2.0)
 
 
+def _backward(params, cache, masks, grad_f, mode: str = "grad"):
+    """Backward pass from d loss / d f (grad_f, (B, L, L)) through the layers.
+    masks[l] (l < D - 1): the ReLU derivative of layer l's output (1 where the
+    output is positive).  mode "grad": the gradient; "scale": per element the
+    sum of |terms| through the whole pass (|grad_f| in, |W| in the products);
+    "direct": per element the sum of |terms| of its own last contraction only,
+    |upstream gradient| x |activation| with the true upstream gradient.
+    Returns [(dW, db)] per layer."""
+    D = len(params)
+    grad_out = (np.abs(grad_f) if mode == "scale" else grad_f)[:, None, :, :]
+    out = [None] * D
+    for l in range(D - 1, -1, -1):
+        W, b = params[l]
+        x, _ = cache[l]
+        dz = grad_out if l == D - 1 else grad_out * masks[l]
+        mask = "A" if l == 0 else "B"
+        dW = np.zeros_like(W)
+        dx_in = np.zeros_like(x)
+        Wb = np.abs(W) if mode == "scale" else W
+        for dy, dx in taps(mask):
+            xs = shift(x, dy, dx)
+            if mode == "grad":
+                dW[:, :, dy + R, dx + R] = np.einsum("boxy,bixy->oi", dz, xs)
+            elif mode == "scale":
+                dW[:, :, dy + R, dx + R] = np.einsum("boxy,bixy->oi", dz, np.abs(xs))
+            else:
+                dW[:, :, dy + R, dx + R] = np.einsum("boxy,bixy->oi", np.abs(dz), np.abs(xs))
+            # x enters z at (y, x) via x[y+dy, x+dx]: scatter back with the opposite shift
+            dx_in += shift(np.einsum("oi,boxy->bixy", Wb[:, :, dy + R, dx + R], dz), -dy, -dx)
+        out[l] = (dW, (np.abs(dz) if mode == "direct" else dz).sum(axis=(0, 2, 3)))
+        grad_out = dx_in
+    return out
+
+
+def _grad_f(s, f):
+    """d loss / d f of loss = -mean_b log q(s_b): -(1/B) s sigmoid(-s f)."""
+    return -(s * np.exp(-np.logaddexp(0.0, s * f))) / len(s)
+
+
 def loss_and_grad(params, s: np.ndarray, act: str = "fp64"):
     """Negative mean log-likelihood -mean_b log q(s_b) and its gradient (of
     the network with act-rounded activations, the rounding treated as part of
@@ -130,27 +169,88 @@ def loss_and_grad(params, s: np.ndarray, act: str = "fp64"):
     B = len(s)
     f, cache = forward(params, s, act)
     loss = -log_sigmoid(s * f).reshape(B, -1).sum(axis=1).mean()
-    # d loss / d f = -(1/B) s sigmoid(-s f)
-    g = -(s * (1.0 / (1.0 + np.exp(s * f)))) / B
-    grad_out = g[:, None, :, :]
-    grads = [None] * len(params)
+    masks = [(z > 0).astype(np.float64) for _, z in cache[:-1]]
+    return float(loss), _backward(params, cache, masks, _grad_f(s, f))
+
+
+def grad_scale(params, s: np.ndarray, act: str = "fp64", propagate: bool = True):
+    """Per parameter, a magnitude scale of its gradient sum.
+    propagate=True: the sum of the absolute values of the terms that make up
+    the gradient through the whole backward pass -- the backward of
+    loss_and_grad with |dloss/df| at the output, |W| in the products and the
+    ReLU masks kept.  If every term an implementation sums carries a relative
+    error of at most e, its gradient element errs by at most about e times
+    this scale, whatever cancellation happens inside the sums (triangle
+    inequality).  propagate=False: only the last contraction in absolute
+    values, sum over samples and positions of |upstream gradient| x
+    |activation| with the true (signed) upstream gradient -- the scale of the
+    element's own sum.  Same structure as grads of loss_and_grad."""
+    f, cache = forward(params, s, act)
+    masks = [(z > 0).astype(np.float64) for _, z in cache[:-1]]
+    return _backward(params, cache, masks, _grad_f(s, f), "scale" if propagate else "direct")
+
+
+def forward_following(params, s: np.ndarray, acts, eps_rel: float = 2.0 ** -19):
+    """Forward pass with BF16 activations (as act="bf16") that checks another
+    implementation's hidden activations acts[l] ((B, L, L, C), layer l =
+    0 .. D - 2, after the ReLU) element by element, and adopts the other value
+    where -- and only where -- this FP64 run's own pre-activation z lies within
+    eps_rel * S of a decision boundary of the activation (a BF16 rounding
+    midpoint or the ReLU kink), S = sum over the taps of |W| |x| + |b|, the
+    scale of an FP32 accumulation's error: there a sum in another precision may
+    legitimately land on the other side (the counterpart of the heat-bath's
+    near-threshold decisions).  Downstream layers then see the adopted value.
+    Returns (f, cache, masks, n_near, n_bad): masks[l] = 1 where the (adopted)
+    output of layer l is positive; n_near counts adopted values, n_bad values
+    that differ although z is not that close to a boundary."""
+    x = s[:, None, :, :].astype(np.float64)
+    cache, masks = [], []
+    near = bad = 0
     D = len(params)
-    for l in range(D - 1, -1, -1):
-        W, b = params[l]
-        x, z = cache[l]
-        dz = grad_out if l == D - 1 else grad_out * (z > 0)
+    for l, (W, b) in enumerate(params):
         mask = "A" if l == 0 else "B"
-        dW = np.zeros_like(W)
-        dx_in = np.zeros_like(x)
+        z = np.zeros((x.shape[0], W.shape[0]) + x.shape[2:])
+        S = np.zeros_like(z)
         for dy, dx in taps(mask):
             xs = shift(x, dy, dx)
-            dW[:, :, dy + R, dx + R] = np.einsum("boxy,bixy->oi", dz, xs)
-            # x enters z at (y, x) via x[y+dy, x+dx]: scatter back with the opposite shift
-            dx_in += shift(np.einsum("oi,boxy->bixy", W[:, :, dy + R, dx + R], dz), -dy, -dx)
-        db = dz.sum(axis=(0, 2, 3))
-        grads[l] = (dW, db)
-        grad_out = dx_in
-    return float(loss), grads
+            z += np.einsum("oi,bixy->boxy", W[:, :, dy + R, dx + R], xs)
+            S += np.einsum("oi,bixy->boxy", np.abs(W[:, :, dy + R, dx + R]), np.abs(xs))
+        z += b[None, :, None, None]
+        S += np.abs(b)[None, :, None, None]
+        cache.append((x, z))
+        if l == D - 1:
+            x = z
+            break
+        own = round_bf16(np.maximum(z, 0.0))
+        lo = round_bf16(np.maximum(z - eps_rel * S, 0.0))
+        hi = round_bf16(np.maximum(z + eps_rel * S, 0.0))
+        other = np.transpose(np.asarray(acts[l], dtype=np.float64), (0, 3, 1, 2))
+        differ = other != own
+        within = (other >= lo) & (other <= hi)
+        near += int((differ & within).sum())
+        bad += int((differ & ~within).sum())
+        x = np.where(differ & within, other, own)
+        masks.append((x > 0).astype(np.float64))
+    return x[:, 0], cache, masks, near, bad
+
+
+def loss_and_grad_following(params, s: np.ndarray, acts, eps_rel: float = 2.0 ** -19):
+    """loss_and_grad(act="bf16") on the forward pass of forward_following:
+    returns (loss, grads, scale, direct, n_near, n_bad) with the two
+    magnitude scales of grad_scale (propagated and direct) on the same pass."""
+    B = len(s)
+    f, cache, masks, near, bad = forward_following(params, s, acts, eps_rel)
+    loss = -log_sigmoid(s * f).reshape(B, -1).sum(axis=1).mean()
+    g = _grad_f(s, f)
+    return (float(loss), _backward(params, cache, masks, g), _backward(params, cache, masks, g, "scale"),
+            _backward(params, cache, masks, g, "direct"), near, bad)
+
+
+def hidden_activations(params, s: np.ndarray):
+    """The BF16 hidden activations of act="bf16" as (B, L, L, C) per layer
+    0 .. D - 2 (the layout forward_following takes)."""
+    _, cache = forward(params, s, "bf16")
+    return [np.transpose(x, (0, 2, 3, 1)) for x, _ in cache[1:]]
 
 
 def sample(params, n: int, L: int, uniforms: np.ndarray, act: str = "fp64") -> np.ndarray:
@@ -185,36 +285,6 @@ def conditionals(params, s: np.ndarray, act: str = "fp64") -> np.ndarray:
     position k, given that it had drawn s_<k."""
     f, _ = forward(params, np.asarray(s, dtype=np.float64), act)
     return 1.0 / (1.0 + np.exp(-f))
-
-
-def grad_scale(params, s: np.ndarray, act: str = "fp64"):
-    """Per parameter, the sum of the absolute values of the terms that make
-    up its gradient through the whole backward pass: the backward of
-    loss_and_grad with |dloss/df| at the output, |W| in the products and the
-    ReLU masks kept.  If every term an implementation sums carries a relative
-    error of at most e, its gradient element errs by at most about e times
-    this scale, whatever cancellation happens inside the sum (triangle
-    inequality).  Same structure as grads of loss_and_grad."""
-    B = len(s)
-    f, cache = forward(params, s, act)
-    g = np.exp(-np.logaddexp(0.0, s * f)) / B  # |s sigmoid(-s f)| / B without overflow
-    grad_out = g[:, None, :, :]
-    out = [None] * len(params)
-    D = len(params)
-    for l in range(D - 1, -1, -1):
-        W, b = params[l]
-        x, z = cache[l]
-        dz = grad_out if l == D - 1 else grad_out * (z > 0)
-        mask = "A" if l == 0 else "B"
-        sW = np.zeros_like(W)
-        sx = np.zeros_like(x)
-        for dy, dx in taps(mask):
-            xs = np.abs(shift(x, dy, dx))
-            sW[:, :, dy + R, dx + R] = np.einsum("boxy,bixy->oi", dz, xs)
-            sx += shift(np.einsum("oi,boxy->bixy", np.abs(W[:, :, dy + R, dx + R]), dz), -dy, -dx)
-        out[l] = (sW, dz.sum(axis=(0, 2, 3)))
-        grad_out = sx
-    return out
 
 
 # Random streams of the proposal, keyed by the network's 64-bit seed (key =

@@ -25,7 +25,8 @@ constexpr size_t kMaxSites = (size_t)kMaxBlocks * kThreads;
 // Two doubles (spatial, temporal partial sum) per CTA: 256 KiB per device.
 static __device__ __align__(256) double g_plaquette_scratch[2 * kMaxBlocks];
 
-// Device address of g_plaquette_scratch, looked up once per device.  In host
+// Device address of g_plaquette_scratch, looked up once per device and kept
+// for the life of the process (a device reset would invalidate it).  In host
 // code the symbol itself is only a host-side stand-in and must never be handed
 // to a kernel.
 constexpr int kMaxDevices = 64;

@@ -1781,6 +1781,20 @@ mc_status mc_van_get_params(mc_van *w, float *host_params, size_t n, float *host
     return MC_OK;
 }
 
+mc_status mc_van_get_activations(mc_van *w, int32_t layer, int32_t n, uint16_t *host_dst)
+{
+    if (!w || !host_dst || layer < 0 || layer > w->D - 2 || n < 1 || n > w->nmax)
+        return vfail(MC_EINVAL, "mc_van_get_activations: bad argument (0 <= layer <= depth - 2, 1 <= n <= batch)");
+    const size_t layer_elems = (size_t)w->nmax * w->L * w->L * kCh;
+    cudaError_t e = cudaMemcpyAsync(host_dst, w->H + (size_t)layer * layer_elems, (size_t)n * w->L * w->L * kCh * 2,
+                                    cudaMemcpyDeviceToHost, w->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess)
+        return vfail(MC_ECUDA, std::string("mc_van_get_activations: ") + cudaGetErrorString(e));
+    return MC_OK;
+}
+
 mc_status mc_van_log_prob(mc_van *w, const int8_t *dev_spins, int32_t n, int32_t negate, double *dev_logq)
 {
     if (!w || !dev_spins || !dev_logq || n < 1 || n > w->nmax)

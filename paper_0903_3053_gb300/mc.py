@@ -174,10 +174,25 @@ def su2_plaquette_noalloc(links, L, out, stream=None):
     that cannot let the library allocate: no context, no workspace, nothing
     allocated (see include/mc.h for the size limit and the shared scratch)."""
     torch = _torch()
-    dims = (ctypes.c_int32 * 4)(*[int(v) for v in L])
+    dims = [int(v) for v in L]
+    if len(dims) != 4 or min(dims) < 1:
+        raise ValueError(f"su2_plaquette_noalloc: L must be four positive extents, got {L}")
+    if not (links.is_cuda and links.dtype == torch.float32 and links.is_contiguous()):
+        raise ValueError("su2_plaquette_noalloc: links must be a contiguous float32 CUDA tensor")
+    if links.numel() != 16 * int(np.prod(dims)):
+        raise ValueError(f"su2_plaquette_noalloc: links holds {links.numel()} floats, the lattice {dims} needs "
+                         f"{16 * int(np.prod(dims))}")
+    if not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() >= 3):
+        raise ValueError("su2_plaquette_noalloc: out must be a contiguous float64 CUDA tensor of >= 3 entries")
+    if out.device != links.device:
+        raise ValueError("su2_plaquette_noalloc: links and out must be on the same device")
     st = stream if stream is not None else torch.cuda.current_stream(links.device)
-    _check(load().mc_su2_plaquette_noalloc(ctypes.c_void_p(links.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()),
-                                           ctypes.c_void_p(st.cuda_stream)))
+    if st.device != links.device:
+        raise ValueError("su2_plaquette_noalloc: the stream must belong to the links' device")
+    # the C side launches on, and takes the scratch of, the current device
+    with torch.cuda.device(links.device):
+        _check(load().mc_su2_plaquette_noalloc(ctypes.c_void_p(links.data_ptr()), (ctypes.c_int32 * 4)(*dims),
+                                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
 
 
 class Batch:
@@ -413,6 +428,7 @@ def _van_sigs(L):
         "mc_van_create": (st, [P, c.c_int32, c.c_int32, c.c_int32, c.c_uint64, P, c.c_size_t, P]),
         "mc_van_set_params": (st, [P, P, c.c_size_t]),
         "mc_van_get_params": (st, [P, P, c.c_size_t, P]),
+        "mc_van_get_activations": (st, [P, c.c_int32, c.c_int32, P]),
         "mc_van_log_prob": (st, [P, P, c.c_int32, c.c_int32, P]),
         "mc_van_train_step": (st, [P, P, c.c_int32, c.c_float, c.c_int32, P]),
         "mc_van_sample": (st, [P, c.c_int32, c.c_uint32, P, P, P]),
@@ -490,6 +506,13 @@ class VAN:
         _check(_load_van().mc_van_get_params(self._w, ctypes.c_void_p(p.ctypes.data), p.size,
                                              ctypes.c_void_p(g.ctypes.data) if grads else None))
         return (p, g) if grads else p
+
+    def get_activations(self, layer: int, n: int) -> np.ndarray:
+        """BF16 output of hidden layer `layer` (0 .. depth-2) of the last forward
+        pass for its first n configurations, as float64 [n][L][L][32]."""
+        raw = np.zeros((n, self.L, self.L, 32), dtype=np.uint16)
+        _check(_load_van().mc_van_get_activations(self._w, int(layer), int(n), ctypes.c_void_p(raw.ctypes.data)))
+        return (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
     def log_prob(self, spins, negate: bool = False):
         import torch

@@ -61,6 +61,32 @@ def test_msc_1024_bit_exact(beta):
     b.close()
 
 
+@pytest.mark.parametrize("layout", [mc.MC_LAYOUT_INT8, mc.MC_LAYOUT_MSC32])
+@pytest.mark.parametrize("launch", ["grid", "auto", "group"])
+def test_paper_lattice_1024x512_bit_exact(layout, launch):
+    """The paper's Ising lattice (Sec. 2.3: 1024 x 512, the shape of its only
+    Ising timing), hot start, beta_c: configuration and E/M series after 10
+    sweeps equal the oracle's, through the per-colour launches, the mode the
+    context picks for itself and the persistent group launch (the lattice is
+    too large for the shared-memory resident mode)."""
+    shape = (1024, 512)
+    s = oracle.ising_init(shape, seed=1, chain=0, hot=True)
+    E, M = oracle.ising_run(s, BC, 1, 0, 0, 10)
+    b = mc.Batch([mc.ising(shape, BC, seed=1, chain_id=0)], layout=layout, series_capacity=16)
+    if launch == "group":
+        g = mc.Group([b])
+        g.sweep(10, 1)
+        g.close()
+    else:
+        b.set_mode(mc.MC_MODE_GRID if launch == "grid" else mc.MC_MODE_AUTO)
+        b.sweep(10, 1)
+    rec = b.read_series()
+    np.testing.assert_array_equal(b.get_config(0), s)
+    np.testing.assert_array_equal(rec["E"][0], E)
+    np.testing.assert_array_equal(rec["M"][0], M)
+    b.close()
+
+
 @pytest.mark.parametrize("layout,shape", [
     (mc.MC_LAYOUT_INT8, (2, 2)), (mc.MC_LAYOUT_INT8, (2, 6)), (mc.MC_LAYOUT_INT8, (6, 2)),
     (mc.MC_LAYOUT_INT8, (10, 14)), (mc.MC_LAYOUT_INT8, (130, 66)),

@@ -14,6 +14,13 @@ from conftest import binned_mean_err
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
 EPS = 1e-6
+# A decision FP32 and FP64 take differently needs its acceptance margin within
+# the FP32 error of the test (a few 1e-7) of zero.  With ~1.2 tries per link and
+# a margin density of order one near zero, the expected count is ~1e-7 per
+# decision: ~0.002 per sweep of 8^4 x 4 links.  More than NEAR_MAX in one sweep
+# would mean a systematic error in the FP32 heat-bath, not rounding.
+NEAR_MAX = 3
+NEAR_TALLY = {"near": 0, "decisions": 0}
 
 
 def f32_roundtrip(q):
@@ -50,7 +57,11 @@ def test_one_sweep_per_link(beta, L, hot):
     err = np.abs(g - q).max()
     assert err < TOL, err
     assert b.failed_updates() == fails
-    print(f"near-threshold decisions: {near} of {tries.size}")
+    assert near <= NEAR_MAX, f"{near} near-threshold decisions in one sweep"
+    NEAR_TALLY["near"] += near
+    NEAR_TALLY["decisions"] += tries.size
+    print(f"near-threshold decisions: {near} of {tries.size} links "
+          f"(all cases so far: {NEAR_TALLY['near']} of {NEAR_TALLY['decisions']})")
     b.close()
 
 
@@ -180,10 +191,26 @@ def test_full_size_sampled_links(L):
     b.close()
 
 
+def _golden_plaquette_8x4():
+    """Mean and standard error of <P> at 8^4, beta = 2.3, from the stored
+    40,000-sweep FP64 oracle run (tests/golden/make_su2_plaquette_8x4.py)."""
+    import os
+    vals = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "su2_plaquette_8x4_beta2.3.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals["mean"], vals["err"]
+
+
 @pytest.mark.slow
 def test_plaquette_average_8x4_long_run():
-    """10^4 sweeps of 8^4 at beta = 2.3 on the GPU (FP64 plaquette sums) against
-    an independent, shorter oracle run: averages within 3 combined binned sigma."""
+    """10^4 measured sweeps of 8^4 at beta = 2.3 on the GPU (after 1000
+    thermalisation sweeps, the paper's protocol) against the stored
+    independent 40,000-sweep FP64 oracle run: the averages agree within 3
+    combined statistical sigma (binned errors; bins of 500 sweeps are far
+    longer than the plaquette's autocorrelation), with no added slack."""
     L = (8, 8, 8, 8)
     beta = 2.3
     b = mc.Batch([mc.su2(L, beta, seed=21)], series_capacity=10_000)
@@ -191,16 +218,12 @@ def test_plaquette_average_8x4_long_run():
     b.read_series()
     b.sweep(10_000, 1)
     P = b.read_series()["P"][0]
+    b.close()
     gm, ge = binned_mean_err(P, 20)
-    q = oracle.su2_init(L, 33, 0, True)
-    Po = []
-    for k in range(1300):
-        oracle.su2_sweep(q, L, beta, 33, 0, k)
-        if k >= 300:
-            Po.append(oracle.su2_plaquette(q, L)[0])
-    om, oe = binned_mean_err(Po, 10)
-    assert abs(gm - om) < 3 * np.hypot(ge, oe) + 1e-4, (gm, ge, om, oe)
-    print(f"<P> GPU {gm:.6f} +- {ge:.6f}  oracle {om:.6f} +- {oe:.6f}")
+    om, oe = _golden_plaquette_8x4()
+    print(f"<P> GPU {gm:.6f} +- {ge:.6f}  oracle {om:.6f} +- {oe:.6f}  "
+          f"({(gm - om) / np.hypot(ge, oe):+.2f} sigma)")
+    assert abs(gm - om) < 3 * np.hypot(ge, oe), (gm, ge, om, oe)
 
 
 @pytest.mark.parametrize("n_or", [1, 3])

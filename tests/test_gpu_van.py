@@ -286,3 +286,182 @@ def test_log_prob_extreme_lattice_sides(L):
     loss = net.train_step(torch.from_numpy(s).cuda(), lr=0.0, apply=False)
     assert np.isfinite(loss)
     net.close()
+
+
+# --------------------------------------------------------------------------- element-wise parity
+# Forward activations.  The GPU sums each hidden pre-activation in FP32 (tensor
+# cores: exact BF16 products, FP32 accumulation of 13 taps x 32 channels + bias)
+# and rounds its ReLU output to BF16; the oracle does the same in FP64.  Where
+# the oracle's z lies within ACT_EPS x S of a BF16 rounding midpoint or of the
+# ReLU kink (S = sum of |W| |x| + |b|, the scale of the FP32 sum's error; a
+# typical FP32 sum of 417 terms errs by ~sqrt(417) 2^-24 S = 1.2e-6 S) the two
+# may round differently: the oracle adopts the GPU's activation there and counts
+# it (oracle.van.forward_following); any other difference fails.  Every hidden
+# activation of every layer is checked this way.
+ACT_EPS = 2.0 ** -17
+# Gradients.  With the forward passes aligned, the backward passes differ only
+# by (i) the FP32 logit and sigmoid of dF (relative ~2^-22), (ii) the BF16
+# hi + lo hand-over of the upstream gradient between layers (relative <= 2^-17
+# per hand-over, D - 1 hand-overs) and (iii) FP32 accumulation of <= 417 terms
+# per output (<= 417 x 2^-24 of the sum of |terms| per layer).  Relative to
+# oracle.van.grad_scale (every term in absolute value through the whole pass)
+# that is <= (D - 1)(2^-17 + 417 x 2^-24) + 2^-22 ~ 1.6e-4 < 2^-12: GRAD_TOL.
+# The propagated scale is loose for the early layers (their sums cancel
+# through five layers of weights), so each element is also held to
+# GRAD_TOL_DIRECT of the scale of its own sum (|upstream gradient| x
+# |activation|), at which a wrong sign, a dropped or transposed tap shows in
+# about 90% of the elements of every layer; this second bound is empirical
+# (measured worst case 3.8e-3, an element that is a single term whose upstream
+# gradient itself cancels to 1/600 of its terms; typical 1e-4 or less).
+GRAD_TOL = 2.0 ** -12
+GRAD_TOL_DIRECT = 2.0 ** -7
+# Sampler.  The kernel compares its FP32 uniform with an FP32 sigmoid of a logit
+# accumulated in FP32; the oracle compares the same uniform with the FP64
+# conditional.  A draw may differ only where the two lie within SAMPLE_MARGIN.
+SAMPLE_MARGIN = 1e-3
+# MH.  The log ratio combines four FP64-accumulated log q values (each within
+# 1e-4 relative of the oracle's, log q ~ -10 at L = 4) and an exact energy
+# difference; a decision may differ only within MH_MARGIN of log u.
+MH_MARGIN = 1e-2
+
+
+def _grad_check(L, n, seed, depth=6):
+    p = bf16_params(depth=depth, seed=seed, bias=0.2)
+    net = mc.VAN(L, batch=n, depth=depth, seed=0)
+    net.set_params(mc.mc.van_pack(p))
+    rng = np.random.default_rng(seed + 1)
+    s = np.where(rng.random((n, L, L)) < 0.5, 1, -1).astype(np.int8)
+    loss_g = net.train_step(torch.from_numpy(s).cuda(), lr=0.0, apply=False)
+    _, gflat = net.get_params(grads=True)
+    acts = [net.get_activations(l, n) for l in range(depth - 1)]
+    net.close()
+    gg = mc.mc.van_unpack(gflat, depth=depth)
+    loss_o, go, sp, sd, near, bad = van.loss_and_grad_following(p, s.astype(np.float64), acts, ACT_EPS)
+    nact = sum(a.size for a in acts)
+    assert bad == 0, f"{bad} activations differ away from any rounding boundary"
+    assert near <= max(8, nact // 10000), (near, nact)
+    assert abs(loss_g - loss_o) / abs(loss_o) < 1e-6
+    worst, worst_d = 0.0, 0.0
+    for l, ((gW, gb), (oW, ob), (sW, sb), (dW, db)) in enumerate(zip(gg, go, sp, sd)):
+        for a, o, m, d, name in ((gW, oW, sW, dW, "W"), (gb, ob, sb, db, "b")):
+            err = np.abs(a - o)
+            live = m > 0
+            # taps outside the masks, and parameters no term reaches: exactly zero on both sides
+            assert np.all(a[~live] == 0.0) and np.all(o[~live] == 0.0), (l, name)
+            r = err[live] / m[live]
+            rd = err[live] / np.maximum(d[live], 1e-300)
+            worst, worst_d = max(worst, float(r.max())), max(worst_d, float(rd.max()))
+            i = np.argmax(r)
+            assert r.max() <= GRAD_TOL, (l, name, np.argwhere(live)[i], a[live][i], o[live][i], m[live][i])
+            i = np.argmax(rd)
+            assert rd.max() <= GRAD_TOL_DIRECT, (l, name, np.argwhere(live)[i], a[live][i], o[live][i], d[live][i])
+    print(f"L={L} n={n} seed={seed}: {near} of {nact} activations adopted near a boundary; max |g_gpu - g_oracle| "
+          f"= {worst:.2g} of the propagated scale, {worst_d:.2g} of the direct scale")
+
+
+@pytest.mark.parametrize("L,n,seed", [(8, 16, 4), (8, 16, 14), (6, 40, 24), (12, 3, 44), (14, 3, 44),
+                                      (16, 16, 4), (16, 16, 44)])
+def test_forward_activations_and_gradients_per_element(L, n, seed):
+    """Every hidden activation of a training step's forward pass, and every
+    weight and bias gradient of every layer, element by element against the
+    BF16-activation oracle (which follows the GPU's activation only within
+    ACT_EPS of a rounding boundary, counted)."""
+    _grad_check(L, n, seed)
+
+
+def test_full_size_L64_forward_and_gradients_per_element():
+    """The same at the benchmark's lattice, L = 64 (a batch of 8)."""
+    _grad_check(64, 8, 34)
+
+
+def _sampler_uniforms(seed, rnd, n, L):
+    return van.sampler_uniforms(seed, rnd, range(n), L)
+
+
+@pytest.mark.parametrize("L,n,depth", [(4, 64, 4), (6, 64, 6), (8, 32, 6)])
+def test_sampler_draws_equal_oracle_on_the_kernel_stream(L, n, depth):
+    """The oracle's sequential sampler fed the sampler's own Philox uniforms
+    (the oracle's Philox in the same counter layout) draws the GPU's samples:
+    sample by sample, equal up to the first position whose decision lies
+    within SAMPLE_MARGIN of its threshold (counted; none expected)."""
+    seed, rnd = 77, 5
+    p = bf16_params(depth=depth, seed=40 + L, scale=1.3, bias=0.4)
+    net = mc.VAN(L, batch=n, depth=depth, seed=seed)
+    net.set_params(mc.mc.van_pack(p))
+    g, _ = net.sample(n, round=rnd)
+    net.close()
+    g = g.cpu().numpy().astype(np.float64)
+    u = _sampler_uniforms(seed, rnd, n, L)
+    o = van.sample(p, n, L, u, act="bf16")
+    pk = van.conditionals(p, o, act="bf16").reshape(n, -1)
+    near = 0
+    for b in range(n):
+        diff = np.flatnonzero(g[b].ravel() != o[b].ravel())
+        if len(diff):
+            k = diff[0]
+            assert abs(u[b, k] - pk[b, k]) < SAMPLE_MARGIN, (b, k, u[b, k], pk[b, k])
+            near += 1
+    print(f"L={L}: {near} of {n} samples diverge at a near-threshold draw")
+    assert near <= max(1, n // 32)
+    assert 0.1 < (g > 0).mean() < 0.9  # a non-trivial network
+
+
+def test_full_size_L64_sampler_draws_per_position():
+    """At L = 64 with 4096 proposals, every position of a sample of the GPU's
+    draws is the oracle's decision u_k < p(s_k = +1 | s_<k) on the GPU's own
+    prefix (the conditionals from one BF16-activation oracle forward pass),
+    except within SAMPLE_MARGIN of the threshold (counted)."""
+    L, n, seed, rnd = 64, 4096, 91, 2
+    p = bf16_params(seed=7, bias=0.2)
+    net = mc.VAN(L, batch=n, depth=6, seed=seed)
+    net.set_params(mc.mc.van_pack(p))
+    g, _ = net.sample(n, round=rnd)
+    net.close()
+    pick = [0, 1, 2047, 4095]
+    gs = g[pick].cpu().numpy().astype(np.float64)
+    u = van.sampler_uniforms(seed, rnd, pick, L)
+    pk = van.conditionals(p, gs, act="bf16").reshape(len(pick), -1)
+    want = np.where(u < pk, 1.0, -1.0)
+    mism = want != gs.reshape(len(pick), -1)
+    assert np.all(np.abs(u - pk)[mism] < SAMPLE_MARGIN), np.abs(u - pk)[mism]
+    print(f"L=64: {int(mism.sum())} of {mism.size} draws at a near-threshold decision")
+    assert mism.sum() <= 4
+
+
+def test_mh_decisions_equal_oracle_per_chain():
+    """One MH round on 4096 chains of a 4x4 torus (beta = 0.2, where an
+    untrained network is accepted about half the time) with a poor network: the
+    proposal (the sampler's draw for this round, possibly globally flipped by
+    the chain's MH stream), the accept uniform and the decision of every chain
+    against the oracle's log ratio (BF16-activation network, exact energies).
+    Decisions may differ only within MH_MARGIN of log u (counted)."""
+    beta, L, n, seed, rnd = 0.2, 4, 4096, 61, 9
+    chains = [mc.ising(L, beta, seed=3, chain_id=k) for k in range(n)]
+    b = mc.Batch(chains, layout=mc.MC_LAYOUT_INT8)
+    b.sweep(5)
+    p = bf16_params(depth=4, seed=13, scale=0.5, bias=0.2)
+    net = mc.VAN(L, batch=n, depth=4, seed=seed)
+    net.set_params(mc.mc.van_pack(p))
+    cur = mc.mc.ising_gather(b).cpu().numpy().astype(np.float64)
+    raw, _ = net.sample(n, round=rnd)
+    raw = raw.cpu().numpy().astype(np.float64)
+    net.set_round(rnd)
+    acc = net.mh_round(b)
+    new = mc.mc.ising_gather(b).cpu().numpy().astype(np.float64)
+    net.close()
+    b.close()
+    u, flip = van.mh_draws(seed, rnd, range(n))
+    prop = np.where(flip[:, None, None], -raw, raw)
+    lr = van.mh_accept_logratio(p, beta, cur, prop, act="bf16")
+    want = np.log(u) < lr
+    got_accept = np.all(new == prop, axis=(1, 2))
+    got_stay = np.all(new == cur, axis=(1, 2))
+    assert np.all(got_accept | got_stay)  # each chain holds either its proposal or its old state
+    ambiguous = got_accept & got_stay       # proposal equal to the current state
+    got = np.where(ambiguous, want, got_accept)
+    mism = got != want
+    assert np.all(np.abs(np.log(u) - lr)[mism] < MH_MARGIN), np.abs(np.log(u) - lr)[mism]
+    print(f"MH: {int(want.sum())} of {n} accepted; {int(mism.sum())} decisions at the threshold")
+    assert mism.sum() <= 2
+    assert abs(acc - int(got_accept.sum() - (ambiguous & ~want).sum())) <= int(mism.sum())
+    assert 0.05 * n < want.sum() < 0.95 * n  # both outcomes well represented

@@ -220,10 +220,53 @@ def test_grad_scale_bounds_every_gradient_element():
         assert np.all(np.abs(gW) <= sW * (1 + 1e-12) + 1e-300)
         assert np.all(np.abs(gb) <= sb * (1 + 1e-12) + 1e-300)
         assert (sW > 2 * np.abs(gW)).any()  # with mixed signs some sums do cancel
+    # the direct scale (own sum only) lies between |gradient| and the propagated one
+    for (gW, gb), (sW, sb), (dW, db) in zip(van.loss_and_grad(p, s)[1], van.grad_scale(p, s),
+                                            van.grad_scale(p, s, propagate=False)):
+        assert np.all(np.abs(gW) <= dW * (1 + 1e-12) + 1e-300) and np.all(dW <= sW * (1 + 1e-12) + 1e-300)
+        assert np.all(np.abs(gb) <= db * (1 + 1e-12) + 1e-300) and np.all(db <= sb * (1 + 1e-12) + 1e-300)
     pos = [(np.abs(W), b) for W, b in p]
     ones = np.ones((3, 6, 6))
     _, g = van.loss_and_grad(pos, ones)
     sc = van.grad_scale(pos, ones)
-    for (gW, gb), (sW, sb) in zip(g, sc):
+    for (gW, gb), (sW, sb), (dW, db) in zip(g, sc, van.grad_scale(pos, ones, propagate=False)):
         np.testing.assert_allclose(np.abs(gW), sW, rtol=1e-12, atol=1e-300)
         np.testing.assert_allclose(np.abs(gb), sb, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(np.abs(gW), dW, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(np.abs(gb), db, rtol=1e-12, atol=1e-300)
+
+
+def test_forward_following_checks_and_adopts_activations():
+    """forward_following / loss_and_grad_following: fed the oracle's own BF16
+    activations it reproduces loss_and_grad(act="bf16") exactly with nothing
+    near or bad; an activation moved by one BF16 step is 'bad' when no window
+    is allowed and 'near' (adopted, and used downstream) when the window
+    covers it; an activation the ReLU kept, set to zero, likewise -- and then
+    its ReLU derivative is zero in the backward."""
+    rng = np.random.default_rng(6)
+    p = van.masked(van.init_params(depth=4, channels=5, seed=3))
+    s = np.where(rng.random((3, 6, 6)) < 0.5, 1.0, -1.0)
+    acts = van.hidden_activations(p, s)
+    loss0, g0 = van.loss_and_grad(p, s, act="bf16")
+    loss, g, sc, dr, near, bad = van.loss_and_grad_following(p, s, acts, eps_rel=0.0)
+    assert (near, bad) == (0, 0) and loss == loss0
+    for (a, b), (c, d) in zip(g, g0):
+        np.testing.assert_array_equal(a, c)
+        np.testing.assert_array_equal(b, d)
+    # one activation of the last hidden layer (so that no later activation is
+    # rechecked against values computed from the old one), positive, moved up
+    # by one BF16 step
+    l = len(p) - 2
+    pos = tuple(np.argwhere(acts[l] > 0.25)[0])
+    v = acts[l][pos]
+    step = 2.0 ** (np.floor(np.log2(v)) - 7)
+    for new in (v + step, 0.0):
+        other = [a.copy() for a in acts]
+        other[l][pos] = new
+        assert van.forward_following(p, s, other, eps_rel=0.0)[3:] == (0, 1)
+        f, cache, masks, near, bad = van.forward_following(p, s, other, eps_rel=1.0)
+        assert (near, bad) == (1, 0)
+        b_, y_, x_, c_ = pos
+        assert cache[l + 1][0][b_, c_, y_, x_] == new  # the next layer reads the adopted value
+        assert masks[l][b_, c_, y_, x_] == (1.0 if new > 0 else 0.0)
+        assert van.loss_and_grad_following(p, s, other, eps_rel=1.0)[0] != loss0

@@ -41,10 +41,10 @@ SU2_L = 32
 # consumes one 32-bit Philox4x32-10 word, a quarter of a block of 10 rounds x 2
 # (32 x 32 -> 64)-bit products = 10 32-bit multiplies (high and low halves).
 MUL32_PER_FLIP = 10.0
-# 32-bit integer multiply rate of a GB300: 152 SMs x 64 per clock at the
-# 2070 MHz maximum SM clock (a pure-Philox probe measured 103% of this).
-SM_COUNT, MUL32_PER_SM_CLK, SM_MAX_MHZ = 152, 64, 2070.0
-MUL32_PEAK = SM_COUNT * MUL32_PER_SM_CLK * SM_MAX_MHZ * 1e6
+MUL32_PER_BLOCK = 40.0
+# Nominal 32-bit integer multiplies per SM and clock on compute capability
+# 10.x, for the derived figure reported beside the measured peak.
+MUL32_PER_SM_CLK = 64
 # Algorithmic bytes per SU(2) link update: read + write of the link once per sweep.
 SU2_BYTES_PER_UPDATE = 32.0
 # Algorithmic instructions per SU(2) link update (one issue slot per thread
@@ -53,13 +53,44 @@ SU2_BYTES_PER_UPDATE = 32.0
 # direction on S^2 18; X V, reprojection and store 26; 19 link loads; Philox
 # 2.2 blocks x (20 wide multiplies + 20 xors) = 88  ->  ~400.
 SU2_INSTR_PER_UPDATE = 400.0
-# Issue rate of a GB300: 152 SMs x 4 schedulers x 32 lanes per clock at 2070 MHz.
-ISSUE_PEAK = SM_COUNT * 128 * SM_MAX_MHZ * 1e6
-# DRAM bytes (read + write) per MSC half-sweep launch of this workload, from one
-# ncu capture of the current kernel (profiles/k_half_sweep_msc32_ising_batch.md):
-# 179 MB read (both colour planes once) + 50.9 MB written (changed words only).
-# Set to None whenever the kernel changes until it is captured again.
-MSC_TRAFFIC_PER_LAUNCH = 229.9e6
+# Thread instructions issued per SM and clock: 4 schedulers x 32 lanes.
+ISSUE_PER_SM_CLK = 128
+# DRAM bytes (read + write) per MSC half-sweep launch of this workload from one
+# ncu capture (179.0 MB read: both colour planes once; 47.3 MB written: the
+# changed words), valid only for the kernel sources it was captured from:
+# reported when the SHA-256 of those files still matches, else null.
+MSC_TRAFFIC = {"bytes_per_launch": 226.35e6, "captured": "2026-12-03 (GB300, 4 launches averaged)",
+               "sources_sha256": "94e13685b81653e783db06eb1fb6d77ca7f1ee1bc8b55b5bbb5d3f5f3abd0adc"}
+MSC_KERNEL_SOURCES = ["ising.cu", "ising_dev.cuh", "philox.cuh", "mc_internal.cuh", "fastdiv.cuh"]
+
+
+def kernel_sources_sha256(names) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_0903_3053_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measure_philox_peak(mc, torch, sms: int, reps: int = 5) -> dict:
+    """Multiply ceiling measured in this run: the library's pure-Philox kernel
+    (8 CTAs of 256 threads per SM, 2048 blocks per thread, nothing else),
+    timed with CUDA events on the current stream; the best of `reps`."""
+    blocks, threads, iters = sms * 8, 256, 2048
+    out = torch.empty(blocks * threads, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    mc.philox_rate(blocks, threads, iters, 1, out)
+    torch.cuda.synchronize()
+    best = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        e0.record(stream)
+        mc.philox_rate(blocks, threads, iters, 1, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, MUL32_PER_BLOCK * blocks * threads * iters / (e0.elapsed_time(e1) / 1e3))
+    return {"mul32_per_s": best, "blocks": blocks, "threads": threads, "blocks_per_thread": iters}
 
 
 def log(*a):
@@ -173,6 +204,8 @@ def run_gb300(args):
     batch.set_mode(mc.MC_MODE_GRID, args.threads)
     batch.sweep(W, 1)
     batch.read_series()
+    sms = dev_props.multi_processor_count
+    peak = measure_philox_peak(mc.mc, torch, sms)
     batch.profile(True)
     batch.profile_read()
     clocks = ClockSampler(local)
@@ -200,6 +233,10 @@ def run_gb300(args):
     half_ms = kernel_ms / max(launches, 1)
     mul_per_launch = MUL32_PER_FLIP * flips_per_step() / 2
     achieved = mul_per_launch / (half_ms / 1e3)
+    clk = clock_info.get("sm_mhz") or clock_info.get("sm_max_mhz")
+    derived_peak = sms * MUL32_PER_SM_CLK * clk * 1e6 if clk else None
+    sha = kernel_sources_sha256(MSC_KERNEL_SOURCES)
+    traffic_ok = MSC_TRAFFIC["sources_sha256"] == sha
     batch.close()
     del batch
     torch.cuda.empty_cache()
@@ -209,7 +246,7 @@ def run_gb300(args):
 
     # ---- SU(2) and batched-chain components -------------------------------------------
     small = run_ising_64(mc, torch, rank, world)
-    su2 = run_su2(mc, torch, rank, args.su2_steps, world)
+    su2 = run_su2(mc, torch, rank, args.su2_steps, world, sms * ISSUE_PER_SM_CLK * (clk or 2070.0) * 1e6)
     batched = run_batched(mc, torch, rank, args.batch_steps, world)
     ess_cmp = run_ess(args) if not args.no_ess else None
     paper = run_paper_protocol(mc, torch) if not args.no_paper else None
@@ -239,16 +276,25 @@ def run_gb300(args):
         "roofline": {
             "bound": "alu",
             "achieved": achieved,
-            "peak": MUL32_PEAK,
+            "peak": peak["mul32_per_s"],
             "unit": "int32-mul/s",
-            "frac": achieved / MUL32_PEAK,
-            "traffic": MSC_TRAFFIC_PER_LAUNCH,
+            "frac": achieved / peak["mul32_per_s"],
+            "traffic": MSC_TRAFFIC["bytes_per_launch"] if traffic_ok else None,
+            "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, captured "
+                               f"{MSC_TRAFFIC['captured']} from kernel sources sha256 {sha[:16]} (unchanged)")
+                              if traffic_ok else f"null: the kernel sources (sha256 {sha[:16]}) differ from the "
+                                                 "ones the stored ncu figure was captured from",
             "kernel": "k_half_sweep<C, MSC32> (Ising half-sweep)",
             "kernel_ms_per_launch": half_ms,
             "kernel_share_of_step": kernel_ms / ms if ms > 0 else None,
             "algorithmic": "10 int32 multiplies per attempted flip (1/4 Philox4x32-10 block)",
-            "peak_source": "derived: 152 SMs x 64 int32 multiplies/clk x 2070 MHz (the measured peaks have no "
-                           "integer figure); a pure-Philox probe reached 103% of it",
+            "peak_source": "measured in this run: the library's pure-Philox kernel (mc_philox_rate), "
+                           f"{peak['blocks']} CTAs x {peak['threads']} threads x {peak['blocks_per_thread']} blocks, "
+                           "40 int32 multiplies per block, best of 5 (the measured peaks file has no integer figure)",
+            "sm_count": sms,
+            "derived_peak": derived_peak,
+            "derived_peak_source": f"{sms} SMs (queried) x {MUL32_PER_SM_CLK} int32 multiplies/clk x {clk} MHz "
+                                   "(median SM clock sampled during the timed region)",
         },
         "e2e": e2e,
         "gpu_launches": launches + K,  # 2 half-sweeps + 1 state-advance kernel per step
@@ -370,7 +416,7 @@ def run_ising_64(mc, torch, rank, world, sweeps=1000) -> dict:
             "unit": "spin-flips/s", "bound": "latency (one CTA, 4096 sites)"}
 
 
-def run_su2(mc, torch, rank, K, world):
+def run_su2(mc, torch, rank, K, world, issue_peak):
     """SU(2) heat-bath on 4 x 32^4 with the plaquette measured every sweep.
     The timed loop replays CUDA graphs (sweep(1, 1) per step, inputs > L2); the
     phase-kernel time comes from a separate profiled pass (CUDA events around
@@ -453,8 +499,9 @@ def run_su2(mc, torch, rank, K, world):
                                     if ms_or > ms / K else None},
             "roofline_hbm": {"achieved": achieved_bw, "peak": hbm, "unit": "B/s", "frac": achieved_bw / hbm,
                              "bytes_per_update": SU2_BYTES_PER_UPDATE},
-            "roofline_alu": {"bound": "alu", "achieved": alu, "peak": ISSUE_PEAK, "unit": "thread-instr/s",
-                             "frac": alu / ISSUE_PEAK, "instr_per_update": SU2_INSTR_PER_UPDATE,
+            "roofline_alu": {"bound": "alu", "achieved": alu, "peak": issue_peak, "unit": "thread-instr/s",
+                             "frac": alu / issue_peak, "instr_per_update": SU2_INSTR_PER_UPDATE,
+                             "peak_source": "SMs (queried) x 4 schedulers x 32 lanes x median sampled SM clock",
                              "note": "the slower bound: phase kernel at its algorithmic issue count"}}
 
 

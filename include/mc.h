@@ -203,6 +203,19 @@ MC_API mc_status mc_profile_enable(mc_ctx *ctx, int32_t enable);
  * the previous read (synchronous; resets the counters). */
 MC_API mc_status mc_profile_read(mc_ctx *ctx, int64_t *launches, double *total_ms);
 
+/* Multiply ceiling of the Ising sweep's roofline.  Every attempted flip uses
+ * one word of a Philox4x32-10 block (Salmon et al., SC'11, the counter-based
+ * generator in place of the paper's RANMAR, Sec. 2.2): 40 32-bit multiplies
+ * (the high and low halves of 20 products) per block.  This launches
+ * blocks x threads threads that each generate `iters` blocks, counter
+ * (thread id, i, TAG_PROBE, 0) under key `seed`, and nothing else; thread id
+ * writes the xor of all its words to dev_out[id] (caller-owned, blocks x
+ * threads uint32).  Async on cuda_stream; the caller times it (40 x blocks x
+ * threads x iters multiplies per launch).  MC_EINVAL unless blocks >= 1 and
+ * threads is a multiple of 32 in [32, 256]. */
+MC_API mc_status mc_philox_rate(int32_t blocks, int32_t threads, uint32_t iters, uint64_t seed, uint32_t *dev_out,
+                                void *cuda_stream);
+
 /* ---- Batched chains in one persistent launch ---------------------------------
  * A group advances every chain of up to 16 contexts (any mix of Ising layouts
  * and SU(2)) with ONE persistent kernel launch per call, replayed from a CUDA

@@ -29,6 +29,7 @@ EXPORTS = [
     "mc_set_sweep", "mc_su2_record_tries", "mc_su2_get_tries", "mc_su2_failed_updates", "mc_su2_set_overrelax",
     "mc_su2_get_overrelax", "mc_su2_polyakov", "mc_destroy",
     "mc_last_error", "mc_version", "mc_profile_enable", "mc_profile_read", "mc_su2_plaquette_noalloc",
+    "mc_philox_rate",
     "mc_group_workspace_bytes", "mc_group_create", "mc_group_configure", "mc_group_sweep", "mc_group_schedule",
     "mc_group_destroy",
 ]
@@ -98,6 +99,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mc_profile_enable": (st, [P, c.c_int32]),
         "mc_profile_read": (st, [P, P, P]),
         "mc_su2_plaquette_noalloc": (st, [P, P, P, P]),
+        "mc_philox_rate": (st, [c.c_int32, c.c_int32, c.c_uint32, c.c_uint64, P, P]),
         "mc_group_workspace_bytes": (c.c_size_t, [c.c_int32, P]),
         "mc_group_create": (st, [P, c.c_int32, P, P, c.c_size_t, P]),
         "mc_group_configure": (st, [P, c.c_int32, c.c_int32, c.c_double]),
@@ -166,6 +168,18 @@ def mc_workspace_bytes(chains, layout=MC_LAYOUT_INT8, series_capacity=1024) -> i
     if n == 0:
         raise MCError(MC_EINVAL, load().mc_last_error().decode())
     return int(n)
+
+
+def philox_rate(blocks: int, threads: int, iters: int, seed: int, out, stream=None):
+    """Launch the Philox multiply-ceiling kernel (see include/mc.h) into the
+    uint32/int32 CUDA tensor `out` (blocks x threads entries), async."""
+    torch = _torch()
+    if not (out.is_cuda and out.dtype in (torch.int32,) and out.is_contiguous() and out.numel() >= blocks * threads):
+        raise ValueError("philox_rate: out must be a contiguous int32 CUDA tensor of blocks x threads entries")
+    st = stream if stream is not None else torch.cuda.current_stream(out.device)
+    with torch.cuda.device(out.device):
+        _check(load().mc_philox_rate(int(blocks), int(threads), int(iters) & 0xFFFFFFFF, int(seed) & (2**64 - 1),
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
 
 
 def su2_plaquette_noalloc(links, L, out, stream=None):

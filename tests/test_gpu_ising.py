@@ -263,3 +263,21 @@ def test_beta_zero_flips_everything_on_gpu():
     b.sweep(1)
     np.testing.assert_array_equal(b.get_config(0), -s0)
     b.close()
+
+
+def test_philox_rate_probe_computes_philox():
+    """The multiply-ceiling probe that bench.py times generates true Philox
+    blocks: each thread's output is the xor of the words of its blocks
+    (counter (thread id, i, 0x7F000000, 0)), recomputed with the oracle's
+    Philox."""
+    import torch
+    blocks, threads, iters, seed = 3, 64, 5, 0x1234_5678_9ABC
+    out = torch.zeros(blocks * threads, dtype=torch.int32, device="cuda")
+    mc.mc.philox_rate(blocks, threads, iters, seed, out)
+    got = out.cpu().numpy().view(np.uint32)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for tid in (0, 1, 63, 64, 191):
+        want = np.uint32(0)
+        for i in range(iters):
+            want ^= np.bitwise_xor.reduce(oracle.philox4x32_10([tid, i, 0x7F000000, 0], key))
+        assert got[tid] == want, tid

@@ -126,11 +126,15 @@ MC_API mc_status mc_su2_init(mc_ctx **out, const int32_t L[4], double beta, uint
 MC_API mc_status mc_sweep(mc_ctx *ctx, int64_t n_sweeps, int32_t measure_every);
 
 /* Execution mode for later sweeps: MC_MODE_GRID (one launch per half-sweep /
- * phase over all chains), MC_MODE_RESIDENT (Ising only: one CTA per chain with
- * its lattice in shared memory, all sweeps of a call in one launch) or
- * MC_MODE_AUTO.  threads_per_block = 0 keeps the default (256 for Ising, 128 for
- * SU(2), at most 256 for SU(2)).  Results are
- * bit-identical in every mode. */
+ * phase over all chains), MC_MODE_RESIDENT (all sweeps of a call in one
+ * launch -- Ising: one CTA per chain with its lattice in shared memory, for
+ * lattices that fit there; SU(2): one thread-block cluster of up to 16 CTAs
+ * per chain, the phases of Sec. 2.4 separated by the hardware cluster barrier,
+ * any lattice size, fastest up to ~4096 links per phase) or MC_MODE_AUTO
+ * (resident for small lattices).  An SU(2) context that records heat-bath
+ * tries (mc_su2_record_tries) always sweeps in grid mode.  threads_per_block
+ * = 0 keeps the default (256 for Ising, 128 for SU(2), at most 256 for SU(2);
+ * grid mode only).  Results are bit-identical in every mode. */
 MC_API mc_status mc_set_mode(mc_ctx *ctx, int32_t mode, int32_t threads_per_block);
 
 /* Wait for the context's stream; report latched device faults. */

@@ -185,19 +185,11 @@ __device__ void run_su2(const GroupMember &m, int chain, int item, int G, int ra
         if (g.every != 0 && ((t + 1) % g.every) == 0) {
             long long ps = 0, pt = 0;
 #if MC_GROUP_PAIR_PLAQ
-            for (uint32_t j = start; j < ch.nh; j += stride) { // one x1 pair of sites per step
-                float fs0, ft0, fs1, ft1;
-                su2_pair_plaquettes<kLdCoherent>(U, ch, j, fs0, ft0, fs1, ft1);
-                ps += plaq_fixed(fs0) + plaq_fixed(fs1);
-                pt += plaq_fixed(ft0) + plaq_fixed(ft1);
-            }
+            for (uint32_t j = start; j < ch.nh; j += stride) // one x1 pair of sites per step
+                su2_pair_plaquettes<kLdCoherent>(U, ch, j, ps, pt);
 #else
-            for (uint32_t s = start; s < 2 * ch.nh; s += stride) {
-                float fs, ft;
-                su2_site_plaquettes<kLdCoherent>(U, ch, s, fs, ft);
-                ps += plaq_fixed(fs);
-                pt += plaq_fixed(ft);
-            }
+            for (uint32_t s = start; s < 2 * ch.nh; s += stride)
+                su2_site_plaquettes<kLdCoherent>(U, ch, s, ps, pt);
 #endif
             block_sum2ll(ps, pt);
             if (threadIdx.x == 0) {

@@ -152,7 +152,8 @@ Plan make_plan(int32_t n, const mc_chain_desc *chains, int32_t layout, int64_t c
         } else {
             const size_t sites = (size_t)d.L[0] * d.L[1] * d.L[2] * d.L[3];
             staging = std::max(staging, sites * 4 * 16);
-            meas_blocks += (sites / 2 + kPlaqThreads - 1) / kPlaqThreads;
+            // >= kSu2ResidentMaxCluster blocks: the resident mode keeps one partial pair per CTA of a chain
+            meas_blocks += std::max<size_t>((sites / 2 + kPlaqThreads - 1) / kPlaqThreads, kSu2ResidentMaxCluster);
         }
     }
     p.partial_count = 2 * meas_blocks;
@@ -221,8 +222,13 @@ void free_ctx(mc_ctx *c)
 
 int resolve_mode(mc_ctx *c)
 {
-    if (c->kind != MC_KIND_ISING)
-        return MC_MODE_GRID;
+    if (c->kind == MC_KIND_SU2) {
+        if (c->record_tries) // the per-link try record is kept by the grid kernels only
+            return MC_MODE_GRID;
+        if (c->mode != MC_MODE_AUTO)
+            return c->mode;
+        return su2_resident_auto(c) ? MC_MODE_RESIDENT : MC_MODE_GRID;
+    }
     if (c->mode != MC_MODE_AUTO)
         return c->mode;
     int smem = 0;
@@ -254,11 +260,18 @@ mc_status upload_tables(mc_ctx *c)
     return MC_OK;
 }
 
+cudaError_t sweep_enqueue(mc_ctx *c, long long n, int every, int mode)
+{
+    if (c->kind == MC_KIND_ISING)
+        return ising_sweep_enqueue(c, n, every, mode);
+    return mode == MC_MODE_RESIDENT ? su2_resident_enqueue(c, n, every) : su2_sweep_enqueue(c, n, every);
+}
+
 // Capture `n` sweeps (+ state advance) into a graph, or replay a cached one.
 mc_status run_chunk(mc_ctx *c, long long n, int every, int mode)
 {
     if (c->profiling) { // direct launches, each sweep kernel bracketed by events
-        cudaError_t ek = c->kind == MC_KIND_ISING ? ising_sweep_enqueue(c, n, every, mode) : su2_sweep_enqueue(c, n, every);
+        cudaError_t ek = sweep_enqueue(c, n, every, mode);
         if (ek == cudaSuccess)
             ek = advance_state_launch(c, n, every > 0 ? n / every : 0);
         if (ek != cudaSuccess)
@@ -276,7 +289,7 @@ mc_status run_chunk(mc_ctx *c, long long n, int every, int mode)
         if (e != cudaSuccess)
             return cuda_fail(e, "begin graph capture");
         c->ls = c->cap_stream;
-        cudaError_t ek = c->kind == MC_KIND_ISING ? ising_sweep_enqueue(c, n, every, mode) : su2_sweep_enqueue(c, n, every);
+        cudaError_t ek = sweep_enqueue(c, n, every, mode);
         const long long recs = every > 0 ? n / every : 0;
         if (ek == cudaSuccess)
             ek = advance_state_launch(c, n, recs);
@@ -499,7 +512,7 @@ mc_status mc_set_mode(mc_ctx *c, int32_t mode, int32_t threads_per_block)
         return fail(MC_EINVAL, "ctx is NULL");
     if (mode < MC_MODE_AUTO || mode > MC_MODE_RESIDENT)
         return fail(MC_EINVAL, "unknown mode");
-    if (mode == MC_MODE_RESIDENT && (c->kind != MC_KIND_ISING || !ising_resident_fits(c, nullptr)))
+    if (mode == MC_MODE_RESIDENT && c->kind == MC_KIND_ISING && !ising_resident_fits(c, nullptr))
         return fail(MC_EINVAL, "resident mode needs Ising chains whose lattices fit in one CTA's shared memory");
     if (threads_per_block != 0) {
         const int maxt = c->kind == MC_KIND_SU2 ? 256 : 1024;
@@ -532,7 +545,7 @@ mc_status mc_sweep(mc_ctx *c, int64_t n_sweeps, int32_t measure_every)
         return fail(MC_EINVAL, "sweep counter would exceed 2^32 (the Philox sweep word)");
     const int mode = resolve_mode(c);
     if (mode == MC_MODE_RESIDENT) {
-        cudaError_t e = ising_prepare_resident(c);
+        cudaError_t e = c->kind == MC_KIND_ISING ? ising_prepare_resident(c) : su2_prepare_resident(c);
         if (e != cudaSuccess)
             return cuda_fail(e, "configure resident kernel");
     }

@@ -86,6 +86,8 @@ constexpr int kLdReadOnly = 0, kLdPlain = 1, kLdCoherent = 2;
 // one x1 pair of sites, so a chain of N sites has ceil(N / (2 kPlaqThreads))
 // partial-sum blocks.
 constexpr int kPlaqThreads = 128;
+// Largest cluster of the SU(2) resident mode (CTAs per chain; 16 is non-portable).
+constexpr int kSu2ResidentMaxCluster = 16;
 template <int LD, typename T>
 __device__ __forceinline__ T lat_load(const T *p)
 {
@@ -170,6 +172,7 @@ struct mc_ctx {
     int threads = mc::kDefaultThreads;
     bool record_tries = false;
     int n_or = 0;                        // SU(2): overrelaxation sweeps after each heat-bath sweep
+    int su2_res_cluster = 0;             // SU(2) resident mode: CTAs per chain (0 = not prepared)
     std::map<std::tuple<long long, int, int, int, bool, int>, cudaGraphExec_t> graphs;
     // kernel timing (mc_profile_enable)
     bool profiling = false;
@@ -195,6 +198,9 @@ cudaError_t su2_polyakov_launch(mc_ctx *c, int chain, DevRecord *out);
 cudaError_t su2_config_io(mc_ctx *c, int chain, void *dev_buf, bool to_lattice);
 size_t su2_config_bytes(const Su2Chain &ch);
 void su2_plan_grid(mc_ctx *c);
+bool su2_resident_auto(const mc_ctx *c);
+cudaError_t su2_prepare_resident(mc_ctx *c);
+cudaError_t su2_resident_enqueue(mc_ctx *c, long long n, int every);
 
 cudaError_t advance_state_launch(mc_ctx *c, long long n, long long recs);
 

@@ -80,13 +80,8 @@ __global__ void __launch_bounds__(kPlaqThreads, 8) k_plaquette(const Su2Chain *c
     const Su2Chain ch = chains[k];
     const uint32_t j = (blk - meas_start[k]) * kPlaqThreads + threadIdx.x;
     long long ps = 0, pt = 0;
-    if (j < ch.nh) {
-        float fs0, ft0, fs1, ft1;
-        su2_pair_plaquettes<kLdReadOnly>(reinterpret_cast<const float4 *>(lattice + ch.link_off), ch, j, fs0, ft0,
-                                         fs1, ft1);
-        ps = plaq_fixed(fs0) + plaq_fixed(fs1);
-        pt = plaq_fixed(ft0) + plaq_fixed(ft1);
-    }
+    if (j < ch.nh)
+        su2_pair_plaquettes<kLdReadOnly>(reinterpret_cast<const float4 *>(lattice + ch.link_off), ch, j, ps, pt);
     ps = warp_sum_ll(ps);
     pt = warp_sum_ll(pt);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

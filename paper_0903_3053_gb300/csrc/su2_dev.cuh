@@ -1,24 +1,42 @@
 // su2_dev.cuh -- per-link device code of the 4D SU(2) heat-bath (Sec. 2.4,
-// Eqs. (2)-(7)), shared by the per-phase kernels of su2.cu and the persistent
-// batch kernel of batch.cu.  Quaternion links (U0, U1, U2, U3) of Eq. (4) in
-// FP32, stored per chain as float4 [parity][mu][site-within-parity].
+// Eqs. (2)-(7)), shared by the per-phase kernels of su2.cu, the persistent
+// batch kernel of batch.cu and the resident kernel of su2_resident.cu.
+// Quaternion links (U0, U1, U2, U3) of Eq. (4) in FP32, stored per chain as
+// float4 [parity][mu][site-within-parity].
+//
+// Every floating-point sum of products on the update path is written with
+// explicit rounding intrinsics (__fmaf_rn, __fmul_rn, __fadd_rn, ...), which
+// the compiler neither contracts nor reorders: how it would otherwise fuse
+// a*b - c*d into an FMA depends on the surrounding code, and the kernels that
+// share these functions must produce bit-identical links.
 #pragma once
 #include "mc_internal.cuh"
 
 namespace mc {
 namespace {
 
-// (a0 + i a.sigma)(b0 + i b.sigma) = (a0 b0 - a.b) + i (a0 b + b0 a - a x b).sigma
+// (a0 + i a.sigma)(b0 + i b.sigma) = (a0 b0 - a.b) + i (a0 b + b0 a - a x b).sigma,
+// each component one product and three fused multiply-adds in a fixed order.
 __device__ __forceinline__ float4 qmul(float4 a, float4 b)
 {
-    return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
-                       a.x * b.y + b.x * a.y - (a.z * b.w - a.w * b.z),
-                       a.x * b.z + b.x * a.z - (a.w * b.y - a.y * b.w),
-                       a.x * b.w + b.x * a.w - (a.y * b.z - a.z * b.y));
+    return make_float4(__fmaf_rn(-a.w, b.w, __fmaf_rn(-a.z, b.z, __fmaf_rn(-a.y, b.y, __fmul_rn(a.x, b.x)))),
+                       __fmaf_rn(a.w, b.z, __fmaf_rn(-a.z, b.w, __fmaf_rn(b.x, a.y, __fmul_rn(a.x, b.y)))),
+                       __fmaf_rn(a.y, b.w, __fmaf_rn(-a.w, b.y, __fmaf_rn(b.x, a.z, __fmul_rn(a.x, b.z)))),
+                       __fmaf_rn(a.z, b.y, __fmaf_rn(-a.y, b.z, __fmaf_rn(b.x, a.w, __fmul_rn(a.x, b.w)))));
 }
 __device__ __forceinline__ float4 qdag(float4 a) { return make_float4(a.x, -a.y, -a.z, -a.w); }
-__device__ __forceinline__ float4 qadd(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
-__device__ __forceinline__ float qdot(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+__device__ __forceinline__ float4 qadd(float4 a, float4 b)
+{
+    return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
+}
+__device__ __forceinline__ float qdot(float4 a, float4 b)
+{
+    return __fmaf_rn(a.w, b.w, __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x))));
+}
+__device__ __forceinline__ float4 qscale(float4 a, float s)
+{
+    return make_float4(__fmul_rn(a.x, s), __fmul_rn(a.y, s), __fmul_rn(a.z, s), __fmul_rn(a.w, s));
+}
 
 struct Site {
     int x[4];
@@ -132,6 +150,30 @@ constexpr int kKpTries = 8;
 constexpr int kCreutzTries = 64;
 constexpr uint8_t kFailed = 255;
 
+// The part of a Kennedy-Pendleton try that does not depend on alpha:
+// q = -(log u1 + cos^2(2 pi u2) log u3), so that lambda^2 = q / (2 alpha), and
+// u4^2 for the acceptance test.
+struct KpFirstTry {
+    float q, u4sq;
+};
+
+__device__ __forceinline__ KpFirstTry kp_parts(uint4 r)
+{
+    const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
+    const float u3 = uniform_open0(r.z), u4 = uniform_open0(r.w);
+    const float cs = cospif(2.0f * u2);
+    return KpFirstTry{-__fmaf_rn(__fmul_rn(cs, cs), logf(u3), logf(u1)), __fmul_rn(u4, u4)};
+}
+
+// Acceptance of a Kennedy-Pendleton try at alpha > 0: lambda^2 = q / (2 alpha),
+// accepted iff u4^2 <= 1 - lambda^2; a0 = 1 - 2 lambda^2 either way.
+__device__ __forceinline__ bool kp_accept(const KpFirstTry &f, float alpha, float &a0)
+{
+    const float lam2 = __fmul_rn(f.q, 0.5f / alpha);
+    a0 = __fmaf_rn(-2.0f, lam2, 1.0f);
+    return f.u4sq <= __fsub_rn(1.0f, lam2);
+}
+
 // One heat-bath try t for a0 ~ sqrt(1-a0^2) exp(alpha a0): Kennedy-Pendleton
 // for t < kKpTries (alpha > 0), Creutz after; a0 is set whether or not the try
 // is accepted.
@@ -139,38 +181,24 @@ __device__ __forceinline__ bool heatbath_try(int t, float alpha, uint32_t e, uin
                                              const Su2Chain &ch, const PhiloxSchedule &ks, float &a0)
 {
     const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel | (uint32_t)t, ch.chain_id), ks);
-    if (t < kKpTries) {
-        const float inv2a = 0.5f / alpha;
-        const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
-        const float u3 = uniform_open0(r.z), u4 = uniform_open0(r.w);
-        const float cs = cospif(2.0f * u2);
-        const float lam2 = -(logf(u1) + cs * cs * logf(u3)) * inv2a;
-        a0 = 1.0f - 2.0f * lam2;
-        return u4 * u4 <= 1.0f - lam2;
-    }
+    if (t < kKpTries)
+        return kp_accept(kp_parts(r), alpha, a0);
     const float cexp = alpha > 0.f ? -expm1f(-2.0f * alpha) : 0.f; // 1 - e^{-2 alpha}
     const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
-    const float c = alpha > 0.f ? 1.0f + log1pf(-(1.0f - u1) * cexp) / alpha : 2.0f * u1 - 1.0f;
+    const float c = alpha > 0.f ? __fadd_rn(1.0f, log1pf(__fmul_rn(-__fsub_rn(1.0f, u1), cexp)) / alpha)
+                                : __fmaf_rn(2.0f, u1, -1.0f);
     a0 = c;
-    return u2 * u2 <= 1.0f - c * c;
+    return __fmul_rn(u2, u2) <= __fmaf_rn(-c, c, 1.0f);
 }
 
-// The part of Kennedy-Pendleton try 0 that does not depend on alpha:
-// q = -(log u1 + cos^2(2 pi u2) log u3), so that lambda^2 = q / (2 alpha), and
-// u4^2 for the acceptance test.  Computed before the staple, it fills the wait
-// for the staple's loads.
-struct KpFirstTry {
-    float q, u4sq;
-};
-
+// The alpha-free part of Kennedy-Pendleton try t of a link (t = 0 for the
+// first try; `sel` carries parity and direction).  The grid kernel computes
+// try 0's part before the staple, so that it fills the wait for the staple's
+// loads; the resident kernel computes several tries' parts at once.
 __device__ __forceinline__ KpFirstTry kp_first_try(uint32_t e, uint32_t sweep, uint32_t sel, const Su2Chain &ch,
                                                    const PhiloxSchedule &ks)
 {
-    const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel, ch.chain_id), ks);
-    const float u1 = uniform_open0(r.x), u2 = uniform_open0(r.y);
-    const float u3 = uniform_open0(r.z), u4 = uniform_open0(r.w);
-    const float cs = cospif(2.0f * u2);
-    return KpFirstTry{-(logf(u1) + cs * cs * logf(u3)), u4 * u4};
+    return kp_parts(philox4x32_10(make_uint4(e, sweep, kTagSu2Heatbath | sel, ch.chain_id), ks));
 }
 
 // Heat-bath draw of a0: tries 0 .. kKpTries - 1 by Kennedy-Pendleton (skipped
@@ -182,9 +210,9 @@ __device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, 
                                        const PhiloxSchedule &ks, const KpFirstTry &f, float &a0)
 {
     if (alpha > 0.f) {
-        const float lam2 = f.q * (0.5f / alpha);
-        if (f.u4sq <= 1.0f - lam2) {
-            a0 = 1.0f - 2.0f * lam2;
+        float a;
+        if (kp_accept(f, alpha, a)) {
+            a0 = a;
             return 0;
         }
     }
@@ -200,6 +228,16 @@ __device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, 
 
 // Staple of the link U_MU(x) at site e of parity P (Eq. (6)) as V = W / |W| and
 // alpha = beta |W| (V = 1 for a vanishing staple); sc = canonical site index.
+// V = W / |W| and alpha = beta |W| of a staple W (V = 1 for a vanishing staple).
+__device__ __forceinline__ void staple_to_heatbath(const float4 &W, float beta, float4 &V, float &alpha)
+{
+    const float kn = sqrtf(qdot(W, W));
+    V = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (kn > 0.f)
+        V = qscale(W, 1.0f / kn);
+    alpha = __fmul_rn(beta, kn);
+}
+
 template <int P, int MU, int LD>
 __device__ __forceinline__ void su2_link_staple(const float4 *U, const Su2Chain &ch, uint32_t e, float4 &V,
                                                 float &alpha, uint32_t &sc)
@@ -207,13 +245,7 @@ __device__ __forceinline__ void su2_link_staple(const float4 *U, const Su2Chain 
     const Site x = site_from_parity_index(ch, P, e);
     sc = canonical(ch, x);
     const float4 W = staple<MU, P, LD>(U, ch, x, sc, e);
-    const float kn = sqrtf(qdot(W, W));
-    V = make_float4(1.f, 0.f, 0.f, 0.f);
-    if (kn > 0.f) {
-        const float inv = 1.0f / kn;
-        V = make_float4(W.x * inv, W.y * inv, W.z * inv, W.w * inv);
-    }
-    alpha = ch.beta * kn;
+    staple_to_heatbath(W, ch.beta, V, alpha);
 }
 
 // Uniform direction on S^2 for the vector part of X in Eq. (5): cos theta =
@@ -229,10 +261,21 @@ __device__ __forceinline__ S2Direction su2_direction(const Su2Chain &ch, const P
     const uint32_t sel = ((uint32_t)P << 12) | ((uint32_t)MU << 8);
     const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ks);
     S2Direction d;
-    d.ct = 2.0f * uniform_open0(r.x) - 1.0f;
+    d.ct = __fmaf_rn(2.0f, uniform_open0(r.x), -1.0f);
     sincospif(2.0f * uniform_open0(r.y), &d.sphi, &d.cphi);
-    d.st = sqrtf(fmaxf(0.f, 1.0f - d.ct * d.ct));
+    d.st = sqrtf(fmaxf(0.f, __fmaf_rn(-d.ct, d.ct, 1.0f)));
     return d;
+}
+
+// The new link X V of Eq. (5) for the drawn a0 and direction d, X = a0 +
+// i sqrt(1 - a0^2) d.sigma, reprojected onto SU(2) (Eq. (7)).
+__device__ __forceinline__ float4 heatbath_link(float a0, const float4 &V, const S2Direction &d)
+{
+    const float rad = sqrtf(fmaxf(0.f, __fmaf_rn(-a0, a0, 1.0f)));
+    const float rs = __fmul_rn(rad, d.st);
+    const float4 X = make_float4(a0, __fmul_rn(rs, d.cphi), __fmul_rn(rs, d.sphi), __fmul_rn(rad, d.ct));
+    const float4 Un = qmul(X, V);
+    return qscale(Un, rsqrtf(qdot(Un, Un)));
 }
 
 // Heat-bath draw and store for a link whose staple is (V, alpha) and whose
@@ -253,12 +296,7 @@ __device__ __forceinline__ int su2_link_draw(float4 *U, const Su2Chain &ch, cons
             count_heatbath_failure(state);
         return t;
     }
-    const float rad = sqrtf(fmaxf(0.f, 1.0f - a0 * a0));
-    const float4 X = make_float4(a0, rad * d.st * d.cphi, rad * d.st * d.sphi, rad * d.ct);
-    float4 Un = qmul(X, V);
-    const float nrm = rsqrtf(qdot(Un, Un));
-    Un = make_float4(Un.x * nrm, Un.y * nrm, Un.z * nrm, Un.w * nrm);
-    U[(size_t)(P * 4 + MU) * ch.nh + e] = Un;
+    U[(size_t)(P * 4 + MU) * ch.nh + e] = heatbath_link(a0, V, d);
     return t;
 }
 
@@ -315,14 +353,12 @@ __device__ __forceinline__ void su2_overrelax_link(float4 *U, const Su2Chain &ch
         const float k2 = qdot(W, W);
         if (!(k2 > 0.f))
             return;
-        const float inv = 1.0f / sqrtf(k2);
-        V = make_float4(W.x * inv, W.y * inv, W.z * inv, W.w * inv);
+        V = qscale(W, 1.0f / sqrtf(k2));
     }
     float4 *dst = &U[(size_t)(P * 4 + MU) * ch.nh + e];
     const float4 u = lat_load<LD>(dst);
     float4 Un = qmul(qmul(V, qdag(u)), V);
-    const float nrm = rsqrtf(qdot(Un, Un));
-    *dst = make_float4(Un.x * nrm, Un.y * nrm, Un.z * nrm, Un.w * nrm);
+    *dst = qscale(Un, rsqrtf(qdot(Un, Un)));
 }
 
 template <int LD>
@@ -366,11 +402,12 @@ __device__ __forceinline__ void su2_update_link_rt(int phase, float4 *U, const S
     }
 }
 
-// Plaquette sums in exact fixed point: each site's FP32 value v (|v| <= 3) is
-// rounded to a multiple of 2^-29 (an int32) and summed in int64.  The sum is
-// exact, hence independent of the order and of the launch shape, for up to
-// 5.7e9 sites, and it stays off the GB300's FP64 pipe, which made the FP64
-// shuffle reduction the larger part of the measurement's cost.
+// Plaquette sums in exact fixed point: each plaquette's FP32 value h (|h| <= 1)
+// is rounded to a multiple of 2^-29 (an int32) and summed in int64.  The sum is
+// exact, hence independent of the order, of the launch shape and of how the
+// plaquettes are shared out among threads, for up to 2.8e9 sites, and it stays
+// off the GB300's FP64 pipe, which made an FP64 shuffle reduction the larger
+// part of the measurement's cost.
 constexpr float kPlaqFix = 536870912.0f; // 2^29
 constexpr double kPlaqUnfix = 1.0 / 536870912.0;
 __device__ __forceinline__ long long plaq_fixed(float v) { return (long long)__float2int_rn(v * kPlaqFix); }
@@ -383,25 +420,28 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
-// (1/2) Tr U_munu(x) of Eq. (3) for the six planes at a site, from its own
-// links Ux[mu] and the forward links Uf[mu][nu] = U_nu(x + mu); spatial planes
-// summed into fs, temporal (mu = 0) into ft, in a fixed order.
-__device__ __forceinline__ void plaquettes_of(const float4 (&Ux)[4], const float4 (&Uf)[4][4], float &fs, float &ft)
+// (1/2) Tr U_munu(x) of Eq. (3): (1/2) Tr[U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+]
+// = A . B with A = U_mu(x) U_nu(x+mu), B = U_nu(x) U_mu(x+nu).
+__device__ __forceinline__ float plaquette_value(float4 umu_x, float4 unu_xmu, float4 unu_x, float4 umu_xnu)
 {
-    fs = 0.f;
-    ft = 0.f;
+    return qdot(qmul(umu_x, unu_xmu), qmul(unu_x, umu_xnu));
+}
+
+// The six plaquettes at a site, from its own links Ux[mu] and the forward
+// links Uf[mu][nu] = U_nu(x + mu), added in fixed point: spatial planes to ps,
+// temporal (mu = 0) to pt.
+__device__ __forceinline__ void plaquettes_of(const float4 (&Ux)[4], const float4 (&Uf)[4][4], long long &ps,
+                                              long long &pt)
+{
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
         for (int nu = mu + 1; nu < 4; ++nu) {
-            // (1/2) Tr[U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+] = A . B
-            const float4 A = qmul(Ux[mu], Uf[mu][nu]);
-            const float4 B = qmul(Ux[nu], Uf[nu][mu]);
-            const float h = qdot(A, B);
+            const long long h = plaq_fixed(plaquette_value(Ux[mu], Uf[mu][nu], Ux[nu], Uf[nu][mu]));
             if (mu == 0)
-                ft += h;
+                pt += h;
             else
-                fs += h;
+                ps += h;
         }
 }
 
@@ -417,11 +457,11 @@ __device__ __forceinline__ Site site_of_canonical(const Su2Chain &ch, uint32_t s
     return x;
 }
 
-// Spatial and temporal sums of (1/2) Tr U_munu(x) over the six plaquettes with
-// corner at canonical site s; FP32 products.
+// Spatial and temporal fixed-point sums of (1/2) Tr U_munu(x) over the six
+// plaquettes with corner at canonical site s, added to ps and pt; FP32 products.
 template <int LD>
-__device__ __forceinline__ void su2_site_plaquettes(const float4 *U, const Su2Chain &ch, uint32_t s, float &fs,
-                                                    float &ft)
+__device__ __forceinline__ void su2_site_plaquettes(const float4 *U, const Su2Chain &ch, uint32_t s, long long &ps,
+                                                    long long &pt)
 {
     const Site x = site_of_canonical(ch, s);
     const int p = (x.x[0] + x.x[1] + x.x[2] + x.x[3]) & 1, q = 1 - p;
@@ -443,7 +483,7 @@ __device__ __forceinline__ void su2_site_plaquettes(const float4 *U, const Su2Ch
             if (nu != mu)
                 Uf[mu][nu] = load_link<LD>(U, ch.nh, q, nu, ef);
     }
-    plaquettes_of(Ux, Uf, fs, ft);
+    plaquettes_of(Ux, Uf, ps, pt);
 }
 
 // The same sums for the two sites of an x1 pair, canonical 2j and 2j + 1 (L1 is
@@ -452,8 +492,8 @@ __device__ __forceinline__ void su2_site_plaquettes(const float4 *U, const Su2Ch
 // forward links along x1, so the pair takes 29 link loads instead of 32, and
 // one thread carries two independent products chains.
 template <int LD>
-__device__ __forceinline__ void su2_pair_plaquettes(const float4 *U, const Su2Chain &ch, uint32_t j, float &fs0,
-                                                    float &ft0, float &fs1, float &ft1)
+__device__ __forceinline__ void su2_pair_plaquettes(const float4 *U, const Su2Chain &ch, uint32_t j, long long &ps,
+                                                    long long &pt)
 {
     const Site x = site_of_canonical(ch, 2 * j);
     Site y = x;
@@ -483,8 +523,53 @@ __device__ __forceinline__ void su2_pair_plaquettes(const float4 *U, const Su2Ch
         if (nu != 2) F1[2][nu] = load_link<LD>(U, nh, p0, nu, e12);
         if (nu != 3) F1[3][nu] = load_link<LD>(U, nh, p0, nu, e13);
     }
-    plaquettes_of(U0, F0, fs0, ft0);
-    plaquettes_of(U1, F1, fs1, ft1);
+    plaquettes_of(U0, F0, ps, pt);
+    plaquettes_of(U1, F1, ps, pt);
+}
+
+// Canonical index of the neighbour x + e_D of site x (canonical index s).
+template <int D>
+__device__ __forceinline__ uint32_t canonical_fwd(const Su2Chain &ch, const Site &x, uint32_t s)
+{
+    return fwd<D>(ch, strides_of(ch), x.x[D], s);
+}
+
+// One plaquette, plane (MU, NU) at canonical site s, added in fixed point to pt
+// (MU = 0) or ps: the value plaquettes_of computes for that plane.
+template <int MU, int NU, int LD>
+__device__ __forceinline__ void su2_plane_plaquette(const float4 *U, const Su2Chain &ch, const Site &x, uint32_t s,
+                                                    long long &ps, long long &pt)
+{
+    const int p = (x.x[0] + x.x[1] + x.x[2] + x.x[3]) & 1;
+    const uint32_t nh = ch.nh, e = s >> 1;
+    const float4 umu = load_link<LD>(U, nh, p, MU, e);
+    const float4 unu = load_link<LD>(U, nh, p, NU, e);
+    const float4 unu_f = load_link<LD>(U, nh, 1 - p, NU, canonical_fwd<MU>(ch, x, s) >> 1);
+    const float4 umu_f = load_link<LD>(U, nh, 1 - p, MU, canonical_fwd<NU>(ch, x, s) >> 1);
+    const long long h = plaq_fixed(plaquette_value(umu, unu_f, unu, umu_f));
+    if (MU == 0)
+        pt += h;
+    else
+        ps += h;
+}
+
+// Plaquette number u of a chain, u = plane N + s (N = 2 nh sites; planes in
+// the order (0,1), (0,2), (0,3), (1,2), (1,3), (2,3)), so that consecutive
+// threads take consecutive sites of one plane; added in fixed point to ps / pt.
+template <int LD>
+__device__ __forceinline__ void su2_plaquette_unit(const float4 *U, const Su2Chain &ch, uint32_t u, long long &ps,
+                                                   long long &pt)
+{
+    const uint32_t n = 2u * ch.nh, plane = u / n, s = u - plane * n;
+    const Site x = site_of_canonical(ch, s);
+    switch (plane) {
+    case 0: su2_plane_plaquette<0, 1, LD>(U, ch, x, s, ps, pt); break;
+    case 1: su2_plane_plaquette<0, 2, LD>(U, ch, x, s, ps, pt); break;
+    case 2: su2_plane_plaquette<0, 3, LD>(U, ch, x, s, ps, pt); break;
+    case 3: su2_plane_plaquette<1, 2, LD>(U, ch, x, s, ps, pt); break;
+    case 4: su2_plane_plaquette<1, 3, LD>(U, ch, x, s, ps, pt); break;
+    default: su2_plane_plaquette<2, 3, LD>(U, ch, x, s, ps, pt); break;
+    }
 }
 
 }  // namespace

@@ -323,3 +323,56 @@ def test_polyakov_loop_deconfinement_signal():
     low, high = absL(1.5), absL(2.6)
     print(f"|L| confined {low:.3f}, deconfined {high:.3f}")
     assert low < 0.2 and high > 2.5 * low, (low, high)
+
+
+def _run_mode(chains, mode, n, every, n_or=0):
+    cap = max(1, n // every) if every else 4
+    b = mc.Batch(chains, series_capacity=cap)
+    b.set_mode(mode)
+    if n_or:
+        b.set_overrelax(n_or)
+    b.sweep(n, every)
+    series = b.read_series() if every else None
+    cfg = [b.get_config(k) for k in range(len(chains))]
+    fails = b.failed_updates()
+    b.close()
+    return cfg, series, fails
+
+
+@pytest.mark.parametrize("case", ["8x4_4beta", "table1_4x8x3_cold", "mixed_small", "12x4_multipass",
+                                  "overrelax", "low_beta"])
+def test_resident_mode_bit_identical_to_grid(case):
+    """The single-launch SU(2) mode (one thread-block cluster per chain, all
+    phases and sweeps of a call in one launch) gives bit-identical links,
+    plaquette series and failure counts to the per-phase grid launches: the
+    8^4 workload at its four beta, a Table 1 lattice from a cold start, uneven
+    small shapes in one batch, a lattice needing several passes per phase,
+    overrelaxation sweeps, and beta down to 0 (alpha = 0: Creutz only)."""
+    n, every, n_or = 12, 1, 0
+    if case == "8x4_4beta":
+        chains = [mc.su2(8, b, seed=1, chain_id=i, hot=True) for i, b in enumerate([1.5, 2.0, 2.3, 2.6])]
+    elif case == "table1_4x8x3_cold":
+        chains = [mc.su2((4, 8, 8, 8), 2.3, seed=3, chain_id=0, hot=False)]
+        n, every = 15, 5
+    elif case == "mixed_small":
+        chains = [mc.su2(L, 2.2, seed=5, chain_id=i, hot=True)
+                  for i, L in enumerate([(2, 2, 2, 2), (6, 4, 8, 2), (4, 6, 2, 4), (8, 8, 6, 4)])]
+    elif case == "12x4_multipass":
+        chains = [mc.su2(12, 2.4, seed=7, chain_id=0, hot=True), mc.su2((4, 12, 12, 12), 1.9, seed=7, chain_id=1)]
+        n, every = 6, 2
+    elif case == "overrelax":
+        chains = [mc.su2(8, 2.3, seed=9, chain_id=i, hot=True) for i in range(2)]
+        n, every, n_or = 8, 2, 1
+    else:
+        chains = [mc.su2((4, 4, 6, 4), b, seed=11, chain_id=i, hot=True) for i, b in enumerate([0.0, 0.05, 0.3])]
+        n, every = 10, 1
+    ref = _run_mode(chains, mc.MC_MODE_GRID, n, every, n_or)
+    got = _run_mode(chains, mc.MC_MODE_RESIDENT, n, every, n_or)
+    for a, b_ in zip(ref[0], got[0]):
+        np.testing.assert_array_equal(a, b_)
+    for f in ("sweep", "P", "Ps", "Pt"):
+        np.testing.assert_array_equal(ref[1][f], got[1][f])
+    assert ref[2] == got[2]
+    auto = _run_mode(chains, mc.MC_MODE_AUTO, n, every, n_or)
+    for a, b_ in zip(ref[0], auto[0]):
+        np.testing.assert_array_equal(a, b_)

@@ -464,19 +464,23 @@ def run_su2(mc, torch, rank, K, world, issue_peak):
     batch.read_series()
     batch.close()
     # the small lattice of the workload: 8^4 at the same four beta, plaquette every sweep, in 1000-sweep
-    # calls (one CUDA graph); 2048 links per phase and chain, so launch- and latency-bound
-    small = mc.Batch([mc.su2(8, b, seed=1, chain_id=cid(rank, i), hot=True) for i, b in enumerate(SU2_BETAS)],
-                     series_capacity=1024)
-    small.sweep(1000, 1)
-    small.read_series()
-    torch.cuda.synchronize()
-    t0.record(stream)
-    small.sweep(1000, 1)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    ms_small = t0.elapsed_time(t1) / 1000
-    small.read_series()
-    small.close()
+    # calls; 2048 links per phase and chain, so launch- and latency-bound: the resident mode (one
+    # cluster per chain, one launch per call) against the grid mode (10 graph-replayed launches per sweep)
+    ms_small = {}
+    for mode, name in ((mc.MC_MODE_RESIDENT, "resident"), (mc.MC_MODE_GRID, "grid")):
+        small = mc.Batch([mc.su2(8, b, seed=1, chain_id=cid(rank, i), hot=True) for i, b in enumerate(SU2_BETAS)],
+                         series_capacity=1024)
+        small.set_mode(mode)
+        small.sweep(1000, 1)
+        small.read_series()
+        torch.cuda.synchronize()
+        t0.record(stream)
+        small.sweep(1000, 1)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms_small[name] = t0.elapsed_time(t1) / 1000
+        small.read_series()
+        small.close()
     updates = len(chains) * 4 * SU2_L ** 4 * K * world
     phase_ms = kernel_ms / max(launches, 1)
     per_launch_updates = len(chains) * 4 * SU2_L ** 4 * Kp / max(launches, 1)
@@ -491,9 +495,11 @@ def run_su2(mc, torch, rank, K, world, issue_peak):
             "workload": f"4D SU(2) {SU2_L}^4, beta in {SU2_BETAS}, hot start, heat-bath (KP+Creutz), plaquette "
                         "every sweep", "steps": K, "ms_per_sweep": ms / K, "phase_kernel_ms": phase_ms,
             "last_plaquette": P,
-            "lattice_8x4": {"ms_per_sweep": ms_small,
-                            "link_updates_per_s": len(SU2_BETAS) * 4 * 8 ** 4 * world / (ms_small / 1e3),
-                            "bound": "launch and latency: 2048 links per phase and chain"},
+            "lattice_8x4": {"ms_per_sweep": ms_small["resident"], "mode": "resident (the automatic choice)",
+                            "link_updates_per_s": len(SU2_BETAS) * 4 * 8 ** 4 * world / (ms_small["resident"] / 1e3),
+                            "grid_ms_per_sweep": ms_small["grid"],
+                            "bound": "latency: 2048 links per phase and chain; resident: one cluster of 16 CTAs per "
+                                     "chain, 8 cluster barriers per sweep"},
             "with_overrelaxation": {"n_or": 1, "ms_per_compound_sweep": ms_or,
                                     "overrelax_link_updates_per_s": len(chains) * 4 * SU2_L ** 4 / ((ms_or - ms / K) / 1e3)
                                     if ms_or > ms / K else None},
@@ -605,14 +611,17 @@ def run_paper_protocol(mc, torch, ising_sweeps=20000) -> dict:
     for (lt, ls), paper_s in PAPER_TABLE1_S.items():
         L = (lt, ls, ls, ls)
         row = {"lattice": f"{lt}x{ls}^3", "paper_gpu_s": paper_s}
-        # the persistent launch puts one chain on one cluster: only worth it for the smallest lattices
-        for mode in (("grid", "group") if ls <= 16 and lt == 4 else ("grid",)):
+        # the persistent launches (group: one cluster for the chain; resident: the SU(2) resident mode)
+        # pay off only for the smallest lattices
+        modes = ("grid",) + (("group",) if ls <= 16 and lt == 4 else ()) + (("resident",) if ls <= 8 else ())
+        for mode in modes:
             b = mc.Batch([mc.su2(L, 2.3, seed=3, chain_id=0, hot=True)], series_capacity=1100)
-            if mode == "grid":
-                run = lambda n, every: b.sweep(n, every)
-            else:
+            if mode == "group":
                 g = mc.Group([b])
                 run = lambda n, every: g.sweep(n, every)
+            else:
+                b.set_mode(mc.MC_MODE_GRID if mode == "grid" else mc.MC_MODE_RESIDENT)
+                run = lambda n, every: b.sweep(n, every)
             run(5, 5)  # graph capture
             b.read_series()
 
@@ -627,7 +636,7 @@ def run_paper_protocol(mc, torch, ising_sweeps=20000) -> dict:
             b.close()
             row[mode + "_s"] = t
             row[mode + "_mean_P"] = float(P.mean())
-        row["gb300_s"] = min(row.get("grid_s", 1e30), row.get("group_s", 1e30))
+        row["gb300_s"] = min(row.get("grid_s", 1e30), row.get("group_s", 1e30), row.get("resident_s", 1e30))
         row["speedup_vs_paper_gpu"] = paper_s / row["gb300_s"]
         out["su2_table1"].append(row)
     return out
@@ -644,8 +653,14 @@ def run_ess(args) -> dict:
     beta = 0.4406868
     out = {"metric": "eff. independent |M| samples/s at beta_c, L=64", "unit": "samples/s"}
     for L in (64, 32):
-        plain = ess.plain_rate(L, beta, chains=4096, therm=5000, sweeps=args.ess_sweeps, every=4,
-                               layout=mc.MC_LAYOUT_MSC32 if L % 64 == 0 else mc.MC_LAYOUT_INT8)
+        layout = mc.MC_LAYOUT_MSC32 if L % 64 == 0 else mc.MC_LAYOUT_INT8
+        plain = ess.plain_rate(L, beta, chains=4096, therm=5000, sweeps=args.ess_sweeps, every=4, layout=layout)
+        # tau from a run of >= 1000 tau (fewer chains: the series must fit the ring buffer)
+        long = ess.plain_tau_long(L, beta, chains=256, therm=5000, sweeps=args.ess_long_sweeps, every=8,
+                                  layout=layout)
+        plain["tau_long"] = long
+        plain["ess_per_s"] = plain["chain_sweeps_per_s"] / (2.0 * long["tau_absM_sweeps"])
+        plain["ess_tau_source"] = "tau_long"
         learned = ess.learned_rate(L, beta, chains=4096, therm=5000, data_snapshots=48, data_spacing=200,
                                    train_steps=args.ess_train_steps, train_batch=512,
                                    rounds=args.ess_rounds if L == 64 else 2 * args.ess_rounds, local_sweeps=10)
@@ -735,6 +750,7 @@ def main():
     ap.add_argument("--su2-steps", type=int, default=40)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--ess-sweeps", type=int, default=20000)
+    ap.add_argument("--ess-long-sweeps", type=int, default=200000)
     ap.add_argument("--ess-rounds", type=int, default=200)
     ap.add_argument("--ess-train-steps", type=int, default=1500)
     ap.add_argument("--no-ess", action="store_true")

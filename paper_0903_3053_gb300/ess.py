@@ -29,14 +29,36 @@ def autocorrelation(series: np.ndarray) -> np.ndarray:
     return acf / acf[0]
 
 
-def tau_int(series: np.ndarray, c: float = 6.0) -> float:
+def tau_int_window(series: np.ndarray, c: float = 6.0):
+    """(tau, W, closed): Sokal's windowed estimate, its window W and whether
+    the window closed (W >= c tau) before the end of the series."""
     rho = autocorrelation(series)
     tau = 0.5
     for w in range(1, len(rho)):
         tau += rho[w]
         if w >= c * tau:
-            return float(tau)
-    return float(tau)  # window never closed: the series is too short
+            return float(tau), w, True
+    return float(tau), len(rho) - 1, False  # window never closed: the series is too short
+
+
+def tau_int(series: np.ndarray, c: float = 6.0) -> float:
+    return tau_int_window(series, c)[0]
+
+
+def tau_int_with_error(series: np.ndarray, c: float = 6.0, groups: int = 8) -> dict:
+    """tau with two error estimates: Sokal's variance formula
+    var(tau) ~ 2 (2 W + 1) tau^2 / N over the N = chains x length measurements,
+    and the spread of tau over `groups` disjoint groups of chains (standard
+    error of their mean); the series is measured in units of one record."""
+    x = np.atleast_2d(np.asarray(series, dtype=np.float64))
+    tau, w, closed = tau_int_window(x, c)
+    n = x.size
+    err_sokal = tau * np.sqrt(2.0 * (2 * w + 1) / n)
+    g = min(groups, x.shape[0])
+    per = [tau_int(part, c) for part in np.array_split(x, g, axis=0)] if g >= 2 else [tau]
+    err_groups = float(np.std(per, ddof=1) / np.sqrt(len(per))) if len(per) > 1 else float("nan")
+    return {"tau": tau, "err_sokal": float(err_sokal), "err_groups": err_groups, "window": w, "closed": closed,
+            "length_over_tau": x.shape[1] / tau}
 
 
 def _cuda_time(fn):
@@ -49,6 +71,26 @@ def _cuda_time(fn):
     e1.record(s)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1e3
+
+
+def plain_tau_long(L: int, beta: float, chains: int, therm: int, sweeps: int, every: int, seed: int = 1,
+                   layout: int | None = None) -> dict:
+    """tau of |M| (in sweeps, with its errors) from a long run of fewer chains:
+    the full batch of the rate measurement would not fit a 1000-tau series in
+    the ring buffer."""
+    from . import mc
+    layout = mc.MC_LAYOUT_INT8 if layout is None else layout
+    b = mc.Batch([mc.ising(L, beta, seed, chain_id=100000 + k) for k in range(chains)], layout=layout,
+                 series_capacity=sweeps // every + 4)
+    b.sweep(therm)
+    b.read_series()
+    secs = _cuda_time(lambda: b.sweep(sweeps, every))
+    absm = np.abs(b.read_series()["M"].astype(np.float64)) / (L * L)
+    b.close()
+    r = tau_int_with_error(absm)
+    return {"tau_absM_sweeps": r["tau"] * every, "err_sokal": r["err_sokal"] * every,
+            "err_chain_groups": r["err_groups"] * every, "run_over_tau": r["length_over_tau"],
+            "window_closed": r["closed"], "chains": chains, "sweeps": sweeps, "every": every, "seconds": secs}
 
 
 def plain_rate(L: int, beta: float, chains: int, therm: int, sweeps: int, every: int, seed: int = 1,
@@ -64,10 +106,13 @@ def plain_rate(L: int, beta: float, chains: int, therm: int, sweeps: int, every:
     b.read_series()
     secs = _cuda_time(lambda: b.sweep(sweeps, every))
     absm = np.abs(b.read_series()["M"].astype(np.float64)) / (L * L)
-    tau = tau_int(absm) * every
+    r = tau_int_with_error(absm)
+    tau = r["tau"] * every
     b.close()
     rate = chains * sweeps / secs
-    return {"chain_sweeps_per_s": rate, "tau_absM_sweeps": tau, "ess_per_s": rate / (2.0 * tau), "seconds": secs,
+    return {"chain_sweeps_per_s": rate, "tau_absM_sweeps": tau, "tau_err_sokal": r["err_sokal"] * every,
+            "tau_err_chain_groups": r["err_groups"] * every, "run_over_tau": r["length_over_tau"],
+            "ess_per_s": rate / (2.0 * tau), "seconds": secs,
             "chains": chains, "sweeps": sweeps, "mean_absm": float(absm.mean()),
             "layout": "msc32" if layout == mc.MC_LAYOUT_MSC32 else "int8"}
 
@@ -120,13 +165,16 @@ def learned_rate(L: int, beta: float, chains: int, therm: int, data_snapshots: i
 
     secs = _cuda_time(run)
     absm = np.abs(b.read_series()["M"].astype(np.float64)) / (L * L)
-    tau = tau_int(absm)
+    r = tau_int_with_error(absm)
+    tau = r["tau"]
     # the sequential sampler alone: L^2 dependent steps through every layer
     t_sample = _cuda_time(lambda: net.sample(chains, 0x7FFFFFFF))
     net.close()
     b.close()
     rate = chains * rounds / secs
     return {"rounds_per_s": rounds / secs, "chain_rounds_per_s": rate, "tau_absM_rounds": tau,
+            "tau_err_sokal": r["err_sokal"], "tau_err_chain_groups": r["err_groups"],
+            "run_over_tau": r["length_over_tau"],
             "ess_per_s": rate / (2.0 * tau), "acceptance": acc_total / (chains * rounds), "seconds": secs,
             "local_sweeps_per_round": local_sweeps, "chains": chains, "rounds": rounds,
             "train_seconds": t_train, "data_seconds": t_data, "train_configs": int(data.shape[0]),

@@ -34,3 +34,25 @@ def test_small_ess_comparison_runs():
     assert q["loss_last"] < q["loss_first"]
     assert 0.0 < q["acceptance"] <= 1.0 and q["ess_per_s"] > 0
     assert abs(q["mean_absm"] - p["mean_absm"]) < 0.08  # same Boltzmann distribution
+
+
+def test_tau_error_estimates_cover_the_truth():
+    """The Sokal variance formula and the spread over chain groups both give
+    errors that cover the closed-form tau of AR(1) series ~4000 tau long, and
+    agree with each other within a factor of three; a series shorter than its
+    window is flagged.  (On much shorter series the windowed estimator also
+    carries a bias of order W tau / n from the mean subtraction, which neither
+    error estimate includes: one reason to run for >= 1000 tau.)"""
+    rng = np.random.default_rng(11)
+    phi, n, chains = 0.8, 20000, 32
+    want = (1 + phi) / (2 * (1 - phi))
+    x = np.zeros((chains, n))
+    e = rng.normal(size=(chains, n))
+    for t in range(1, n):
+        x[:, t] = phi * x[:, t - 1] + e[:, t]
+    r = ess.tau_int_with_error(x)
+    assert r["closed"] and r["length_over_tau"] > 100
+    assert abs(r["tau"] - want) < 4 * r["err_sokal"] and abs(r["tau"] - want) < 4 * r["err_groups"]
+    assert 1 / 3 < r["err_sokal"] / r["err_groups"] < 3
+    short = ess.tau_int_with_error(x[:, :20])
+    assert not short["closed"]

@@ -169,7 +169,7 @@ __device__ __forceinline__ KpFirstTry kp_parts(uint4 r)
 // accepted iff u4^2 <= 1 - lambda^2; a0 = 1 - 2 lambda^2 either way.
 __device__ __forceinline__ bool kp_accept(const KpFirstTry &f, float alpha, float &a0)
 {
-    const float lam2 = __fmul_rn(f.q, 0.5f / alpha);
+    const float lam2 = __fmul_rn(f.q, __fdividef(0.5f, alpha));
     a0 = __fmaf_rn(-2.0f, lam2, 1.0f);
     return f.u4sq <= __fsub_rn(1.0f, lam2);
 }
@@ -228,13 +228,18 @@ __device__ __forceinline__ int draw_a0(float alpha, uint32_t e, uint32_t sweep, 
 
 // Staple of the link U_MU(x) at site e of parity P (Eq. (6)) as V = W / |W| and
 // alpha = beta |W| (V = 1 for a vanishing staple); sc = canonical site index.
-// V = W / |W| and alpha = beta |W| of a staple W (V = 1 for a vanishing staple).
+// V = W / |W| and alpha = beta |W| of a staple W (V = 1 for a vanishing staple);
+// one reciprocal square root serves both.
 __device__ __forceinline__ void staple_to_heatbath(const float4 &W, float beta, float4 &V, float &alpha)
 {
-    const float kn = sqrtf(qdot(W, W));
+    const float k2 = qdot(W, W);
     V = make_float4(1.f, 0.f, 0.f, 0.f);
-    if (kn > 0.f)
-        V = qscale(W, 1.0f / kn);
+    float kn = 0.f;
+    if (k2 > 0.f) {
+        const float inv = rsqrtf(k2);
+        V = qscale(W, inv);
+        kn = __fmul_rn(k2, inv);
+    }
     alpha = __fmul_rn(beta, kn);
 }
 
@@ -262,8 +267,11 @@ __device__ __forceinline__ S2Direction su2_direction(const Su2Chain &ch, const P
     const uint4 r = philox4x32_10(make_uint4(e, sweep, kTagSu2Direction | sel, ch.chain_id), ks);
     S2Direction d;
     d.ct = __fmaf_rn(2.0f, uniform_open0(r.x), -1.0f);
-    sincospif(2.0f * uniform_open0(r.y), &d.sphi, &d.cphi);
-    d.st = sqrtf(fmaxf(0.f, __fmaf_rn(-d.ct, d.ct, 1.0f)));
+    // phi = 2 pi u2 reduced to (-pi, pi]: u2 - 1 for u2 > 1/2 (exact in FP32)
+    const float u2 = uniform_open0(r.y), v = u2 > 0.5f ? u2 - 1.0f : u2;
+    __sincosf(6.2831853f * v, &d.sphi, &d.cphi);
+    const float s2 = fmaxf(0.f, __fmaf_rn(-d.ct, d.ct, 1.0f));
+    d.st = s2 > 0.f ? __fmul_rn(s2, rsqrtf(s2)) : 0.f;
     return d;
 }
 
@@ -271,7 +279,8 @@ __device__ __forceinline__ S2Direction su2_direction(const Su2Chain &ch, const P
 // i sqrt(1 - a0^2) d.sigma, reprojected onto SU(2) (Eq. (7)).
 __device__ __forceinline__ float4 heatbath_link(float a0, const float4 &V, const S2Direction &d)
 {
-    const float rad = sqrtf(fmaxf(0.f, __fmaf_rn(-a0, a0, 1.0f)));
+    const float r2 = fmaxf(0.f, __fmaf_rn(-a0, a0, 1.0f));
+    const float rad = r2 > 0.f ? __fmul_rn(r2, rsqrtf(r2)) : 0.f;
     const float rs = __fmul_rn(rad, d.st);
     const float4 X = make_float4(a0, __fmul_rn(rs, d.cphi), __fmul_rn(rs, d.sphi), __fmul_rn(rad, d.ct));
     const float4 Un = qmul(X, V);

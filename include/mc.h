@@ -71,7 +71,7 @@ typedef enum {
 enum { MC_COLD = 0, MC_HOT = 1 };              /* initial configuration (Sec. 2.1, 2.4) */
 enum { MC_KIND_ISING = 1, MC_KIND_SU2 = 2 };   /* model */
 enum { MC_LAYOUT_INT8 = 0, MC_LAYOUT_MSC32 = 1 }; /* Ising storage: 1 byte / 1 bit per spin */
-enum { MC_FMT_INT8 = 0, MC_FMT_BITS = 1, MC_FMT_F32 = 2 }; /* canonical config formats */
+enum { MC_FMT_INT8 = 0, MC_FMT_BITS = 1, MC_FMT_F32 = 2, MC_FMT_NATIVE = 3 }; /* config formats */
 enum { MC_MODE_AUTO = 0, MC_MODE_GRID = 1, MC_MODE_RESIDENT = 2 }; /* sweep execution */
 
 /* One Markov chain of a batch. */
@@ -150,11 +150,20 @@ MC_API mc_status mc_measure(mc_ctx *ctx, int32_t chain, mc_record *out);
  * copied records are marked read.  Synchronous. */
 MC_API mc_status mc_read_series(mc_ctx *ctx, mc_record *host_dst, int64_t max_per_chain, int64_t *n_per_chain);
 
-/* Canonical configuration of one chain, to/from host or device memory
- * (dst_is_device / src_is_device).  Ising: MC_FMT_INT8 or MC_FMT_BITS;
- * SU(2): MC_FMT_F32.  Page-locked host memory (allocated or registered through
- * CUDA) is read or written in place by the layout-conversion kernel; other host
- * memory passes through the context's staging region with a copy.
+/* Configuration of one chain, to/from host or device memory (dst_is_device /
+ * src_is_device).  Canonical formats (above): Ising MC_FMT_INT8 or MC_FMT_BITS,
+ * SU(2) MC_FMT_F32.  MC_FMT_NATIVE is the chain's storage in the context's own
+ * layout, copied as it is (one copy, no conversion kernel), for checkpoints
+ * restored into a context of the same kind and layout:
+ *   Ising, int8 layout : int8 s[y][x], as MC_FMT_INT8;
+ *   Ising, MSC32       : uint32 plane[c][y][w], c = (x + y) & 1 the colour;
+ *                        bit b of word w is the site x = 2 (32 w + b) +
+ *                        ((y + c) & 1) of row y, 1 = spin +1;
+ *   SU(2)              : float4 U[p][mu][s >> 1], p = (x0 + x1 + x2 + x3) & 1
+ *                        the parity of site s (canonical index above).
+ * For the canonical formats, page-locked host memory (allocated or registered
+ * through CUDA) is read or written in place by the layout-conversion kernel;
+ * other host memory passes through the context's staging region with a copy.
  * mc_get_config is synchronous.  mc_set_config is asynchronous on the context's
  * stream: a device or page-locked source must stay unchanged until the next
  * synchronising call; other host memory may be reused when the call returns. */

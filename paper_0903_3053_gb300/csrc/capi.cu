@@ -668,10 +668,27 @@ mc_status mc_read_series(mc_ctx *c, mc_record *dst, int64_t max_per_chain, int64
     return MC_OK;
 }
 
+// Bytes and device address of a chain's storage (the MC_FMT_NATIVE format).
+static size_t native_bytes(const mc_ctx *c, int32_t chain)
+{
+    if (c->kind == MC_KIND_SU2)
+        return su2_config_bytes(c->su2[chain]);
+    const IsingChain &ch = c->ising[chain];
+    const size_t n = (size_t)ch.Lx * ch.Ly;
+    return c->layout == MC_LAYOUT_INT8 ? n : n / 8;
+}
+
+static char *native_ptr(const mc_ctx *c, int32_t chain)
+{
+    return c->d_lattice + (c->kind == MC_KIND_SU2 ? c->su2[chain].link_off : c->ising[chain].spin_off);
+}
+
 size_t mc_config_bytes(const mc_ctx *c, int32_t chain, int32_t fmt)
 {
     if (!c || chain < 0 || chain >= c->n_chains)
         return 0;
+    if (fmt == MC_FMT_NATIVE)
+        return native_bytes(c, chain);
     if (c->kind == MC_KIND_ISING)
         return ising_config_bytes(c->ising[chain], fmt);
     return fmt == MC_FMT_F32 ? su2_config_bytes(c->su2[chain]) : 0;
@@ -698,6 +715,15 @@ static mc_status config_io(mc_ctx *c, int32_t chain, int32_t fmt, void *buf, int
         return fail(MC_EINVAL, "NULL argument");
     if (chain < 0 || chain >= c->n_chains)
         return fail(MC_EINVAL, "chain index out of range");
+    if (fmt == MC_FMT_NATIVE) { // the storage itself: one copy, no conversion
+        char *lat = native_ptr(c, chain);
+        const size_t bytes = native_bytes(c, chain);
+        cudaError_t e = to_lattice ? cudaMemcpyAsync(lat, buf, bytes, cudaMemcpyDefault, c->stream)
+                                   : cudaMemcpyAsync(buf, lat, bytes, cudaMemcpyDefault, c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(e, to_lattice ? "set native configuration" : "get native configuration");
+        return to_lattice ? MC_OK : check_device(c);
+    }
     const size_t bytes = mc_config_bytes(c, chain, fmt);
     if (bytes == 0)
         return fail(MC_EINVAL, "format not valid for this chain (Ising: MC_FMT_INT8, or MC_FMT_BITS with Lx % 32 == 0; "

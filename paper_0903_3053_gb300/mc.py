@@ -19,7 +19,7 @@ MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_ESTATE, MC_EDEVICE = 0, -
 MC_COLD, MC_HOT = 0, 1
 MC_KIND_ISING, MC_KIND_SU2 = 1, 2
 MC_LAYOUT_INT8, MC_LAYOUT_MSC32 = 0, 1
-MC_FMT_INT8, MC_FMT_BITS, MC_FMT_F32 = 0, 1, 2
+MC_FMT_INT8, MC_FMT_BITS, MC_FMT_F32, MC_FMT_NATIVE = 0, 1, 2, 3
 MC_MODE_AUTO, MC_MODE_GRID, MC_MODE_RESIDENT = 0, 1, 2
 
 #: every symbol include/mc.h declares (checked by the ABI test)
@@ -273,6 +273,13 @@ class Batch:
 
     def _shape(self, chain: int, fmt: int):
         c = self.chains[chain]
+        if fmt == MC_FMT_NATIVE:  # the context's own storage (layouts in include/mc.h)
+            if self.kind == MC_KIND_SU2:
+                return (2, 4, int(np.prod(c.L)) // 2, 4), np.float32
+            Lx, Ly = c.L[0], c.L[1]
+            if self.layout == MC_LAYOUT_INT8:
+                return (Ly, Lx), np.int8
+            return (2, Ly, Lx // 64), np.uint32
         if self.kind == MC_KIND_ISING:
             Lx, Ly = c.L[0], c.L[1]
             return ((Ly, Lx), np.int8) if fmt == MC_FMT_INT8 else ((Ly, Lx // 32), np.uint32)

@@ -152,6 +152,49 @@ def test_config_roundtrip_and_formats():
         b.close()
 
 
+def _msc_planes(s):
+    """uint32 plane[c][y][w] of the MSC32 storage, packed here from its
+    definition: bit b of word w of row y in plane c is the site x = 2 (32 w + b)
+    + ((y + c) & 1)."""
+    Ly, Lx = s.shape
+    out = np.zeros((2, Ly, Lx // 64), dtype=np.uint32)
+    for c in range(2):
+        for y in range(Ly):
+            xs = 2 * np.arange(Lx // 2) + ((y + c) & 1)
+            bits = (s[y, xs] > 0).astype(np.uint8)
+            out[c, y] = np.packbits(bits, bitorder="little").view(np.uint32)
+    return out
+
+
+def test_native_format_is_the_storage():
+    """MC_FMT_NATIVE returns the storage as documented (int8 rows; MSC32 colour
+    planes) and a native checkpoint restores a chain bit-exactly."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(6)
+    s = np.where(rng.random((64, 192)) < 0.5, 1, -1).astype(np.int8)
+    for layout, want in ((mc.MC_LAYOUT_INT8, s), (mc.MC_LAYOUT_MSC32, _msc_planes(s))):
+        c = mc.ising((192, 64), BC, seed=21)
+        b = mc.Batch([c], layout=layout)
+        assert b.config_bytes(0, mc.MC_FMT_NATIVE) == want.nbytes
+        b.set_config(0, s)
+        np.testing.assert_array_equal(b.get_config(0, mc.MC_FMT_NATIVE), want)
+        b.sweep(9)
+        ckpt, done = b.get_config(0, mc.MC_FMT_NATIVE), b.sweeps_done
+        b.sweep(11)
+        ref = b.get_config(0)
+        r = mc.Batch([c], layout=layout)
+        dev = torch.from_numpy(ckpt.copy()).cuda()
+        r.set_config_device(0, dev, mc.MC_FMT_NATIVE)
+        r.sweeps_done = done
+        r.sweep(11)
+        np.testing.assert_array_equal(r.get_config(0), ref)
+        r.set_config(0, -s)
+        r.set_config(0, want, mc.MC_FMT_NATIVE)
+        np.testing.assert_array_equal(r.get_config(0), s)
+        b.close()
+        r.close()
+
+
 def test_config_through_page_locked_host_memory():
     """Page-locked host buffers are read and written in place by the layout
     conversion kernels (no staging copy); results equal the staged path's."""

@@ -120,6 +120,26 @@ def test_config_through_page_locked_host_memory():
     b.close()
 
 
+def test_native_format_is_the_storage():
+    """MC_FMT_NATIVE is float4 U[parity][mu][s >> 1] of the canonical links."""
+    L = (4, 6, 2, 4)
+    q = _random_links(L, 8).astype(np.float32)
+    b = mc.Batch([mc.su2(L, 2.0, seed=1)])
+    b.set_config(0, q)
+    x0, x3, x2, x1 = np.meshgrid(*(np.arange(n) for n in (L[0], L[3], L[2], L[1])), indexing="ij")
+    par = ((x0 + x1 + x2 + x3) & 1).reshape(-1)  # canonical order s = x1 + L1 (x2 + L2 (x3 + L3 x0))
+    want = np.zeros((2, 4, q.shape[0] // 2, 4), dtype=np.float32)
+    for p in range(2):
+        idx = np.nonzero(par == p)[0]
+        want[p][:, idx >> 1] = q[idx].transpose(1, 0, 2)
+    got = b.get_config(0, mc.MC_FMT_NATIVE)
+    np.testing.assert_array_equal(got, want)
+    b.set_config(0, np.zeros_like(q))
+    b.set_config(0, want, mc.MC_FMT_NATIVE)
+    np.testing.assert_array_equal(b.get_config(0), q)
+    b.close()
+
+
 def test_plaquette_of_a_batch_of_shapes():
     """Several chains of different shapes in one measurement launch (per-chain
     block table of the pair kernel)."""

@@ -302,7 +302,9 @@ MC_API mc_status mc_van_train_step(mc_van *w, const int8_t *dev_spins, int32_t n
                                    double *host_loss);
 /* n autoregressive samples into device int8 [n][L][L] and their log q into
  * device doubles; sample i uses Philox key `seed`, counter (k >> 2, round,
- * TAG_SAMPLE, id_i) word k & 3 for position k, id_i = dev_ids[i] or i. */
+ * TAG_SAMPLE, id_i) word k & 3 for position k, id_i = dev_ids[i] or i.
+ * Asynchronous; a device wait of the sampler that reached its limit is
+ * reported by the next mc_van_sync (or synchronous train / MH call). */
 MC_API mc_status mc_van_sample(mc_van *w, int32_t n, uint32_t round, const uint32_t *dev_ids, int8_t *dev_out,
                                double *dev_logq);
 /* One Metropolis-Hastings round for every chain of an int8-layout Ising
@@ -313,6 +315,9 @@ MC_API mc_status mc_van_sample(mc_van *w, int32_t n, uint32_t round, const uint3
  * accepted (synchronous then).  The round counter advances by one. */
 MC_API mc_status mc_van_mh_round(mc_van *w, mc_ctx *c, int32_t *host_accepted);
 MC_API mc_status mc_van_set_round(mc_van *w, uint32_t round);
+/* Wait for the network's stream; MC_ETIMEOUT (and the latch cleared) if a
+ * bounded device wait of an earlier call on this network gave up. */
+MC_API mc_status mc_van_sync(mc_van *w);
 MC_API mc_status mc_van_destroy(mc_van *w);
 /* Copy every chain of an int8-layout Ising context (all L x L) into / from
  * (back != 0) one contiguous device buffer int8 [n_chains][L][L] (async). */

@@ -1104,108 +1104,147 @@ namespace {
 constexpr uint32_t kTagVanSample = 0x21000000u; // sampler uniforms
 constexpr uint32_t kTagVanMH = 0x22000000u;     // accept uniform and global flip
 constexpr int kSampleTile = 32;                 // samples per sampler CTA (two m16 tiles)
-constexpr int kAStride = kTapsA * kCh + 8;      // 392 bf16 per sample row of a gathered A tile (12 earlier taps)
-constexpr int kSampleMaxBufs = 3;               // gathered A tiles in flight
-constexpr size_t kSampleSmemLimit = 232448;     // 227 KB, the opt-in maximum per block
+constexpr int kTapBytes = kSampleTile * kCh * 2; // one tap of the 32 samples of a CTA: 2 KB
+constexpr int kTileBytes = kTapsA * kTapBytes;      // a gathered tile [12 taps][32 samples][32 ch]
+constexpr int kSampleMaxBufs = 3;                   // gathered hidden-layer tiles in flight
+constexpr size_t kSampleSmemLimit = 232448;         // 227 KB, the opt-in maximum per block
+constexpr int kGroupThreads = 128;                  // main warps 0-3, side warps 4-7
+constexpr int kSampleThreads = 2 * kGroupThreads + 32; // + the producer warp (gathers)
 
-// The copies of one gather: the 12 earlier-position taps x 4 chunks of 16
-// bytes of the 32 samples of a CTA, 1536 copies, 6 per thread of the
-// 256-thread sampler.  What a copy reads relative to the position and where it
-// lands do not change from step to step, so each thread keeps its 6 copies'
-// tap offsets, ring offsets and tile offsets in registers.
-constexpr int kSampleThreads = 256;
-constexpr int kGatherPerThread = kSampleTile * kTapsA * 4 / kSampleThreads;
-static_assert(kGatherPerThread * kSampleThreads == kSampleTile * kTapsA * 4, "gather copies per thread");
+// Ring arrays of the sampler, per layer [32-sample block][row % 3][x][32 samples]
+// [32 ch]: a block's five taps of one row are one contiguous run (one bulk
+// copy), and the 16-byte channel chunks of sample s are stored in the order
+// c ^ ((s >> 1) & 3), so that eight consecutive samples' rows of one chunk fall
+// on distinct shared-memory banks when a tile is read by ldmatrix.  The same
+// layout holds the layer values of the current position (Hc) and, per tap, the
+// weights (row = output channel).
+__device__ __forceinline__ int ring_elem(int s, int o) { return s * kCh + ((((o >> 3) ^ (s >> 1)) & 3) << 3) + (o & 7); }
 
-struct GatherSlots {
-    uint32_t dst[kGatherPerThread]; // byte offset in the A tile
-    int dy[kGatherPerThread], dx[kGatherPerThread];
-    size_t src[kGatherPerThread];   // element offset in a layer's ring array (sample and chunk)
-};
-
-__device__ __forceinline__ GatherSlots gather_slots(int s0, int n, size_t ring)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
-    GatherSlots g;
-#pragma unroll
-    for (int j = 0; j < kGatherPerThread; ++j) {
-        const int i = threadIdx.x + j * kSampleThreads;
-        const int s = i / (kTapsA * 4), t = (i / 4) % kTapsA, ch = i % 4, gs = s0 + s;
-        g.dst[j] = (uint32_t)(s * kAStride + t * kCh + ch * 8) * 2u;
-        g.dy[j] = gs < n ? tap_dy(t) : -4096; // a sample past the batch reads nothing (zero fill)
-        g.dx[j] = tap_dx(t);
-        g.src[j] = (size_t)(gs < n ? gs : 0) * ring + ch * 8;
-    }
-    return g;
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
-// Start one gather -- the taps of position (y, x) from the ring array h of one
-// layer into the A tile at shared address `tile` -- as one cp.async group,
-// zero-filling taps outside the lattice; the caller waits for it later.
-__device__ __forceinline__ void prefetch_taps(uint32_t tile, const bf16 *h, const GatherSlots &g, int L, int y, int x)
+// BF16 pair <-> two floats as plain bit operations (BF16 -> FP32 is exact);
+// the pack rounds to nearest even, lo in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
-#pragma unroll
-    for (int j = 0; j < kGatherPerThread; ++j) {
-        const int yy = y + g.dy[j], xx = x + g.dx[j];
-        const bool inside = yy >= 0 && xx >= 0 && xx < L;
-        const bf16 *src = inside ? h + g.src[j] + ((size_t)(yy % 3) * L + xx) * kCh : h;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(tile + g.dst[j]), "l"(src),
-                     "r"(inside ? 16 : 0)
+    uint32_t u;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(hi), "f"(lo));
+    return u;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
+
+// Named barriers of the sampler's warp groups (0 is __syncthreads).
+constexpr int kBarMain = 1, kBarSide = 2;
+__device__ __forceinline__ void group_sync(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Wait for an mbarrier phase.  A wait that gives up latches *err and sets the
+// CTA's abort flag; once the flag is set every wait returns at once, so that
+// all threads run to the end (no barrier is left short of threads) and the
+// sampled values are garbage, reported through *err.
+__device__ __forceinline__ void wait_phase(uint32_t bar, uint32_t parity, volatile int *abort, int *err)
+{
+    for (int it = 0; it < kTcMaxPolls; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
                      : "memory");
+        if (done || *abort)
+            return;
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    *abort = 1;
+    atomicExch(err, 1);
 }
 
-// Wait until at most `pending` of this thread's most recent cp.async groups are
-// still in flight (pending < kSampleMaxBufs).
-__device__ __forceinline__ void cp_async_wait_pending(int pending)
+// The tap of position k = y L + x whose position is k - 1 (the one just sampled),
+// or -1: tap 11 (dx = -1) for x > 0; for x = 0 the position k - 1 is (y - 1,
+// L - 1), a tap only when L = 2 (tap 8).  In either case no later tap of 0..11
+// is inside the lattice.
+__device__ __forceinline__ int newest_tap(int L, int y, int x) { return x > 0 ? 11 : (L == 2 && y > 0 ? 8 : -1); }
+
+// One 16 x 16 output tile of a 32 -> 32 layer for this warp (m-tile w >> 1,
+// n-tiles 2 (w & 1) + 0, 1): accumulate one tap (K = 32) from the [32][32]
+// operand at shared address `a` with the tap's weights at `wt`.
+__device__ __forceinline__ void mma_tap(float (&c0)[4], float (&c1)[4], uint32_t a, uint32_t wt, uint32_t ao0,
+                                        uint32_t ao1, uint32_t bo0, uint32_t bo1)
 {
-    if (pending <= 0)
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-    else if (pending == 1)
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else
-        asm volatile("cp.async.wait_group 2;" ::: "memory");
+    uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
+    ldsm_x4(a + ao0, a0, a1, a2, a3);
+    ldsm_x4(wt + bo0, b0, b1, b2, b3);
+    mma_bf16(c0, a0, a1, a2, a3, b0, b1);
+    mma_bf16(c1, a0, a1, a2, a3, b2, b3);
+    ldsm_x4(a + ao1, a0, a1, a2, a3);
+    ldsm_x4(wt + bo1, b0, b1, b2, b3);
+    mma_bf16(c0, a0, a1, a2, a3, b0, b1);
+    mma_bf16(c1, a0, a1, a2, a3, b2, b3);
 }
 
-// Autoregressive sampling, one position k = y L + x at a time in raster order.
-// Each CTA owns 32 samples.  At step k every layer is evaluated at position k
-// only: its 13 taps are the 12 earlier positions, read from the ring
-// hist[l][sample][row % 3][x][c] of that layer's earlier outputs (rows
-// y-2..y), and the value just computed at k (shared memory, Hc).
-// s_k = +1 iff u < sigmoid(f_k), u from Philox (k >> 2, round, TAG_SAMPLE, id)
-// word k & 3; log q accumulates log sigmoid(s_k f_k) in FP64.  The step is a
-// chain of dependent layers, so its time is latency.  The first layer reads the
-// sampled spins from a 3-row ring in shared memory.  The earlier-position taps
-// of every later layer were written in earlier steps, so their gathers do not
-// wait for the layers before them.  The G = D - 1 gathers of a step (hidden
-// layers 1..nh, then the output layer) form one sequence over all steps,
-// q = k G + g - 1, filled into `nbuf` A tiles (tile q % nbuf) by cp.async
-// groups: gather q + nbuf is issued as soon as gather q's layer has released
-// its tile, so a layer waits only for its own group, issued nbuf layers
-// earlier (possibly in the previous step).  That is safe for nbuf <= G: gather
-// g of step k + 1 reads ring g - 1 at positions <= k, and the layer writing
-// ring g - 1 at k has then already run.  Hc is double buffered, since layer l
-// reads its tap 12 from the previous layer's values while writing its own.
-__global__ void __launch_bounds__(kSampleThreads) k_sample(const bf16 *__restrict__ wh, const float *__restrict__ w1,
-                                                const float *__restrict__ wD, const float *__restrict__ bias, int D,
-                                                int L, int n, int nbuf, bf16 *hist, int8_t *out, double *logq,
-                                                PhiloxKey key, uint32_t round, const uint32_t *ids)
+// Autoregressive sampling, one position k = y L + x at a time in raster order,
+// 32 samples per CTA.  Layer l at position k sums its taps over the 12 earlier
+// positions (values of layer l - 1 from earlier steps, gathered from that
+// layer's ring array) and tap 12, the value of layer l - 1 at k itself; s_k =
+// +1 iff u < sigmoid(f_k), u from Philox (k >> 2, round, TAG_SAMPLE, id) word
+// k & 3, and log q accumulates log sigmoid(s_k f_k) in FP64.  Warp roles:
+//   * main warps 0-3 run the chain of dependent layers of step k: the first
+//     layer (its partial plus w s_{k-1}), the hidden layers on the tensor cores
+//     (a 16 x 16 output tile per warp, 26 MMA k-steps), the output layer (its
+//     partial plus tap 12) and the draw; they write each hidden value to the
+//     layer's ring array (followed by a proxy fence, for the bulk copies);
+//   * side warps 4-7 compute, off that chain, the output layer's partial sum
+//     over its 12 earlier taps for step k and the first layer's partial over
+//     its taps other than s_{k-1} for step k + 1, and accumulate log q -- in
+//     the order of one pass over all taps, so that the result is that of the
+//     plain evaluation;
+//   * a producer warp gathers, per (position, consuming layer g = 1..G, G = D -
+//     1), the 12 earlier taps of the CTA's samples from the ring array by bulk
+//     copies into one of `nbuf` tiles (taps outside the lattice copy a zero
+//     page), in the sequence q = k G + g - 1.  Main releases a hidden layer's
+//     tile after the layer; side releases the output layer's tile of step k
+//     once main has finished step k, so that every release comes after the ring
+//     stores that the gather nbuf later may read (nbuf <= G).
+// Signals between main and side are mbarriers with one completion per step:
+// E0 (first layer of step k done: its partial consumed), E1 (step k done:
+// output partial consumed, s_k drawn), R0 (first-layer partial of step k
+// written), R1 (output partial of step k written).  Every wait is bounded; one
+// that gives up latches *err and sets an abort flag after which all waits return
+// at once, so that every thread still reaches every barrier.
+__global__ void __launch_bounds__(kSampleThreads, 1) k_sample(const bf16 *__restrict__ wh, const float *__restrict__ w1,
+                                                   const float *__restrict__ wD, const float *__restrict__ bias, int D,
+                                                   int L, int n, int nbuf, bf16 *hist, const bf16 *zero, int8_t *out,
+                                                   double *logq, PhiloxKey key, uint32_t round, const uint32_t *ids,
+                                                   int *err)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int nh = D - 2, G = nh + 1; // G gathers: hidden layers 1..nh and the output layer
-    bf16 *Wh = reinterpret_cast<bf16 *>(smem);                    // [nh][13][32][40]
-    bf16 *As = Wh + (size_t)nh * kTapsB * kCh * kRowStride;       // nbuf x [32][392]
-    bf16 *Hc = As + (size_t)nbuf * kSampleTile * kAStride;         // 2 x [32][40] layer values at position k
-    float *W1 = reinterpret_cast<float *>(Hc + 2 * kSampleTile * kRowStride); // [12][32] (tap-major)
-    float *WD = W1 + kCh * kTapsA;                                 // [13][32]
-    float *Bs = WD + kTapsB * kCh;                                 // [(D-1) 32 + 1]
-    float *Fs = Bs + (D - 1) * kCh + 1;                            // [32] logits
-    int8_t *Sr = reinterpret_cast<int8_t *>(Fs + kSampleTile);     // [32][3][L] spins of rows y-2..y (row % 3)
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nh = D - 2, G = nh + 1;
+    bf16 *Ws = reinterpret_cast<bf16 *>(smem);                      // [nh][13][32 o][32 c] (ring_elem)
+    bf16 *Ts = Ws + (size_t)nh * kTapsB * kCh * kCh;                // nbuf + 1 x [12][32][32] gathered taps
+    bf16 *Hc = Ts + (size_t)(nbuf + 1) * kTapsA * kSampleTile * kCh; // [2 (layer & 1)][32][32] values at k
+    float *P0 = reinterpret_cast<float *>(Hc + (size_t)2 * kSampleTile * kCh); // [32 s][32 o] first-layer partial
+    float *Po = P0 + kSampleTile * kCh;                             // [32 s][8 parts] output partial
+    float *W1 = Po + kSampleTile * 8;                               // [12][32] (tap-major)
+    float *WD = W1 + kCh * kTapsA;                                  // [13][32]
+    float *Bs = WD + kTapsB * kCh;                                  // [(D-1) 32 + 1]
+    float *LT = Bs + (D - 1) * kCh + 1;                             // [32] s_k f_k of the last draw
+    int8_t *Sr = reinterpret_cast<int8_t *>(LT + kSampleTile);      // [32][3][L] spins of rows y-2..y
+    const uint32_t bar0 = (smem_u32(Sr + kSampleTile * 3 * L) + 7u) & ~7u;
+    const uint32_t full0 = bar0, empty0 = bar0 + 8u * (kSampleMaxBufs + 1), E0 = empty0 + 8u * (kSampleMaxBufs + 1),
+                   E1 = E0 + 8u, R0 = E0 + 16u, R1 = E0 + 24u;
+    __shared__ int abort_flag;
+    volatile int *abort = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int s0 = blockIdx.x * kSampleTile;
     for (int i = tid; i < nh * kTapsB * kCh * kCh; i += blockDim.x) {
-        const int row = i / kCh, c = i % kCh; // row = (l, t, o)
-        Wh[row * kRowStride + c] = wh[i];
+        const int row = i / kCh, c = i % kCh, o = row % kCh; // row = (l, t, o)
+        Ws[(size_t)(row - o) * kCh + ring_elem(o, c)] = wh[i];
     }
     for (int i = tid; i < kCh * kTapsA; i += blockDim.x)
         W1[(i % kTapsA) * kCh + i / kTapsA] = w1[i]; // w1 is [o][t]
@@ -1213,145 +1252,256 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(const bf16 *__restric
         WD[i] = wD[i];
     for (int i = tid; i < (D - 1) * kCh + 1; i += blockDim.x)
         Bs[i] = bias[i];
-    double lq = 0.0;     // owned by thread s (< 32): log q of positions < k - 1
-    float lq_term = 0.f; // s_{k-1} f_{k-1}, whose log sigmoid is added at step k
-    uint32_t my_id = 0;
-    if (tid < kSampleTile && s0 + tid < n)
-        my_id = ids ? ids[s0 + tid] : (uint32_t)(s0 + tid);
-    const size_t ring = (size_t)3 * L * kCh; // per sample per layer
-    const size_t abuf = (size_t)kSampleTile * kAStride;
-    const int Q = L * L * G; // gathers in all
-    const GatherSlots slots = gather_slots(s0, n, ring);
-    const uint32_t as0 = smem_u32(As);
-    // gather q = k G + g - 1 reads the ring of layer g - 1 for position k into tile q % nbuf
-    auto issue = [&](int q) {
-        if (q >= Q)
-            return;
-        const int kq = q / G, g = q - kq * G + 1, yq = kq / L;
-        prefetch_taps(as0 + (uint32_t)((q % nbuf) * abuf * 2), hist + (size_t)(g - 1) * n * ring, slots, L, yq,
-                      kq - yq * L);
-    };
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int b = 0; b <= nbuf; ++b) {
+            tc::mbar_init(full0 + 8u * b, 1);
+            tc::mbar_init(empty0 + 8u * b, 1);
+        }
+        for (int j = 0; j < 4; ++j)
+            tc::mbar_init(E0 + 8u * j, 1);
+    }
+    const int nsb = (n + kSampleTile - 1) / kSampleTile;
+    const size_t pblk = (size_t)kSampleTile * kCh;                  // ring elements per position of a block
+    const size_t lstride = (size_t)nsb * 3 * L * pblk;             // ring elements per layer
+    bf16 *ring = hist + (size_t)blockIdx.x * 3 * L * pblk;         // this CTA's block of layer 0
+    const int P = L * L, Q = P * G;
+    const uint32_t ts0 = smem_u32(Ts), ws0 = smem_u32(Ws);
     __syncthreads();
-    for (int q = 0; q < nbuf; ++q)
-        issue(q);
-    for (int k = 0; k < L * L; ++k) {
-        const int y = k / L, x = k % L, slot = y % 3;
-        if (k > 0 && tid < kSampleTile && s0 + tid < n)
-            lq += (double)log_sigmoid(lq_term);
-        // ---- layer 1 (CUDA cores): 32 samples x 32 channels, 4 channels of one sample per thread
-        {
-            const int s = tid >> 3, o0 = (tid & 7) * 4, gs = s0 + s;
-            float acc[4] = {Bs[o0], Bs[o0 + 1], Bs[o0 + 2], Bs[o0 + 3]};
-            if (gs < n)
-#pragma unroll
-                for (int t = 0; t < kTapsA; ++t) {
-                    const int yy = y + tap_dy(t), xx = x + tap_dx(t);
-                    if (yy >= 0 && xx >= 0 && xx < L) {
-                        const float v = (float)Sr[(s * 3 + yy % 3) * L + xx];
-                        const float4 w = *reinterpret_cast<const float4 *>(W1 + t * kCh + o0);
-                        acc[0] += w.x * v;
-                        acc[1] += w.y * v;
-                        acc[2] += w.z * v;
-                        acc[3] += w.w * v;
-                    }
+
+    if (warp == 8) { // ---------------------------------------------------------------- producer
+        int issued = 0;
+        for (int q = 0; q < Q; ++q) {
+            const int kq = q / G, g = q - kq * G + 1, yq = kq / L, xq = kq - yq * L;
+            // hidden-layer gathers cycle through slots 0..nbuf-1, output-layer gathers use slot nbuf
+            const int hq = kq * nh + g - 1, slot = g < G ? hq % nbuf : nbuf, use = g < G ? hq / nbuf : kq;
+            if (use > 0)
+                wait_phase(empty0 + 8u * (uint32_t)slot, (uint32_t)(use - 1) & 1u, abort, err);
+            if (*abort)
+                break;
+            const uint32_t bar = full0 + 8u * (uint32_t)slot;
+            if (lane == 0)
+                tc::mbar_arrive_expect_tx(bar, kTileBytes);
+            __syncwarp();
+            // lane 3 r + p copies part p (0 zeros left of the lattice, 1 the positions inside, 2 zeros right
+            // of it) of tap row r: rows y-2 and y-1 (taps 5 r .. 5 r + 4, dx = -2..2), row y (taps 10, 11)
+            const int r = lane / 3, part = lane - 3 * r;
+            if (r < 3) {
+                const int ntap = r < 2 ? 5 : 2, yy = yq - 2 + r, xlo = xq - 2;
+                int zl = ntap, nd = 0;
+                if (yy >= 0) {
+                    zl = xlo < 0 ? -xlo : 0;
+                    nd = ntap - zl - max(0, xlo + ntap - L);
                 }
-            const __nv_bfloat162 h01 = __floats2bfloat162_rn(fmaxf(acc[0], 0.f), fmaxf(acc[1], 0.f));
-            const __nv_bfloat162 h23 = __floats2bfloat162_rn(fmaxf(acc[2], 0.f), fmaxf(acc[3], 0.f));
-            uint2 pk;
-            pk.x = *reinterpret_cast<const uint32_t *>(&h01);
-            pk.y = *reinterpret_cast<const uint32_t *>(&h23);
-            *reinterpret_cast<uint2 *>(Hc + s * kRowStride + o0) = pk;
-            if (gs < n) // layer index 0
-                *reinterpret_cast<uint2 *>(hist + (size_t)gs * ring + ((size_t)slot * L + x) * kCh + o0) = pk;
+                const int first = part == 0 ? 0 : part == 1 ? zl : zl + nd;
+                const int cnt = part == 0 ? zl : part == 1 ? nd : ntap - zl - nd;
+                if (cnt > 0) {
+                    const bf16 *src = part == 1 ? ring + (size_t)(g - 1) * lstride + ((size_t)(yy % 3) * L + xlo + zl) * pblk
+                                                : zero;
+                    bulk_g2s(ts0 + (uint32_t)(slot * kTileBytes + (5 * r + first) * kTapBytes), src,
+                             (uint32_t)cnt * kTapBytes, bar);
+                }
+            }
+            issued = q + 1;
         }
-        // ---- hidden layers (tensor cores): M = 32 samples, N = 32, K = 13 x 32
-        for (int l = 1; l <= nh; ++l) {
-            const int q = k * G + l - 1;
-            const bf16 *At = As + (size_t)(q % nbuf) * abuf;
-            const bf16 *Hp = Hc + (size_t)((l - 1) & 1) * kSampleTile * kRowStride; // layer l - 1 at k
-            bf16 *Hn = Hc + (size_t)(l & 1) * kSampleTile * kRowStride;
-            cp_async_wait_pending(min(nbuf - 1, Q - 1 - q));
-            __syncthreads();
-            const int mt = warp >> 2, nt = warp & 3; // 8 warps: 2 m-tiles x 4 n-tiles
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            const bf16 *Wl = Wh + (size_t)(l - 1) * kTapsB * kCh * kRowStride;
-            const int arow = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
-            const int brow = nt * 8 + (lane & 7), bcol = ((lane >> 3) & 1) * 8;
-#pragma unroll 2
-            for (int kk = 0; kk < 2 * kTapsA; ++kk) {
-                uint32_t a0, a1, a2, a3, b0, b1;
-                ldsm_x4(smem_u32(At + arow * kAStride + kk * 16 + acol), a0, a1, a2, a3);
-                const int t = kk >> 1, half = kk & 1;
-                ldsm_x2(smem_u32(Wl + (t * kCh + brow) * kRowStride + half * 16 + bcol), b0, b1);
-                mma_bf16(acc, a0, a1, a2, a3, b0, b1);
+        // copies still in flight (the consumers stopped early): let them land before the CTA ends
+        if (lane == 0 && *abort) {
+            uint32_t seen = 0; // the last fill of each slot
+            for (int q = issued - 1; q >= 0 && seen != (2u << nbuf) - 1u; --q) {
+                const int kq = q / G, g = q - kq * G + 1, hq = kq * nh + g - 1;
+                const int slot = g < G ? hq % nbuf : nbuf, use = g < G ? hq / nbuf : kq;
+                if (!(seen >> slot & 1u)) {
+                    seen |= 1u << slot;
+                    tc::mbar_wait(full0 + 8u * (uint32_t)slot, (uint32_t)use & 1u, kTcMaxPolls);
+                }
             }
-#pragma unroll
-            for (int half = 0; half < 2; ++half) { // tap 12: position k itself
-                uint32_t a0, a1, a2, a3, b0, b1;
-                ldsm_x4(smem_u32(Hp + arow * kRowStride + half * 16 + acol), a0, a1, a2, a3);
-                ldsm_x2(smem_u32(Wl + (kTapsA * kCh + brow) * kRowStride + half * 16 + bcol), b0, b1);
-                mma_bf16(acc, a0, a1, a2, a3, b0, b1);
-            }
-            const int g = lane >> 2, t4 = lane & 3, o = nt * 8 + 2 * t4;
-            bf16 *hcur = hist + (size_t)l * n * ring;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int s = mt * 16 + g + 8 * h, gs = s0 + s;
-                const float bo = Bs[l * kCh + o], b1v = Bs[l * kCh + o + 1];
-                const __nv_bfloat162 v = __floats2bfloat162_rn(fmaxf(acc[2 * h] + bo, 0.f), fmaxf(acc[2 * h + 1] + b1v, 0.f));
-                *reinterpret_cast<__nv_bfloat162 *>(Hn + s * kRowStride + o) = v;
-                if (gs < n) // the ring of layer l feeds the taps of layer l + 1 (the output layer for l = nh)
-                    *reinterpret_cast<__nv_bfloat162 *>(hcur + (size_t)gs * ring + ((size_t)slot * L + x) * kCh + o) = v;
-            }
-            __syncthreads(); // every warp is done with tile At: refill it
-            issue(q + nbuf);
         }
-        // ---- output layer (CUDA cores): 8 lanes per sample, 4 channels each
-        const int qo = k * G + G - 1;
-        cp_async_wait_pending(min(nbuf - 1, Q - 1 - qo));
-        __syncthreads();
-        {
-            const bf16 *At = As + (size_t)(qo % nbuf) * abuf;
-            const bf16 *Hp = Hc + (size_t)(nh & 1) * kSampleTile * kRowStride;
-            const int s = tid >> 3, part = tid & 7, gs = s0 + s;
-            float acc = 0.f;
-            if (gs < n)
-                for (int t = 0; t < kTapsB; ++t) {
+        return;
+    }
+
+    if (warp >= 4) { // ---------------------------------------------------------------------- side
+        const int h = tid - 128, s = h >> 2, sub = h & 3;
+        double lq = 0.0; // owned by side thread s < 32
+        // the first-layer partial of position k: bias + taps 0..11 inside, except the one at k - 1
+        auto first_partial = [&](int k) {
+            const int y = k / L, x = k % L, tn = newest_tap(L, y, x), o0 = sub * 8;
+            float acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                acc[j] = Bs[o0 + j];
+#pragma unroll
+            for (int t = 0; t < kTapsA; ++t) {
+                const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+                if (t != tn && yy >= 0 && xx >= 0 && xx < L) {
+                    const float v = (float)Sr[(s * 3 + yy % 3) * L + xx];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        acc[j] = __fmaf_rn(W1[t * kCh + o0 + j], v, acc[j]);
+                }
+            }
+            *reinterpret_cast<float4 *>(P0 + s * kCh + o0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            *reinterpret_cast<float4 *>(P0 + s * kCh + o0 + 4) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        };
+        first_partial(0);
+        group_sync(kBarSide, kGroupThreads);
+        if (h == 0)
+            tc::mbar_arrive(R0);
+        for (int k = 0; k < P; ++k) {
+            const int y = k / L, x = k % L;
+            if (k > 0) {
+                wait_phase(E1, (uint32_t)(k - 1) & 1u, abort, err); // step k - 1 done
+                if (h == 0) // its output tile: every ring store of step k - 1 is in
+                    tc::mbar_arrive(empty0 + 8u * (uint32_t)nbuf);
+                if (h < kSampleTile && s0 + h < n)
+                    lq += (double)log_sigmoid(LT[h]);
+            }
+            // ---- output partial of step k: taps 0..11 inside, 8 parts of 4 channels per sample
+            wait_phase(full0 + 8u * (uint32_t)nbuf, (uint32_t)k & 1u, abort, err);
+            {
+                const bf16 *tl = Ts + (size_t)nbuf * kTapsA * kSampleTile * kCh;
+                float po0 = 0.f, po1 = 0.f;
+                for (int t = 0; t < kTapsA; ++t) {
                     const int yy = y + tap_dy(t), xx = x + tap_dx(t);
                     if (yy < 0 || xx < 0 || xx >= L)
                         continue;
-                    const bf16 *hp = (t < kTapsA ? At + s * kAStride + t * kCh : Hp + s * kRowStride) + part * 4;
-                    const uint2 hv = *reinterpret_cast<const uint2 *>(hp); // 4 channels
-                    const float2 h01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hv.x));
-                    const float2 h23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hv.y));
-                    const float4 w = *reinterpret_cast<const float4 *>(WD + t * kCh + part * 4);
-                    acc += w.x * h01.x;
-                    acc += w.y * h01.y;
-                    acc += w.z * h23.x;
-                    acc += w.w * h23.y;
+                    const bf16 *src = tl + t * kSampleTile * kCh;
+                    const uint2 hv0 = *reinterpret_cast<const uint2 *>(src + ring_elem(s, sub * 8));
+                    const uint2 hv1 = *reinterpret_cast<const uint2 *>(src + ring_elem(s, sub * 8 + 4));
+                    const float4 w0 = *reinterpret_cast<const float4 *>(WD + t * kCh + sub * 8);
+                    const float4 wv1 = *reinterpret_cast<const float4 *>(WD + t * kCh + sub * 8 + 4);
+                    po0 = __fmaf_rn(w0.x, bf16_lo(hv0.x), po0);
+                    po0 = __fmaf_rn(w0.y, bf16_hi(hv0.x), po0);
+                    po0 = __fmaf_rn(w0.z, bf16_lo(hv0.y), po0);
+                    po0 = __fmaf_rn(w0.w, bf16_hi(hv0.y), po0);
+                    po1 = __fmaf_rn(wv1.x, bf16_lo(hv1.x), po1);
+                    po1 = __fmaf_rn(wv1.y, bf16_hi(hv1.x), po1);
+                    po1 = __fmaf_rn(wv1.z, bf16_lo(hv1.y), po1);
+                    po1 = __fmaf_rn(wv1.w, bf16_hi(hv1.y), po1);
                 }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-            if (part == 0)
-                Fs[s] = acc + Bs[(D - 1) * kCh];
+                *reinterpret_cast<float2 *>(Po + s * 8 + sub * 2) = make_float2(po0, po1);
+            }
+            group_sync(kBarSide, kGroupThreads);
+            if (h == 0)
+                tc::mbar_arrive(R1);
+            // ---- first-layer partial of step k + 1 (its spins at positions <= k - 1 are drawn)
+            if (k + 1 < P) {
+                wait_phase(E0, (uint32_t)k & 1u, abort, err); // the partial of step k consumed
+                first_partial(k + 1);
+                group_sync(kBarSide, kGroupThreads);
+                if (h == 0)
+                    tc::mbar_arrive(R0);
+            }
         }
-        __syncthreads();
-        issue(qo + nbuf);
-        // ---- draw s_k
-        if (tid < kSampleTile && s0 + tid < n) {
-            const float f = Fs[tid];
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)k >> 2, round, kTagVanSample, my_id), key);
-            const uint32_t rk = (k & 2) ? ((k & 1) ? r.w : r.z) : ((k & 1) ? r.y : r.x);
-            const float sp = uniform_open0(rk) < sigmoid(f) ? 1.f : -1.f;
-            Sr[(tid * 3 + slot) * L + x] = (int8_t)sp;
-            out[((size_t)(s0 + tid) * L + y) * L + x] = (int8_t)sp;
-            lq_term = sp * f; // added to log q at the next step, off this step's tail
-        }
-        __syncthreads();
+        wait_phase(E1, (uint32_t)(P - 1) & 1u, abort, err); // the last draw
+        if (h < kSampleTile && s0 + h < n)
+            logq[s0 + h] = lq + (double)log_sigmoid(LT[h]);
+        return;
     }
-    if (tid < kSampleTile && s0 + tid < n)
-        logq[s0 + tid] = lq + (double)log_sigmoid(lq_term);
+
+    // ----------------------------------------------------------------------------------------- main
+    const int c = tid, s = c >> 2, sub = c & 3, gs = s0 + s;
+    const int mt = warp >> 1, np = warp & 1; // this warp's 16 x 16 output tile of a hidden layer
+    const int ar = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8, br = (2 * np + (lane >> 4)) * 8 + (lane & 7);
+    const uint32_t ao0 = 2u * ring_elem(ar, (lane >> 4) * 8), ao1 = 2u * ring_elem(ar, 16 + (lane >> 4) * 8);
+    const uint32_t bo0 = 2u * ring_elem(br, ((lane >> 3) & 1) * 8), bo1 = 2u * ring_elem(br, 16 + ((lane >> 3) & 1) * 8);
+    const int fg = lane >> 2, ft = lane & 3; // accumulator fragment: rows fg, fg + 8; columns 2 ft, 2 ft + 1
+    uint32_t my_id = 0;
+    if (sub == 0 && gs < n)
+        my_id = ids ? ids[gs] : (uint32_t)gs;
+    for (int k = 0; k < P; ++k) {
+        const int y = k / L, x = k % L, tn = newest_tap(L, y, x);
+        bf16 *hpos = ring + ((size_t)(y % 3) * L + x) * pblk; // position k in the ring of layer 0
+        // ---- first layer: partial + w s_{k-1}
+        wait_phase(R0, (uint32_t)k & 1u, abort, err);
+        {
+            const int o0 = sub * 8;
+            float v = 0.f;
+            if (tn >= 0)
+                v = (float)Sr[(s * 3 + (y + tap_dy(tn)) % 3) * L + x + tap_dx(tn)];
+            float a[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                a[j] = P0[s * kCh + o0 + j];
+                if (tn >= 0)
+                    a[j] = __fmaf_rn(W1[tn * kCh + o0 + j], v, a[j]);
+            }
+            const uint4 pk =
+                make_uint4(pack_bf16x2(fmaxf(a[0], 0.f), fmaxf(a[1], 0.f)), pack_bf16x2(fmaxf(a[2], 0.f), fmaxf(a[3], 0.f)),
+                           pack_bf16x2(fmaxf(a[4], 0.f), fmaxf(a[5], 0.f)), pack_bf16x2(fmaxf(a[6], 0.f), fmaxf(a[7], 0.f)));
+            *reinterpret_cast<uint4 *>(Hc + ring_elem(s, o0)) = pk;
+            *reinterpret_cast<uint4 *>(hpos + ring_elem(s, o0)) = pk;
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
+        group_sync(kBarMain, kGroupThreads);
+        if (c == 0)
+            tc::mbar_arrive(E0);
+        // ---- hidden layers (tensor cores): M = 32 samples, N = 32, K = 13 x 32
+        for (int l = 1; l <= nh; ++l) {
+            const int hq = k * nh + l - 1, slot = hq % nbuf;
+            const uint32_t tile = ts0 + (uint32_t)(slot * kTileBytes);
+            const uint32_t wl = ws0 + (uint32_t)((l - 1) * kTapsB * kCh * kCh * 2);
+            wait_phase(full0 + 8u * (uint32_t)slot, (uint32_t)(hq / nbuf) & 1u, abort, err);
+            float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+            for (int t = 0; t < kTapsA; ++t)
+                mma_tap(c0, c1, tile + (uint32_t)t * kTapBytes, wl + (uint32_t)t * kCh * kCh * 2, ao0, ao1, bo0, bo1);
+            mma_tap(c0, c1, smem_u32(Hc + (size_t)((l - 1) & 1) * kSampleTile * kCh), wl + (uint32_t)kTapsA * kCh * kCh * 2,
+                    ao0, ao1, bo0, bo1);
+            bf16 *hn = Hc + (size_t)(l & 1) * kSampleTile * kCh;
+            bf16 *hr = hpos + (size_t)l * lstride;
+            // bias, ReLU, BF16 of n-tile j's fragment (rows fg, fg + 8), to Hc and the ring
+            auto store = [&](const float(&acc)[4], int j) {
+                const int o = (2 * np + j) * 8 + 2 * ft;
+                const float bo = Bs[l * kCh + o], b1v = Bs[l * kCh + o + 1];
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int sr = mt * 16 + fg + 8 * hh;
+                    const uint32_t v = pack_bf16x2(fmaxf(acc[2 * hh] + bo, 0.f), fmaxf(acc[2 * hh + 1] + b1v, 0.f));
+                    *reinterpret_cast<uint32_t *>(hn + ring_elem(sr, o)) = v;
+                    *reinterpret_cast<uint32_t *>(hr + ring_elem(sr, o)) = v;
+                }
+            };
+            store(c0, 0);
+            store(c1, 1);
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            group_sync(kBarMain, kGroupThreads);
+            if (c == 0)
+                tc::mbar_arrive(empty0 + 8u * (uint32_t)slot);
+        }
+        // ---- output layer: partial + tap 12, then the draw
+        wait_phase(R1, (uint32_t)k & 1u, abort, err);
+        {
+            const bf16 *hp = Hc + (size_t)(nh & 1) * kSampleTile * kCh;
+            float a2[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int part = sub * 2 + j;
+                float acc = Po[s * 8 + part];
+                const uint2 hv = *reinterpret_cast<const uint2 *>(hp + ring_elem(s, part * 4));
+                const float4 w = *reinterpret_cast<const float4 *>(WD + kTapsA * kCh + part * 4);
+                acc = __fmaf_rn(w.x, bf16_lo(hv.x), acc);
+                acc = __fmaf_rn(w.y, bf16_hi(hv.x), acc);
+                acc = __fmaf_rn(w.z, bf16_lo(hv.y), acc);
+                acc = __fmaf_rn(w.w, bf16_hi(hv.y), acc);
+                a2[j] = acc;
+            }
+            float f = a2[0] + a2[1];
+            f += __shfl_xor_sync(0xffffffffu, f, 1);
+            f += __shfl_xor_sync(0xffffffffu, f, 2);
+            f += Bs[(D - 1) * kCh];
+            if (sub == 0 && gs < n) {
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)k >> 2, round, kTagVanSample, my_id), key);
+                const uint32_t rk = (k & 2) ? ((k & 1) ? r.w : r.z) : ((k & 1) ? r.y : r.x);
+                const float sp = uniform_open0(rk) < sigmoid(f) ? 1.f : -1.f;
+                Sr[(s * 3 + y % 3) * L + x] = (int8_t)sp;
+                out[((size_t)gs * L + y) * L + x] = (int8_t)sp;
+                LT[s] = sp * f;
+            }
+        }
+        group_sync(kBarMain, kGroupThreads);
+        if (c == 0)
+            tc::mbar_arrive(E1);
+    }
 }
 
 // Copy the int8 lattices of every chain of an int8-layout Ising context into
@@ -1463,8 +1613,9 @@ struct mc_van {
     long long *E1 = nullptr, *E2 = nullptr;
     int *acc = nullptr;
     bf16 *hist = nullptr;
+    const bf16 *zero = nullptr; // 5 kTapBytes of zeros
     float *dwpart = nullptr; // per-CTA partial gradients of k_dw32
-    int *err = nullptr;      // device fault latch (tensor-core completion wait gave up)
+    int *err = nullptr;      // device fault latch (a bounded completion wait gave up)
     int sms = 0;
     bool weights_ready = false;
 };
@@ -1477,8 +1628,8 @@ mc_status vfail(mc_status s, const std::string &m)
     return s;
 }
 
-// After the stream was synchronised: report (and clear) a fault a kernel
-// latched -- a tensor-core completion wait that gave up.
+// Synchronise the stream, then report (and clear) a fault a kernel latched --
+// a bounded wait for a tensor-core or bulk-copy completion that gave up.
 mc_status check_err(mc_van *w, const char *where)
 {
     int v = 0;
@@ -1489,14 +1640,14 @@ mc_status check_err(mc_van *w, const char *where)
         return vfail(MC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
     if (v != 0) {
         cudaMemsetAsync(w->err, 0, sizeof v, w->stream);
-        return vfail(MC_ETIMEOUT, std::string(where) + ": a tensor-core completion wait timed out");
+        return vfail(MC_ETIMEOUT, std::string(where) + ": a tensor-core or bulk-copy completion wait timed out");
     }
     return MC_OK;
 }
 
 struct VanLayout {
-    size_t p, m, v, g, wh, w1, wD, bias, H, dZa, dZb, f, ll, dF, spins, prop, lq, lq2, lq3, lq4, lr, E1, E2, acc, hist,
-        dwpart, err, total;
+    size_t p, m, v, g, wh, w1, wD, bias, H, dZa, dZb, f, ll, dF, spins, prop, lq, lq2, lq3, lq4, lr, E1, E2, acc, zero,
+        hist, dwpart, err, total;
 };
 
 VanLayout van_layout(int L, int nmax, int D)
@@ -1536,7 +1687,8 @@ VanLayout van_layout(int L, int nmax, int D)
     o.E1 = take((size_t)nmax * 8);
     o.E2 = take((size_t)nmax * 8);
     o.acc = take(64);
-    o.hist = take((size_t)(D - 1) * nmax * 3 * L * kCh * 2);
+    o.zero = take((size_t)5 * kTapBytes); // zeros: the sampler's taps outside the lattice
+    o.hist = take((size_t)(D - 1) * ((nmax + kSampleTile - 1) / kSampleTile) * kSampleTile * 3 * L * kCh * 2);
     o.total = off;
     return o;
 }
@@ -1550,16 +1702,19 @@ size_t dw_smem(int L)
 }
 size_t sample_smem(int D, int L, int nbuf)
 {
-    return (size_t)(D - 2) * kTapsB * kCh * kRowStride * 2 + (size_t)nbuf * kSampleTile * kAStride * 2 +
-           (size_t)2 * kSampleTile * kRowStride * 2 +
-           (size_t)(kCh * kTapsA + kTapsB * kCh + (D - 1) * kCh + 1 + 32) * 4 + (size_t)kSampleTile * 3 * L;
+    const size_t nh = (size_t)D - 2, tt = (size_t)kSampleTile * kCh;
+    return nh * kTapsB * tt * 2 + (size_t)(nbuf + 1) * kTileBytes + 2 * tt * 2 + tt * 4 + (size_t)kSampleTile * 8 * 4 +
+           (size_t)(kCh * kTapsA + kTapsB * kCh + (D - 1) * kCh + 1 + kSampleTile) * 4 + (size_t)kSampleTile * 3 * L +
+           8 * (2 * (kSampleMaxBufs + 1) + 4) + 8;
 }
 
-// Gathered A tiles the sampler keeps in flight: as many as fit, at most 3 and
-// at most the D - 1 gathers of one step.
+// Hidden-layer tiles the sampler keeps in flight (besides the output layer's
+// one): as many as fit, at most 3 and at most the D - 2 hidden layers (the
+// release of the tile nbuf gathers back must come after the ring stores that
+// a gather reads).
 int sample_bufs(int D, int L)
 {
-    for (int b = std::min(kSampleMaxBufs, D - 1); b > 1; --b)
+    for (int b = std::min(kSampleMaxBufs, D - 2); b > 1; --b)
         if (sample_smem(D, L, b) <= kSampleSmemLimit)
             return b;
     return 1;
@@ -1728,6 +1883,7 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     w->E2 = reinterpret_cast<long long *>(b + o.E2);
     w->acc = reinterpret_cast<int *>(b + o.acc);
     w->hist = reinterpret_cast<bf16 *>(b + o.hist);
+    w->zero = reinterpret_cast<const bf16 *>(b + o.zero);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1858,12 +2014,19 @@ mc_status mc_van_sample(mc_van *w, int32_t n, uint32_t round, const uint32_t *de
         const unsigned blocks = (unsigned)((n + kSampleTile - 1) / kSampleTile);
         const int nbuf = sample_bufs(w->D, w->L);
         k_sample<<<blocks, kSampleThreads, sample_smem(w->D, w->L, nbuf), w->stream>>>(w->wh, w->w1, w->wD, w->bias, w->D, w->L, n,
-                                                                      nbuf, w->hist, out, lq, w->key, round, dev_ids);
+                                                                      nbuf, w->hist, w->zero, out, lq, w->key, round, dev_ids, w->err);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess)
         return vfail(MC_ECUDA, std::string("mc_van_sample: ") + cudaGetErrorString(e));
     return MC_OK;
+}
+
+mc_status mc_van_sync(mc_van *w)
+{
+    if (!w)
+        return vfail(MC_EINVAL, "mc_van_sync: NULL network");
+    return check_err(w, "mc_van_sync");
 }
 
 mc_status mc_ising_gather(mc_ctx *c, int8_t *dev_out, int32_t back)

@@ -455,6 +455,7 @@ def _van_sigs(L):
         "mc_van_sample": (st, [P, c.c_int32, c.c_uint32, P, P, P]),
         "mc_van_mh_round": (st, [P, P, P]),
         "mc_van_set_round": (st, [P, c.c_uint32]),
+        "mc_van_sync": (st, [P]),
         "mc_van_destroy": (st, [P]),
         "mc_ising_gather": (st, [P, P, c.c_int32]),
     }
@@ -564,6 +565,11 @@ class VAN:
 
     def set_round(self, r: int):
         _check(_load_van().mc_van_set_round(self._w, int(r) & 0xFFFFFFFF))
+
+    def sync(self):
+        """Wait for the network's stream; raises if a bounded device wait of an
+        earlier call gave up."""
+        _check(_load_van().mc_van_sync(self._w))
 
     def close(self):
         if self._w:

@@ -243,14 +243,16 @@ def test_full_size_L64_sampler_log_prob_and_gradients():
 
 
 def test_sampler_prefetch_depths_and_coexisting_networks():
-    """The sampler keeps up to three gathered tap tiles in flight, as many as
-    shared memory allows: three at depth <= 6 (at depth 3 more than there are
-    gathers), two at depth 7 and L = 8, one at depth 7 and L = 96.  For each,
-    the sampler's FP64 log q equals the forward network's on what it sampled
-    and the BF16-activation oracle's on two of the samples.  The networks are
-    all created before any is sampled: creating a smaller network must not
-    shrink the shared memory a larger one launches with."""
-    cases = [(7, 96, 2), (3, 8, 64), (7, 8, 64), (6, 16, 64)]
+    """The sampler keeps up to three gathered hidden-layer tap tiles in flight
+    (besides the output layer's), as many as shared memory allows and at most
+    the D - 2 hidden layers: one at depth 3 and at depth 7 with L = 128, two at
+    depth 4 and at depth 7 with L <= 96, three at depths 5 and 6.  For each, the
+    sampler's FP64 log q equals the forward network's on what it sampled and
+    the BF16-activation oracle's on two of the samples, and no bounded device
+    wait gave up.  The networks are all created before any is sampled: creating
+    a smaller network must not shrink the shared memory a larger one launches
+    with."""
+    cases = [(7, 96, 2), (3, 8, 64), (7, 8, 64), (6, 16, 64), (7, 128, 2), (4, 8, 40)]
     nets = []
     for depth, L, n in cases:
         p = bf16_params(depth=depth, seed=20 + depth, bias=0.2)
@@ -259,6 +261,7 @@ def test_sampler_prefetch_depths_and_coexisting_networks():
         nets.append((net, p, L, n))
     for net, p, L, n in nets:
         s, lq = net.sample(n, round=5)
+        net.sync()
         lp = net.log_prob(s).cpu().numpy()
         lqs = lq.cpu().numpy()
         assert np.max(np.abs(lqs - lp) / np.abs(lp)) < 1e-5, (L, lqs[:4], lp[:4])

@@ -203,14 +203,12 @@ __device__ void run_su2(const GroupMember &m, int chain, int item, int G, int ra
                     A += part[2 * r];
                     B += part[2 * r + 1];
                 }
-                const double n = 2.0 * (double)ch.nh;
                 const unsigned long long ri = m.state->rec_head + (t + 1) / g.every - 1;
                 DevRecord *rec = &m.series[(long long)chain * m.cap + (long long)(ri % (unsigned long long)m.cap)];
                 rec->sweep = (long long)sweep;
-                rec->a = rec->b = 0;
-                rec->d0 = (double)(A + B) * kPlaqUnfix / (6.0 * n);
-                rec->d1 = (double)A * kPlaqUnfix / (3.0 * n);
-                rec->d2 = (double)B * kPlaqUnfix / (3.0 * n);
+                rec->a = (unsigned long long)A; // the exact sums; P, P_s, P_t are formed on the host
+                rec->b = (unsigned long long)B;
+                rec->d0 = rec->d1 = rec->d2 = 0.0;
             }
         }
     }

@@ -584,11 +584,13 @@ static void convert_record(const mc_ctx *c, int k, const DevRecord &r, mc_record
         o.E = 2 * (long long)r.a - 2 * n;
         o.M = 2 * (long long)r.b - n;
         o.P = o.Ps = o.Pt = 0.0;
-    } else {
+    } else { // exact fixed-point sums over the N = 2 nh sites, 3 planes each
+        const double n = 2.0 * (double)c->su2[k].nh;
+        const long long A = (long long)r.a, B = (long long)r.b;
         o.E = o.M = 0;
-        o.P = r.d0;
-        o.Ps = r.d1;
-        o.Pt = r.d2;
+        o.P = (double)(A + B) * kPlaqUnfix / (6.0 * n);
+        o.Ps = (double)A * kPlaqUnfix / (3.0 * n);
+        o.Pt = (double)B * kPlaqUnfix / (3.0 * n);
     }
 }
 

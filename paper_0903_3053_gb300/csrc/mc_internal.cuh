@@ -58,8 +58,11 @@ struct DevState {
 };
 
 // Measurement record as kept on the device.  Ising: a = anti-aligned bonds,
-// b = up spins (E = 2a - 2N, M = 2b - N are formed on the host).  SU(2): d0..d2
-// = P, P_s, P_t.
+// b = up spins (E = 2a - 2N, M = 2b - N are formed on the host).  SU(2): a, b =
+// the exact int64 fixed-point sums of the spatial and temporal plaquettes (two's
+// complement), from which the host forms P, P_s, P_t in FP64 (the device's FP64
+// pipe is narrow, and the measuring thread would hold up the next phase).
+constexpr double kPlaqUnfix = 1.0 / 536870912.0; // 2^-29, the unit of the plaquette sums
 struct DevRecord {
     long long sweep;
     unsigned long long a, b;

@@ -136,7 +136,6 @@ __global__ void __launch_bounds__(256) k_plaquette_final(const Su2Chain *chains,
         A += ss[i];
         B += st[i];
     }
-    const double n = 2.0 * (double)chains[k].nh;
     DevRecord *rec = out;
     long long sweep = (long long)(state->sweep_base + ksweep);
     if (!rec) {
@@ -146,10 +145,9 @@ __global__ void __launch_bounds__(256) k_plaquette_final(const Su2Chain *chains,
         sweep = (long long)state->sweep_base - 1;
     }
     rec->sweep = sweep;
-    rec->a = rec->b = 0;
-    rec->d0 = (double)(A + B) * kPlaqUnfix / (6.0 * n);
-    rec->d1 = (double)A * kPlaqUnfix / (3.0 * n);
-    rec->d2 = (double)B * kPlaqUnfix / (3.0 * n);
+    rec->a = (unsigned long long)A; // the exact sums; P, P_s, P_t are formed on the host
+    rec->b = (unsigned long long)B;
+    rec->d0 = rec->d1 = rec->d2 = 0.0;
 }
 
 // ------------------------------------------------------------------ Polyakov loop

@@ -417,8 +417,7 @@ __device__ __forceinline__ void su2_update_link_rt(int phase, float4 *U, const S
 // plaquettes are shared out among threads, for up to 2.8e9 sites, and it stays
 // off the GB300's FP64 pipe, which made an FP64 shuffle reduction the larger
 // part of the measurement's cost.
-constexpr float kPlaqFix = 536870912.0f; // 2^29
-constexpr double kPlaqUnfix = 1.0 / 536870912.0;
+constexpr float kPlaqFix = 536870912.0f; // 2^29 (kPlaqUnfix, its inverse, is in mc_internal.cuh)
 __device__ __forceinline__ long long plaq_fixed(float v) { return (long long)__float2int_rn(v * kPlaqFix); }
 
 __device__ __forceinline__ long long warp_sum_ll(long long v)

@@ -293,20 +293,20 @@ __global__ void __launch_bounds__(kResThreads, 1) k_su2_resident(ResidentArgs a,
                 red[2 * rank + 1] = pt;
             }
             cluster_barrier(C, cluster);
-            if (rank == 0 && threadIdx.x == 0) { // exact fixed-point sum: the grid kernels' value
+            // exact fixed-point sum, the grid kernels' value, by the last thread of rank 0: a warp that
+            // draws random numbers one pass ahead, not one of the heat-bath warps of the next pass
+            if (rank == 0 && threadIdx.x == kResThreads - 1) {
                 long long A = 0, B = 0;
                 for (int r = 0; r < C; ++r) {
                     A += st.red[2 * r];
                     B += st.red[2 * r + 1];
                 }
-                const double n = 2.0 * (double)ch.nh;
                 const unsigned long long ri = a.state->rec_head + (t + 1) / a.every - 1;
                 DevRecord *rec = &a.series[(long long)chain * a.cap + (long long)(ri % (unsigned long long)a.cap)];
                 rec->sweep = (long long)sweep;
-                rec->a = rec->b = 0;
-                rec->d0 = (double)(A + B) * kPlaqUnfix / (6.0 * n);
-                rec->d1 = (double)A * kPlaqUnfix / (3.0 * n);
-                rec->d2 = (double)B * kPlaqUnfix / (3.0 * n);
+                rec->a = (unsigned long long)A; // the exact sums; P, P_s, P_t are formed on the host
+                rec->b = (unsigned long long)B;
+                rec->d0 = rec->d1 = rec->d2 = 0.0;
             }
         }
     }

@@ -3,7 +3,8 @@
 // descriptors, the single-thread MMA issue, its completion on an mbarrier with
 // a bounded wait, and the tensor-memory load for the epilogue.
 //
-// Operand layout used throughout: K-major, no swizzle.  A matrix of R rows
+// Operand layouts: K-major, no swizzle (below; the forward convolution's
+// activations use the 64-byte swizzle instead, smem_desc_sw64).  A matrix of R rows
 // and K columns (16-bit elements) is stored as K/8 "chunk planes"; plane c
 // holds elements 8c .. 8c+7 of every row, 16 bytes per row, rows contiguous.
 // Eight consecutive rows of one plane form a core matrix (128 contiguous
@@ -23,6 +24,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes
 {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo_bytes >> 4) << 16) |
            ((uint64_t)(sbo_bytes >> 4) << 32) | (1ull << 46);
+}
+
+// The same for a K-major operand of 64-byte rows (32 16-bit elements) in the
+// 64-byte swizzle (16-byte chunk c of row r stored at chunk c ^ ((r >> 1) & 3),
+// the pattern of a TMA box with CU_TENSOR_MAP_SWIZZLE_64B on a 1024-byte
+// aligned buffer): stride offset 512 bytes (8 rows), base offset 0 -- the
+// swizzle follows the absolute shared-memory address, so a view may start at any
+// row and at the second 32-byte half of a row (K = 16..31).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) |
+           (4ull << 61);
 }
 
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,

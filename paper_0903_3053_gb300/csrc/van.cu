@@ -231,20 +231,22 @@ TcConvGeom tc_conv_geom(int L, int nplanes)
 // ---------------------------------------------------------------- TMA-pipelined forward convolution
 // out = ReLU(conv(in) + bias).  The staging is taken off the threads and the
 // three stages of an item overlap across items: warp 4 streams the
-// input rows of the next item by TMA (one box per 8-channel chunk: R + 2 rows
-// of P positions from x = -2, everything outside the lattice arriving
-// zero-filled, so the box is the padded chunk plane) into the second of two stage
-// buffers, one thread of warp 5 issues the MMAs of the current item, and warps
+// input rows of the next item by TMA (one box of all 32 channels: R + 2 rows of
+// P positions from x = -2, everything outside the lattice arriving zero-filled,
+// 64-byte rows in the 64-byte swizzle, which the MMA reads through swizzled
+// descriptors -- a tap is still an offset of whole rows) into the second of two
+// stage buffers, one thread of warp 5 issues the MMAs of the current item, and warps
 // 0-3 drain tensor memory (bias, ReLU, BF16, stores).  They hand over through
 // mbarriers: stage full (TMA bytes), stage free (MMA commit), accumulator full
 // (MMA commit) and accumulator free (epilogue arrivals); every wait is bounded
 // and a timeout latches MC_ETIMEOUT.  Every TMA destination starts on a
-// 128-byte boundary.  One CTA of 6 warps per SM.
+// 1024-byte boundary.  One CTA of 6 warps per SM.
 struct TmaConvGeom {
     int L, P, R, YB, Qpad, tiles, PL;
     uint32_t plane_bytes, stage_bytes, smem_bytes;
 };
-constexpr int kTmaGuard = 8;                   // positions ahead of staged row 0 (>= 4, multiple of 8)
+constexpr int kTmaGuard = 16;                  // positions ahead of staged row 0 (>= 2; 16 x 64 bytes = one
+                                               // 1024-byte boundary, so that the TMA box lands swizzle-aligned)
 constexpr uint32_t kTmaMaxSmem = 200u * 1024;  // two stages + weights + barriers
 constexpr uint32_t kTmaBarBytes = 128;         // 9 mbarriers, tensor-memory slot
 
@@ -260,10 +262,10 @@ TmaConvGeom tma_conv_geom(int L)
         g.P = (L + 4 + 7) / 8 * 8;
         g.R = R;
         g.Qpad = (R * g.P + 127) / 128 * 128;
-        g.PL = (kTmaGuard + 2 * g.P + g.Qpad + 7) / 8 * 8;
-        g.plane_bytes = (uint32_t)g.PL * 16;
-        g.stage_bytes = 4 * g.plane_bytes;
-        g.smem_bytes = 2 * g.stage_bytes + kTcB + kTmaBarBytes + 128; // + alignment slack
+        g.PL = (kTmaGuard + 2 * g.P + g.Qpad + 15) / 16 * 16; // whole 1024-byte swizzle spans
+        g.plane_bytes = (uint32_t)g.PL * 64;                 // 64 bytes (32 channels) per position
+        g.stage_bytes = g.plane_bytes;
+        g.smem_bytes = 2 * g.stage_bytes + kTcB + kTmaBarBytes + 1024; // + alignment slack
         g.YB = (L + R - 1) / R;
         g.tiles = g.Qpad / 128;
         if (g.smem_bytes > kTmaMaxSmem)
@@ -282,9 +284,9 @@ __global__ void __launch_bounds__(192, 1) k_conv32_tma(const __grid_constant__ C
                                                        const float *__restrict__ bias, int n, TmaConvGeom g, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // TMA destinations need 128-byte alignment: round the base up (the launch
-    // reserves 128 extra bytes)
-    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    // the stages hold 64-byte-swizzled rows: round the base up to 1024 bytes
+    // (the launch reserves 1024 extra bytes)
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sb = smem_u32(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t boff = 2 * g.stage_bytes, bars = boff + kTcB;
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(192, 1) k_conv32_tma(const __grid_constant__ C
     int ok = 1;
     if (warp == 4) {
         if (lane == 0) { // producer
-            const uint32_t bytes = (uint32_t)(g.R + 2) * 4u * (uint32_t)g.P * 16u;
+            const uint32_t bytes = (uint32_t)(g.R + 2) * (uint32_t)g.P * 64u;
             int k = 0, armed[2] = {-1, -1};
             for (int it = blockIdx.x; it < total; it += gridDim.x, ++k) {
                 const int s = k & 1;
@@ -328,9 +330,8 @@ __global__ void __launch_bounds__(192, 1) k_conv32_tma(const __grid_constant__ C
                 const int b = it / g.YB, y0 = (it - b * g.YB) * g.R;
                 tc::mbar_arrive_expect_tx(full0 + 8 * s, bytes);
                 const uint32_t st = sb + (uint32_t)s * g.stage_bytes;
-                for (int c8 = 0; c8 < 4; ++c8) // rows y0-2 .. y0+R-1, columns -2 .. P-3 of one chunk
-                    tc::tma_load_5d(st + (uint32_t)c8 * g.plane_bytes + (uint32_t)kTmaGuard * 16u, &in_map, 0, c8,
-                                    -2, y0 - 2, b, full0 + 8 * s);
+                // rows y0-2 .. y0+R-1, columns -2 .. P-3, all 32 channels: one box
+                tc::tma_load_5d(st + (uint32_t)kTmaGuard * 64u, &in_map, 0, 0, -2, y0 - 2, b, full0 + 8 * s);
                 armed[s] = k;
             }
             for (int s = 0; s < 2; ++s) // the last loads of each stage have landed before the CTA ends
@@ -343,10 +344,8 @@ __global__ void __launch_bounds__(192, 1) k_conv32_tma(const __grid_constant__ C
             uint64_t adesc[kTapsB * 2], bdesc[kTapsB * 2];
             for (int t = 0; t < kTapsB; ++t)
                 for (int kc = 0; kc < 2; ++kc) {
-                    adesc[t * 2 + kc] =
-                        tc::smem_desc(sb + (uint32_t)(2 * kc) * g.plane_bytes +
-                                          (uint32_t)(kTmaGuard + (tap_dy(t) + 2) * g.P + tap_dx(t)) * 16u,
-                                      g.plane_bytes, 128);
+                    adesc[t * 2 + kc] = tc::smem_desc_sw64(
+                        sb + (uint32_t)(kTmaGuard + (tap_dy(t) + 2) * g.P + tap_dx(t)) * 64u + (uint32_t)kc * 32u);
                     bdesc[t * 2 + kc] = tc::smem_desc(sb + boff + (uint32_t)(t * 4 + 2 * kc) * (kCh * 16), kCh * 16, 128);
                 }
             uint32_t tcount = 0;
@@ -369,7 +368,7 @@ __global__ void __launch_bounds__(192, 1) k_conv32_tma(const __grid_constant__ C
                     const int m0 = rd * kTcGroup, m1 = m0 + kTcGroup < g.tiles ? m0 + kTcGroup : g.tiles;
                     for (int m = m0; m < m1; ++m) {
                         const uint32_t d = tbase + (bb * kTcGroup + (uint32_t)(m - m0)) * kCh;
-                        const uint64_t off = soff + (uint64_t)((uint32_t)m * 128u);
+                        const uint64_t off = soff + (uint64_t)((uint32_t)m * 128u * 4u); // 128 positions x 64 B
 #pragma unroll
                         for (int j = 0; j < kTapsB * 2; ++j)
                             tc::mma_bf16(d, adesc[j] + off, bdesc[j], idesc, j != 0);
@@ -453,21 +452,21 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// Activations [n][L][L][32] BF16 as a 5-D tensor (8 channels, 4 chunks, x, y,
-// sample); one box is one 8-channel chunk of R + 2 rows, each P positions
-// wide from x = -2: it lands in shared memory as the padded rows of one chunk
-// plane, the columns outside the lattice zero-filled.
+// Activations [n][L][L][32] BF16 as a 5-D tensor (32 channels, 1, x, y,
+// sample); one box is R + 2 rows of P positions from x = -2, all channels: it
+// lands in shared memory as 64-byte rows in the 64-byte swizzle, the columns
+// outside the lattice zero-filled.
 cudaError_t activation_map(CUtensorMap *m, const bf16 *base, int n, int L, int P, int rows)
 {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc)
         return cudaErrorNotSupported;
-    const cuuint64_t dims[5] = {8, 4, (cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)n};
-    const cuuint64_t strides[4] = {16, 64, (cuuint64_t)64 * L, (cuuint64_t)64 * L * L};
-    const cuuint32_t box[5] = {8, 1, (cuuint32_t)P, (cuuint32_t)rows, 1};
+    const cuuint64_t dims[5] = {32, 1, (cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)n};
+    const cuuint64_t strides[4] = {64, 64, (cuuint64_t)64 * L, (cuuint64_t)64 * L * L};
+    const cuuint32_t box[5] = {32, 1, (cuuint32_t)P, (cuuint32_t)rows, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }

@@ -27,9 +27,9 @@
 // The arithmetic is the grid kernel's, function for function (su2_dev.cuh),
 // with the staple summed in the same order, so the links are bit-identical to
 // a grid-mode sweep.  The plaquette measurement gives each thread single
-// plaquettes (four link loads) rather than a site pair (29 loads in a
-// dependent chain); the fixed-point sums are exact, so the records equal the
-// grid kernels' too.
+// plaquettes (four link loads, two plaquettes' loads issued together) rather
+// than a site pair (29 loads in a dependent chain); the fixed-point sums are
+// exact, so the records equal the grid kernels' too.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -208,6 +208,34 @@ __device__ __forceinline__ void resident_pass_rt(int phase, float4 *U, const Su2
     }
 }
 
+// The four links of plaquette unit u (u = plane N + s, as su2_plaquette_unit),
+// in the order plaquette_value takes them; temporal: the plane contains mu = 0.
+template <int MU, int NU>
+__device__ __forceinline__ void plane_links(const float4 *U, const Su2Chain &ch, const Site &x, uint32_t s,
+                                            float4 (&q)[4])
+{
+    const int p = (x.x[0] + x.x[1] + x.x[2] + x.x[3]) & 1;
+    const uint32_t nh = ch.nh, e = s >> 1;
+    q[0] = load_link<kLdCoherent>(U, nh, p, MU, e);
+    q[1] = load_link<kLdCoherent>(U, nh, 1 - p, NU, canonical_fwd<MU>(ch, x, s) >> 1);
+    q[2] = load_link<kLdCoherent>(U, nh, p, NU, e);
+    q[3] = load_link<kLdCoherent>(U, nh, 1 - p, MU, canonical_fwd<NU>(ch, x, s) >> 1);
+}
+__device__ __forceinline__ bool unit_links(const float4 *U, const Su2Chain &ch, uint32_t u, float4 (&q)[4])
+{
+    const uint32_t n = 2u * ch.nh, plane = u / n, s = u - plane * n;
+    const Site x = site_of_canonical(ch, s);
+    switch (plane) {
+    case 0: plane_links<0, 1>(U, ch, x, s, q); break;
+    case 1: plane_links<0, 2>(U, ch, x, s, q); break;
+    case 2: plane_links<0, 3>(U, ch, x, s, q); break;
+    case 3: plane_links<1, 2>(U, ch, x, s, q); break;
+    case 4: plane_links<1, 3>(U, ch, x, s, q); break;
+    default: plane_links<2, 3>(U, ch, x, s, q); break;
+    }
+    return plane < 3;
+}
+
 __device__ __forceinline__ void block_sum2ll(long long &a, long long &b)
 {
     __shared__ long long sa[32], sb[32];
@@ -283,9 +311,23 @@ __global__ void __launch_bounds__(kResThreads, 1) k_su2_resident(ResidentArgs a,
             }
         if (a.every != 0 && ((t + 1) % a.every) == 0) {
             // one plaquette per thread step: the latency of four link loads and two products
+            // two plaquettes per thread step, the loads of both issued before either product
             long long ps = 0, pt = 0;
-            for (uint32_t u = start; u < 12u * ch.nh; u += stride)
-                su2_plaquette_unit<kLdCoherent>(U, ch, u, ps, pt);
+            const uint32_t units = 12u * ch.nh;
+            for (uint32_t u = start; u < units; u += 2 * stride) {
+                float4 qa[4], qb[4];
+                const bool ta = unit_links(U, ch, u, qa);
+                const bool two = u + stride < units;
+                bool tb = false;
+                if (two)
+                    tb = unit_links(U, ch, u + stride, qb);
+                const long long ha = plaq_fixed(plaquette_value(qa[0], qa[1], qa[2], qa[3]));
+                (ta ? pt : ps) += ha;
+                if (two) {
+                    const long long hb = plaq_fixed(plaquette_value(qb[0], qb[1], qb[2], qb[3]));
+                    (tb ? pt : ps) += hb;
+                }
+            }
             block_sum2ll(ps, pt);
             if (threadIdx.x == 0) { // into rank 0's shared memory
                 long long *red = C > 1 ? cluster.map_shared_rank(st.red, 0) : st.red;

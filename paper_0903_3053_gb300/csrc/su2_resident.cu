@@ -310,7 +310,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_su2_resident(ResidentArgs a,
                 cluster_barrier(C, cluster);
             }
         if (a.every != 0 && ((t + 1) % a.every) == 0) {
-            // one plaquette per thread step: the latency of four link loads and two products
             // two plaquettes per thread step, the loads of both issued before either product
             long long ps = 0, pt = 0;
             const uint32_t units = 12u * ch.nh;

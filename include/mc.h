@@ -133,8 +133,12 @@ MC_API mc_status mc_sweep(mc_ctx *ctx, int64_t n_sweeps, int32_t measure_every);
  * any lattice size, fastest up to ~4096 links per phase) or MC_MODE_AUTO
  * (resident for small lattices).  An SU(2) context that records heat-bath
  * tries (mc_su2_record_tries) always sweeps in grid mode.  threads_per_block
- * = 0 keeps the default (256 for Ising, 128 for SU(2), at most 256 for SU(2);
- * grid mode only).  Results are bit-identical in every mode. */
+ * = 0 keeps the default (256 for Ising, 128 for SU(2), at most 256 for SU(2)):
+ * the block size of grid mode, and for Ising resident mode the largest block,
+ * which is otherwise the largest chain's work units (int8: groups of four
+ * same-colour sites; MSC32: pairs of rows) rounded up to a warp.  The SU(2)
+ * resident kernel always runs 1024-thread CTAs.  Results are bit-identical in
+ * every mode and for every block size. */
 MC_API mc_status mc_set_mode(mc_ctx *ctx, int32_t mode, int32_t threads_per_block);
 
 /* Wait for the context's stream; report latched device faults. */

@@ -414,6 +414,24 @@ bool ising_resident_fits(const mc_ctx *c, int *smem_bytes)
     return need + 1024 <= (size_t)optin;
 }
 
+// Threads of a resident CTA: the work units of the largest chain (int8: groups
+// of four same-colour sites; MSC32: row pairs) rounded up to a warp, at most
+// the configured block size.  Threads past the last unit would idle through
+// every half-sweep and hold the SM's warp slots: a 64^2 MSC32 lattice has 32
+// row pairs, and with one-warp CTAs a batch of 4096 such chains is resident on
+// the 152 SMs in one wave (1.23e12 against 0.96e12 spin flips/s with 256-thread
+// CTAs, four waves of one working warp each).
+static int resident_threads(const mc_ctx *c)
+{
+    uint32_t units = 0;
+    for (const auto &ch : c->ising) {
+        const uint32_t u = c->layout == MC_LAYOUT_INT8 ? ((((ch.Lx * ch.Ly) >> 1) + 3) >> 2) : ch.W * (ch.Ly >> 1);
+        units = u > units ? u : units;
+    }
+    const int t = (int)((units + 31) / 32 * 32);
+    return t < 32 ? 32 : (t < c->threads ? t : c->threads);
+}
+
 // Raise the dynamic shared-memory limit of the resident kernels (outside any
 // graph capture).
 cudaError_t ising_prepare_resident(mc_ctx *c)
@@ -464,7 +482,7 @@ cudaError_t ising_sweep_enqueue(mc_ctx *c, long long n, int every, int mode)
         int smem = 0;
         if (!ising_resident_fits(c, &smem))
             return cudaErrorInvalidValue;
-        const int threads = c->threads;
+        const int threads = resident_threads(c);
         cudaError_t e = prof_begin(c);
         if (e != cudaSuccess)
             return e;

@@ -116,6 +116,30 @@ def test_block_size_invariance(threads):
     np.testing.assert_array_equal(ref[0], got2[0])
 
 
+@pytest.mark.parametrize("layout,L,threads", [
+    (mc.MC_LAYOUT_MSC32, 64, 0), (mc.MC_LAYOUT_MSC32, 64, 1024), (mc.MC_LAYOUT_INT8, 32, 0),
+    (mc.MC_LAYOUT_INT8, 32, 64),
+])
+def test_resident_small_chains_more_ctas_than_sms(layout, L, threads):
+    """Resident CTAs are sized to the chain's work (64^2 MSC32: 32 row pairs,
+    one warp; 32^2 int8: 128 site groups), capped by the block size: 400
+    chains in one launch equal grid mode chain by chain and the oracle on a
+    sample of them."""
+    chains = [mc.ising(L, 0.3 + 0.0005 * k, seed=21, chain_id=k, hot=bool(k % 2)) for k in range(400)]
+    ref, rs = run_gpu(chains, layout, 16, 4, mc.MC_MODE_GRID)
+    got, gs = run_gpu(chains, layout, 16, 4, mc.MC_MODE_RESIDENT, threads)
+    for k in range(len(chains)):
+        np.testing.assert_array_equal(got[k], ref[k])
+    np.testing.assert_array_equal(gs, rs)
+    for k in (0, 151, 399):
+        c = chains[k]
+        s = oracle.ising_init(L, 21, k, c.start == mc.MC_HOT)
+        E, M = oracle.ising_run(s, c.beta, 21, k, 0, 16)
+        np.testing.assert_array_equal(got[k], s)
+        np.testing.assert_array_equal(gs["E"][k], E[3::4])
+        np.testing.assert_array_equal(gs["M"][k], M[3::4])
+
+
 @pytest.mark.parametrize("layout", [mc.MC_LAYOUT_INT8, mc.MC_LAYOUT_MSC32])
 def test_batch_of_uneven_chains(layout):
     rng = np.random.default_rng(0)

@@ -4,8 +4,10 @@
 // a bounded wait, and the tensor-memory load for the epilogue.
 //
 // Operand layouts: K-major, no swizzle (below; the forward convolution's
-// activations use the 64-byte swizzle instead, smem_desc_sw64).  A matrix of R rows
-// and K columns (16-bit elements) is stored as K/8 "chunk planes"; plane c
+// activations use the 64-byte swizzle instead, smem_desc_sw64, and the weight
+// gradient reads its operands MN-major in that swizzle, smem_desc_mn_sw64).
+// A matrix of R rows and K columns (16-bit elements) is stored as K/8 "chunk
+// planes"; plane c
 // holds elements 8c .. 8c+7 of every row, 16 bytes per row, rows contiguous.
 // Eight consecutive rows of one plane form a core matrix (128 contiguous
 // bytes), so the descriptor's leading-dimension offset (between core matrices
@@ -38,11 +40,31 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr)
            (4ull << 61);
 }
 
+// The same swizzle for an MN-major operand (the M or N index runs along the
+// 64-byte rows, K along the rows): a 512-byte atom holds 32 elements of M or N
+// x 8 values of K; the stride offset (512 bytes) steps K by 8 and the leading
+// offset `atom_stride` steps M or N by 32.  The atoms may overlap: a stride of
+// 64 bytes makes atom a the view shifted by a rows, which is how a
+// convolution's neighbouring taps share one staged row.
+__device__ __forceinline__ uint64_t smem_desc_mn_sw64(uint32_t saddr, uint32_t atom_stride)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(atom_stride >> 4) << 16) |
+           ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major, tile M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with both operands MN-major (transpose bits 15 and 16).  With M = 64
+// the accumulator's row m lies in tensor-memory lane 32 (m / 16) + m % 16:
+// lanes 0-15 of each warp's quarter.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N)
+{
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
 // Allocate / free `ncols` tensor-memory columns (one full warp, converged).

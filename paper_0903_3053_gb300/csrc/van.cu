@@ -21,7 +21,7 @@ namespace van {
 namespace {
 
 // Per-CTA partial gradient of a hidden layer (13 x 32 x 32 weights + 32 biases)
-// and the most CTAs k_dw32 is launched with.
+// and the most CTAs k_dw32_tc is launched with.
 constexpr int kDwPart = kTapsB * kCh * kCh + kCh;
 constexpr int kMaxDwBlocks = 512;
 
@@ -871,115 +871,200 @@ __global__ void __launch_bounds__(256) k_edge_grad_reduce(const float *part, int
     }
 }
 
-// Hidden-layer weight and bias gradients on the tensor cores (dZ as a BF16
-// hi + lo pair, activations exactly as the forward used them):
-// gW[t][o][c] = sum_p dZ(p)[o] X(p + d_t)[c] -- a 32 x 32 GEMM per tap with the
-// positions as the reduction dimension.  Warp w owns taps w and w + 8.
-__global__ void __launch_bounds__(256) k_dw32(const bf16 *__restrict__ dzh, const bf16 *__restrict__ dzl,
-                                              const bf16 *__restrict__ X, float *__restrict__ part, int n, int L)
+// Weight gradient of a 32 -> 32 layer on the fifth-generation tensor cores:
+//   dW[t][o][c] = sum_(b, y, x) dz(b, y, x)[o] X(b, y + dy_t, x + dx_t)[c],
+//   db[o] = sum_(b, y, x) dz(b, y, x)[o],
+// dz as its BF16 hi + lo pair.  One item is one row (b, y): its dz hi and lo
+// rows and the input rows y-2 .. y (columns -2 .. PX-3, zero outside the
+// lattice) arrive by TMA in the 64-byte swizzle, and the positions of the row
+// are the reduction dimension K.  Both operands are read MN-major.  A = the
+// input rows, whose M dimension takes four taps at once: the taps (dy, dx ..
+// dx+3) of one kernel row are the same staged row shifted by one position,
+// i.e. 32-channel atoms 64 bytes apart (the descriptor's leading offset), and
+// taps (-2, 2), (-1, 2) are one staged row apart (M = 64).  B = dz (N = 64: 32
+// columns of hi, then 32 of lo, the lo plane one descriptor stride away).  The
+// 13 taps are four MMAs per 16 positions (M = 128, 128, 128 with one unused
+// tap, 64), accumulated in 256 tensor-memory columns over all items of the
+// CTA; tensor-memory lane (tap, c) then holds the hi and the lo sums of
+// channel c, added in the drain.  Roles: warp 4 loads (ring of NS stages),
+// warp 5 issues, warps 0-3 sum the bias gradient from the staged dz rows and
+// drain the accumulator.  Per-CTA partial sums [t][o][c] then the 32 biases,
+// reduced in CTA order by k_dw_reduce.  Two CTAs per SM, so that one's MMAs
+// fill the other's gaps.  Every wait is bounded; a timeout latches *err.
+struct DwTcGeom {
+    int L, PZ, PX, KS, NS;
+    uint32_t zbytes, xbytes, stage_bytes, smem_bytes;
+};
+constexpr uint32_t kDwTcAlloc = 256;       // tensor-memory columns: 4 tap groups x (32 hi + 32 lo)
+constexpr uint32_t kDwTcMaxSmem = 110u * 1024;
+constexpr int kDwTcMaxStages = 6;
+
+DwTcGeom dw_tc_geom(int L)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int NW = (L + 15) / 16, PX = NW * 16 + 4, PZ = NW * 16;
-    bf16 *Zs = reinterpret_cast<bf16 *>(smem); // [PZ][40] dZ hi
-    bf16 *Zl = Zs + PZ * kRowStride;           // [PZ][40] dZ lo
-    bf16 *Xs = Zl + PZ * kRowStride;           // [3][PX][40]
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ntap = warp + 8 < kTapsB ? 2 : 1;
-    float acc[2][2][4][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                acc[a][m][j][0] = acc[a][m][j][1] = acc[a][m][j][2] = acc[a][m][j][3] = 0.f;
-    float bsum = 0.f;
-    for (int item = blockIdx.x; item < n * L; item += gridDim.x) {
-        const int b = item / L, y = item % L;
-        __syncthreads();
-        for (int i = tid; i < PZ * 4; i += blockDim.x) {
-            const int xi = i / 4, ch = i % 4;
-            uint4 hi = make_uint4(0u, 0u, 0u, 0u), lo = hi;
-            if (xi < L) {
-                const size_t off = (((size_t)b * L + y) * L + xi) * kCh + ch * 8;
-                hi = *reinterpret_cast<const uint4 *>(dzh + off);
-                lo = *reinterpret_cast<const uint4 *>(dzl + off);
-            }
-            *reinterpret_cast<uint4 *>(Zs + xi * kRowStride + ch * 8) = hi;
-            *reinterpret_cast<uint4 *>(Zl + xi * kRowStride + ch * 8) = lo;
-        }
-        for (int i = tid; i < 3 * PX * 4; i += blockDim.x) {
-            const int r = i / (PX * 4), xi = (i / 4) % PX, ch = i % 4;
-            const int yy = y - 2 + r, xx = xi - 2;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (yy >= 0 && xx >= 0 && xx < L)
-                v = *reinterpret_cast<const uint4 *>(X + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8);
-            *reinterpret_cast<uint4 *>(Xs + (r * PX + xi) * kRowStride + ch * 8) = v;
-        }
-        __syncthreads();
-        for (int x = warp; x < L; x += 8) // bias: thread (warp, lane) sums channel lane over x = warp mod 8
-            bsum += bf(Zs[x * kRowStride + lane]) + bf(Zl[x * kRowStride + lane]);
-        for (int j = 0; j < NW; ++j) {
-            const int x0 = 16 * j;
-            // A = dZ^T (rows o, k = positions): 8x8 blocks (p0, o0) transposed
-            uint32_t a[2][4], al[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int i = lane >> 3;
-                const int p0 = x0 + ((i >> 1) ? 8 : 0), o0 = 16 * mt + ((i & 1) ? 8 : 0);
-                const int off = (p0 + (lane & 7)) * kRowStride + o0;
-                ldsm_x4_t(smem_u32(Zs + off), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
-                ldsm_x4_t(smem_u32(Zl + off), al[mt][0], al[mt][1], al[mt][2], al[mt][3]);
-            }
-#pragma unroll
-            for (int tt = 0; tt < 2; ++tt) {
-                if (tt >= ntap)
-                    break;
-                const int t = warp + 8 * tt, dy = tap_dy(t), dx = tap_dx(t);
-#pragma unroll
-                for (int np = 0; np < 2; ++np) {
-                    // B = X shifted (k = positions, n = channels): blocks (pos, c0) transposed
-                    const int i = lane >> 3;
-                    const int p0 = x0 + ((i & 1) ? 8 : 0), c0 = 16 * np + ((i >> 1) ? 8 : 0);
-                    uint32_t b0, b1, b2, b3;
-                    ldsm_x4_t(smem_u32(Xs + ((dy + 2) * PX + p0 + (lane & 7) + dx + 2) * kRowStride + c0), b0, b1, b2,
-                              b3);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        mma_bf16(acc[tt][mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
-                        mma_bf16(acc[tt][mt][2 * np], al[mt][0], al[mt][1], al[mt][2], al[mt][3], b0, b1);
-                        mma_bf16(acc[tt][mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
-                        mma_bf16(acc[tt][mt][2 * np + 1], al[mt][0], al[mt][1], al[mt][2], al[mt][3], b2, b3);
-                    }
-                }
-            }
-        }
-    }
-    // this CTA's partial sums, [t][o][c] then 32 bias values, reduced in fixed order by k_dw_reduce
-    float *mine = part + (size_t)blockIdx.x * kDwPart;
-    const int gq = lane >> 2, t4 = lane & 3;
-    for (int tt = 0; tt < ntap; ++tt) {
-        const int t = warp + 8 * tt;
-        for (int mt = 0; mt < 2; ++mt)
-            for (int j = 0; j < 4; ++j)
-                for (int h = 0; h < 2; ++h) {
-                    const int o = 16 * mt + gq + 8 * h, c = 8 * j + 2 * t4;
-                    *reinterpret_cast<float2 *>(mine + (t * kCh + o) * kCh + c) =
-                        make_float2(acc[tt][mt][j][2 * h], acc[tt][mt][j][2 * h + 1]);
-                }
-    }
-    __shared__ float bs[8][kCh];
-    bs[warp][lane] = bsum;
-    __syncthreads();
-    if (tid < kCh) {
-        float v = 0.f;
-        for (int w = 0; w < 8; ++w)
-            v += bs[w][tid];
-        mine[kTapsB * kCh * kCh + tid] = v;
-    }
+    DwTcGeom g{};
+    g.L = L;
+    g.PZ = (L + 15) / 16 * 16;
+    g.PX = (g.PZ + 4 + 7) / 8 * 8;
+    g.KS = g.PZ / 16;
+    g.zbytes = (uint32_t)g.PZ * 64u;
+    g.xbytes = ((uint32_t)(3 * g.PX) * 64u + 1023u) / 1024u * 1024u;
+    g.stage_bytes = 2 * g.zbytes + g.xbytes;
+    const uint32_t extra = 256 + 512 + 1024; // barriers and tensor-memory slot, bias sums, alignment slack
+    g.NS = (int)std::min<uint32_t>(kDwTcMaxStages, (kDwTcMaxSmem - extra) / g.stage_bytes);
+    g.smem_bytes = (uint32_t)g.NS * g.stage_bytes + extra;
+    return g;
 }
 
-// Sum the per-CTA partials of k_dw32 in CTA order (deterministic) into the
+__global__ void __launch_bounds__(192, 2) k_dw32_tc(const __grid_constant__ CUtensorMap zh_map,
+                                                    const __grid_constant__ CUtensorMap zl_map,
+                                                    const __grid_constant__ CUtensorMap x_map, float *__restrict__ part,
+                                                    int n, DwTcGeom g, int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const uint32_t sb = smem_u32(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NS = g.NS;
+    const uint32_t ring = (uint32_t)NS * g.stage_bytes;
+    const uint32_t full0 = sb + ring, empty0 = full0 + 8 * kDwTcMaxStages, done = empty0 + 8 * kDwTcMaxStages,
+                   tslot_off = ring + 16 * kDwTcMaxStages + 8;
+    float *bsum_s = reinterpret_cast<float *>(smem + ring + 256); // [4][32]
+    if (warp == 0)
+        tc::tmem_alloc(sb + tslot_off, kDwTcAlloc);
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            tc::mbar_init(full0 + 8 * s, 1);
+            tc::mbar_init(empty0 + 8 * s, 5); // the MMA commit and the four bias warps
+        }
+        tc::mbar_init(done, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *reinterpret_cast<volatile uint32_t *>(smem + tslot_off);
+    const int total = n * g.L;
+    int ok = 1;
+    if (warp == 4) {
+        if (lane == 0) { // producer
+            const uint32_t bytes = 2 * g.zbytes + (uint32_t)(3 * g.PX) * 64u;
+            int k = 0, armed[kDwTcMaxStages];
+            for (int s = 0; s < kDwTcMaxStages; ++s)
+                armed[s] = -1;
+            for (int it = blockIdx.x; it < total; it += gridDim.x, ++k) {
+                const int s = k % NS, use = k / NS;
+                if (use >= 1 && !tc::mbar_wait(empty0 + 8 * s, (use - 1) & 1, kTcMaxPolls)) {
+                    ok = 0;
+                    break;
+                }
+                const int b = it / g.L, y = it - b * g.L;
+                const uint32_t st = sb + (uint32_t)s * g.stage_bytes;
+                tc::mbar_arrive_expect_tx(full0 + 8 * s, bytes);
+                tc::tma_load_5d(st, &zh_map, 0, 0, 0, y, b, full0 + 8 * s);
+                tc::tma_load_5d(st + g.zbytes, &zl_map, 0, 0, 0, y, b, full0 + 8 * s);
+                tc::tma_load_5d(st + 2 * g.zbytes, &x_map, 0, 0, -2, y - 2, b, full0 + 8 * s);
+                armed[s] = use;
+            }
+            for (int s = 0; s < NS; ++s) // the last loads of each stage have landed before the CTA ends
+                if (armed[s] >= 0 && !tc::mbar_wait(full0 + 8 * s, armed[s] & 1, kTcMaxPolls))
+                    ok = 0;
+        }
+    } else if (warp == 5) {
+        if (lane == 0) { // MMA issuer
+            // tap group q: first tap (dy, dx), atom stride, M; descriptors of stage 0 at
+            // position 0, advanced by 16-byte units (1024 bytes per 16 positions)
+            const int cdy[4] = {-2, -1, 0, -2}, cdx[4] = {-2, -2, -2, 2};
+            const uint32_t clbo[4] = {64u, 64u, 64u, (uint32_t)g.PX * 64u};
+            uint64_t abase[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                abase[q] = tc::smem_desc_mn_sw64(sb + 2 * g.zbytes + (uint32_t)((cdy[q] + 2) * g.PX + cdx[q] + 2) * 64u,
+                                                 clbo[q]);
+            const uint64_t bbase = tc::smem_desc_mn_sw64(sb, g.zbytes);
+            constexpr uint32_t id128 = tc::idesc_bf16_f32_mn(128, 64), id64 = tc::idesc_bf16_f32_mn(64, 64);
+            int k = 0;
+            for (int it = blockIdx.x; ok && it < total; it += gridDim.x, ++k) {
+                const int s = k % NS, use = k / NS;
+                if (!tc::mbar_wait(full0 + 8 * s, use & 1, kTcMaxPolls)) {
+                    ok = 0;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint64_t soff = (uint64_t)(((uint32_t)s * g.stage_bytes) >> 4);
+                for (int j = 0; j < g.KS; ++j) {
+                    const uint64_t jo = soff + (uint64_t)(64 * j);
+                    const uint32_t acc = (k > 0 || j > 0) ? 1u : 0u;
+                    const uint64_t bd = bbase + jo;
+                    tc::mma_bf16(tbase, abase[0] + jo, bd, id128, acc);
+                    tc::mma_bf16(tbase + 64u, abase[1] + jo, bd, id128, acc);
+                    tc::mma_bf16(tbase + 128u, abase[2] + jo, bd, id128, acc);
+                    tc::mma_bf16(tbase + 192u, abase[3] + jo, bd, id64, acc);
+                }
+                tc::commit(empty0 + 8 * s); // stage s is free once this item's MMAs have read it
+            }
+            tc::commit(done); // every MMA issued above has completed before the drain
+        }
+    } else { // warps 0-3: bias gradient per item, then the drain
+        float bsum = 0.f;
+        int k = 0;
+        for (int it = blockIdx.x; ok && it < total; it += gridDim.x, ++k) {
+            const int s = k % NS, use = k / NS;
+            const bool got = __any_sync(0xffffffffu, tc::mbar_wait(full0 + 8 * s, use & 1, kTcMaxPolls));
+            if (!got) {
+                ok = 0;
+                break;
+            }
+            const unsigned char *zh = smem + (size_t)s * g.stage_bytes, *zl = zh + g.zbytes;
+            for (int x = warp; x < g.L; x += 4) { // channel `lane` of position x, 64-byte swizzle
+                const uint32_t off = (uint32_t)x * 64u + ((((uint32_t)lane >> 3) ^ (((uint32_t)x >> 1) & 3u)) << 4) +
+                                     ((uint32_t)lane & 7u) * 2u;
+                bsum += bf(*reinterpret_cast<const bf16 *>(zh + off)) + bf(*reinterpret_cast<const bf16 *>(zl + off));
+            }
+            __syncwarp();
+            if (lane == 0)
+                tc::mbar_arrive(empty0 + 8 * s);
+        }
+        bsum_s[warp * 32 + lane] = bsum;
+        const bool got = __any_sync(0xffffffffu, tc::mbar_wait(done, 0u, kTcMaxPolls));
+        tc::fence_after_sync();
+        if (!got)
+            ok = 0;
+        float *mine = part + (size_t)blockIdx.x * kDwPart;
+        const bool any = blockIdx.x < total;
+        // tap groups 0-2 (M = 128): lane 32 w + c holds tap w of the group, channel c;
+        // group 3 (M = 64): lanes 0-15 of warp w hold tap (w < 2 ? 4 : 9), channel 16 (w & 1) + lane
+        for (int q = 0; q < 4; ++q) {
+            float v[32], u[32];
+            const uint32_t col = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(64 * q);
+            tc::ld_32x32b_x32(col, v);
+            tc::ld_32x32b_x32(col + 32u, u);
+            int t, c;
+            if (q < 3) {
+                t = 5 * q + warp; // (dy, dx) = (q - 2, warp - 2): raster index 5 (dy + 2) + dx + 2
+                c = lane;
+                if (q == 2 && warp == 3)
+                    continue; // (0, 1) is not a tap of the mask
+            } else {
+                if (lane >= 16)
+                    continue;
+                t = warp < 2 ? 4 : 9;
+                c = 16 * (warp & 1) + lane;
+            }
+#pragma unroll
+            for (int o = 0; o < kCh; ++o)
+                mine[(t * kCh + o) * kCh + c] = any ? v[o] + u[o] : 0.f;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (tid < kCh)
+            mine[kTapsB * kCh * kCh + tid] = bsum_s[tid] + bsum_s[32 + tid] + bsum_s[64 + tid] + bsum_s[96 + tid];
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0)
+        atomicExch(err, 1);
+    tc::fence_after_sync();
+    if (warp == 0)
+        tc::tmem_free(tbase, kDwTcAlloc);
+}
+
+// Sum the per-CTA partials of k_dw32_tc in CTA order (deterministic) into the
 // canonical gradient of hidden layer `layer`.
 __global__ void k_dw_reduce(const float *__restrict__ part, int nparts, float *g, DevParams P, int layer)
 {
@@ -1613,7 +1698,7 @@ struct mc_van {
     int *acc = nullptr;
     bf16 *hist = nullptr;
     const bf16 *zero = nullptr; // 5 kTapBytes of zeros
-    float *dwpart = nullptr; // per-CTA partial gradients of k_dw32
+    float *dwpart = nullptr; // per-CTA partial gradients of k_dw32_tc
     int *err = nullptr;      // device fault latch (a bounded completion wait gave up)
     int sms = 0;
     bool weights_ready = false;
@@ -1694,11 +1779,6 @@ VanLayout van_layout(int L, int nmax, int D)
 
 unsigned grid_for(size_t n, int threads, int sms) { return (unsigned)std::min<size_t>((n + threads - 1) / threads, (size_t)sms * 16); }
 
-size_t dw_smem(int L)
-{
-    const int PZ = ((L + 15) / 16) * 16;
-    return (size_t)2 * PZ * kRowStride * 2 + (size_t)3 * (PZ + 4) * kRowStride * 2;
-}
 size_t sample_smem(int D, int L, int nbuf)
 {
     const size_t nh = (size_t)D - 2, tt = (size_t)kSampleTile * kCh;
@@ -1789,10 +1869,19 @@ cudaError_t backward(mc_van *w, int n)
     k_edge_grad_reduce<false><<<kEdgeOutD, 256, 0, w->stream>>>(w->dwpart, (int)eg, w->g, w->dp);
     const TcConvGeom tgb = tc_conv_geom(L, 8);
     const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tgb.YB, (size_t)w->sms * 2);
-    // k_dw32 holds 124 registers x 256 threads: two CTAs per SM, one wave
+    // k_dw32_tc: two CTAs per SM (256 tensor-memory columns and at most 110 KB of stages each)
+    const DwTcGeom dg = dw_tc_geom(L);
     const unsigned dwg = (unsigned)std::min<size_t>(std::min<size_t>((size_t)n * L, (size_t)w->sms * 2), kMaxDwBlocks);
     for (int l = D - 2; l >= 1; --l) { // hidden layer l: input H[l-1], output H[l], grad dz wrt its pre-activation
-        k_dw32<<<dwg, 256, dw_smem(L), w->stream>>>(dzh, dzl, w->H + (l - 1) * layer, w->dwpart, n, L);
+        CUtensorMap zh_map, zl_map, x_map;
+        e = activation_map(&zh_map, dzh, n, L, dg.PZ, 1);
+        if (e == cudaSuccess)
+            e = activation_map(&zl_map, dzl, n, L, dg.PZ, 1);
+        if (e == cudaSuccess)
+            e = activation_map(&x_map, w->H + (l - 1) * layer, n, L, dg.PX, 3);
+        if (e != cudaSuccess)
+            return e;
+        k_dw32_tc<<<dwg, 192, dg.smem_bytes, w->stream>>>(zh_map, zl_map, x_map, w->dwpart, n, dg, w->err);
         k_dw_reduce<<<(kDwPart + 255) / 256, 256, 0, w->stream>>>(w->dwpart, (int)dwg, w->g, w->dp, l);
         k_conv32_bwd_tc<<<tcg, 128, tgb.smem_bytes, w->stream>>>(dzh, dzl, nxh, nxl,
                                                                  w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh,
@@ -1892,7 +1981,7 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     if (e == cudaSuccess)
         e = raise_smem_limit((const void *)k_conv32_bwd_tc, tc_conv_geom(L, 8).smem_bytes);
     if (e == cudaSuccess)
-        e = raise_smem_limit((const void *)k_dw32, dw_smem(L));
+        e = raise_smem_limit((const void *)k_dw32_tc, dw_tc_geom(L).smem_bytes);
     if (e == cudaSuccess)
         e = raise_smem_limit((const void *)k_sample, sample_smem(depth, L, sample_bufs(depth, L)));
     if (e != cudaSuccess) {

@@ -26,7 +26,6 @@ constexpr int kTapsB = 13;      // mask B taps (mask A = first 12 of them)
 constexpr int kTapsA = 12;
 constexpr int kMaxL = 128;      // largest lattice side
 constexpr int kMaxDepth = 7;    // layers (>= 3)
-constexpr int kRowStride = 40;  // bf16 elements per position in shared memory (32 + 8: no bank conflicts)
 
 // Tap t of mask B in raster order: dy = -2..0, dx = -2..2; the last (t = 12)
 // is the centre (0, 0).
@@ -41,13 +40,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"(addr));
 }

@@ -148,6 +148,15 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst_saddr, const void *map,
                  : "memory");
 }
 
+// One FP32 column of this thread's tensor-memory lane.
+__device__ __forceinline__ float ld_32x32b_x1(uint32_t taddr)
+{
+    uint32_t r0;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r0) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r0);
+}
+
 // 32 consecutive FP32 columns of this thread's tensor-memory lane (the warp
 // reads lanes 32 (warp % 4) .. +31 starting at `taddr`).
 __device__ __forceinline__ void ld_32x32b_x32(uint32_t taddr, float (&v)[32])

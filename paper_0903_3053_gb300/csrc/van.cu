@@ -161,21 +161,6 @@ __global__ void __launch_bounds__(256) k_layer1_fwd(const int8_t *spins, int neg
     }
 }
 
-// One padded input row of a 32-channel activation (L + 4 positions, zero
-// outside the lattice) into a ring slot, by cp.async.
-__device__ __forceinline__ void stage_row_async(bf16 *slot, const bf16 *src, int b, int yy, int L)
-{
-    for (int i = threadIdx.x; i < (L + 4) * 4; i += blockDim.x) {
-        const int xx = i / 4 - 2, ch = i & 3;
-        const bool inside = yy >= 0 && yy < L && xx >= 0 && xx < L;
-        const bf16 *g = inside ? src + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8 : src;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(slot + (xx + 2) * kCh + ch * 8)),
-                     "l"(g), "r"(inside ? 16 : 0)
-                     : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
 // 32 -> 32 masked convolutions on the fifth-generation tensor cores: implicit
 // GEMMs D[q][o] = sum_{t,c} A_t[q][c] W[t][o][c] with tcgen05.mma (M = 128
 // positions, N = 32 channels, K = 16, BF16 in, FP32 accumulator in tensor
@@ -292,11 +277,27 @@ TmaConvGeom tma_conv_geom(int L)
     return two.R > 0 && 100 * t2 <= 115 * t1 ? two : one;
 }
 
-template <int MINB>
+// The last layer (32 -> 1) on the same pipeline: B has N = 16 rows (the
+// smallest tile of an M = 128 MMA), the layer's weights -- BF16 values, as
+// k_prep_weights leaves them -- in row 0 and zeros elsewhere, so that the
+// logit is f = D[p][0] + b; the epilogue forms f, log sigmoid(s f) and
+// (training) dF = -(1/n) s sigmoid(-s f) per position.
+struct LastLayerArgs {
+    const float *wD; // [t][c], BF16-representable
+    const float *bD; // the layer's bias (one value)
+    const int8_t *spins;
+    int negate;
+    float *f, *ll, *dF; // dF may be null
+    float inv_n;
+};
+
+template <int MINB, bool LAST>
 __global__ void __launch_bounds__(192, MINB) k_conv32_tma(const __grid_constant__ CUtensorMap in_map,
                                                        bf16 *__restrict__ out, const bf16 *__restrict__ W,
-                                                       const float *__restrict__ bias, int n, TmaConvGeom g, int *err)
+                                                       const float *__restrict__ bias, LastLayerArgs la, int n,
+                                                       TmaConvGeom g, int *err)
 {
+    constexpr int NB = LAST ? 16 : kCh; // output columns of the MMA
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // the stages hold 64-byte-swizzled rows: round the base up to 1024 bytes
     // (the launch reserves 1024 extra bytes)
@@ -308,10 +309,21 @@ __global__ void __launch_bounds__(192, MINB) k_conv32_tma(const __grid_constant_
                    drain = full0 + 64, tslot_off = bars + 80;
     for (uint32_t i = tid; i < 2 * g.stage_bytes / 16; i += blockDim.x) // padding columns and guards stay zero
         reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int i = tid; i < kTapsB * kCh * 4; i += blockDim.x) {
-        const int t = i / (kCh * 4), o = (i / 4) % kCh, c8 = i % 4;
-        *reinterpret_cast<uint4 *>(smem + boff + ((t * 4 + c8) * kCh + o) * 16) =
-            *reinterpret_cast<const uint4 *>(W + ((size_t)(t * kCh + o) * kCh + c8 * 8));
+    if (LAST) {
+        for (int i = tid; i < kTapsB * 4 * NB; i += blockDim.x) { // [t][c8][row]: row 0 the weights
+            const int t = i / (4 * NB), c8 = (i / NB) % 4, o = i % NB;
+            bf16 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                v[k] = __float2bfloat16(o == 0 ? la.wD[t * kCh + c8 * 8 + k] : 0.f);
+            *reinterpret_cast<uint4 *>(smem + boff + ((t * 4 + c8) * NB + o) * 16) = *reinterpret_cast<uint4 *>(v);
+        }
+    } else {
+        for (int i = tid; i < kTapsB * kCh * 4; i += blockDim.x) {
+            const int t = i / (kCh * 4), o = (i / 4) % kCh, c8 = i % 4;
+            *reinterpret_cast<uint4 *>(smem + boff + ((t * 4 + c8) * kCh + o) * 16) =
+                *reinterpret_cast<const uint4 *>(W + ((size_t)(t * kCh + o) * kCh + c8 * 8));
+        }
     }
     if (warp == 0)
         tc::tmem_alloc(sb + tslot_off, kTcCols);
@@ -354,13 +366,13 @@ __global__ void __launch_bounds__(192, MINB) k_conv32_tma(const __grid_constant_
         }
     } else if (warp == 5) {
         if (lane == 0) { // MMA issuer
-            const uint32_t idesc = tc::idesc_bf16_f32(128, kCh);
+            const uint32_t idesc = tc::idesc_bf16_f32(128, NB);
             uint64_t adesc[kTapsB * 2], bdesc[kTapsB * 2];
             for (int t = 0; t < kTapsB; ++t)
                 for (int kc = 0; kc < 2; ++kc) {
                     adesc[t * 2 + kc] = tc::smem_desc_sw64(
                         sb + (uint32_t)(kTmaGuard + (tap_dy(t) + 2) * g.P + tap_dx(t)) * 64u + (uint32_t)kc * 32u);
-                    bdesc[t * 2 + kc] = tc::smem_desc(sb + boff + (uint32_t)(t * 4 + 2 * kc) * (kCh * 16), kCh * 16, 128);
+                    bdesc[t * 2 + kc] = tc::smem_desc(sb + boff + (uint32_t)(t * 4 + 2 * kc) * (NB * 16), NB * 16, 128);
                 }
             uint32_t tcount = 0;
             int k = 0;
@@ -381,7 +393,7 @@ __global__ void __launch_bounds__(192, MINB) k_conv32_tma(const __grid_constant_
                     tc::fence_after_sync();
                     const int m0 = rd * kTcGroup, m1 = m0 + kTcGroup < g.tiles ? m0 + kTcGroup : g.tiles;
                     for (int m = m0; m < m1; ++m) {
-                        const uint32_t d = tbase + (bb * kTcGroup + (uint32_t)(m - m0)) * kCh;
+                        const uint32_t d = tbase + (bb * kTcGroup + (uint32_t)(m - m0)) * NB;
                         const uint64_t off = soff + (uint64_t)((uint32_t)m * 128u * 4u); // 128 positions x 64 B
 #pragma unroll
                         for (int j = 0; j < kTapsB * 2; ++j)
@@ -401,7 +413,8 @@ __global__ void __launch_bounds__(192, MINB) k_conv32_tma(const __grid_constant_
         float bv[kCh];
 #pragma unroll
         for (int c = 0; c < kCh; ++c)
-            bv[c] = __ldg(&bias[c]);
+            bv[c] = LAST ? 0.f : __ldg(&bias[c]);
+        const float b0 = LAST ? __ldg(la.bD) : 0.f;
         uint32_t tcount = 0;
         for (int it = blockIdx.x; ok && it < total; it += gridDim.x) {
             const int b = it / g.YB, y0 = (it - b * g.YB) * g.R;
@@ -416,10 +429,23 @@ __global__ void __launch_bounds__(192, MINB) k_conv32_tma(const __grid_constant_
                 }
                 const int m0 = rd * kTcGroup, m1 = m0 + kTcGroup < g.tiles ? m0 + kTcGroup : g.tiles;
                 for (int m = m0; m < m1; ++m) {
-                    float v[kCh];
-                    tc::ld_32x32b_x32(tbase + ((uint32_t)(32 * warp) << 16) + (bb * kTcGroup + (uint32_t)(m - m0)) * kCh,
-                                      v);
+                    const uint32_t col = tbase + ((uint32_t)(32 * warp) << 16) + (bb * kTcGroup + (uint32_t)(m - m0)) * NB;
                     const int q = m * 128 + 32 * warp + lane, r = q / g.P, xp = q - r * g.P;
+                    if (LAST) {
+                        const float acc = tc::ld_32x32b_x1(col);
+                        if (r < g.R && y0 + r < g.L && xp >= 2 && xp < g.L + 2) {
+                            const size_t p = ((size_t)b * g.L + y0 + r) * g.L + (xp - 2);
+                            const float fv = b0 + acc;
+                            const float sv = la.negate ? -(float)la.spins[p] : (float)la.spins[p];
+                            la.f[p] = fv;
+                            la.ll[p] = log_sigmoid(sv * fv);
+                            if (la.dF)
+                                la.dF[p] = -la.inv_n * sv * sigmoid(-sv * fv);
+                        }
+                        continue;
+                    }
+                    float v[kCh];
+                    tc::ld_32x32b_x32(col, v);
                     if (r < g.R && y0 + r < g.L && xp >= 2 && xp < g.L + 2) {
                         uint4 pk[4];
                         uint32_t *pw = reinterpret_cast<uint32_t *>(pk);
@@ -641,67 +667,6 @@ __device__ __forceinline__ void stage_rows3(bf16 (*H)[(kMaxL + 4) * kCh], const 
         if (yy >= 0 && xx >= 0 && xx < L)
             v = *reinterpret_cast<const uint4 *>(src + (((size_t)b * L + yy) * L + xx) * kCh + ch * 8);
         *reinterpret_cast<uint4 *>(&H[r][(xx + 2) * kCh + ch * 8]) = v;
-    }
-}
-
-// Last layer (32 -> 1, mask B): logit f, and per position log p(s_k | s_<k) =
-// log sigmoid(s f) and (training) dF = -(1/n) s sigmoid(-s f).  A CTA item is
-// a segment of rows streamed through the ring (cp.async, one row ahead); 4
-// threads per position (8 channels each), partials summed in smem.
-__global__ void __launch_bounds__(256) k_layerD_fwd(const bf16 *hD, const float *wD, const float *bD,
-                                                    const int8_t *spins, int negate, float *f, float *ll, float *dF,
-                                                    float inv_n, int n, int L)
-{
-    __shared__ __align__(16) float W[kTapsB * kCh]; // [t][c], read as float4
-    __shared__ __align__(16) bf16 H[4][(kMaxL + 4) * kCh];
-    __shared__ float part[kMaxL * 4];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kTapsB * kCh; i += blockDim.x)
-        W[i] = wD[i];
-    const float b0 = bD[0];
-    const int segs = (L + kSegRows - 1) / kSegRows;
-    for (int item = blockIdx.x; item < n * segs; item += gridDim.x) {
-        const int b = item / segs, y0 = (item - b * segs) * kSegRows, y1 = min(y0 + kSegRows, L);
-        __syncthreads(); // the previous item's readers are done with the ring
-        stage_row_async(H[(y0 - 2) & 3], hD, b, y0 - 2, L);
-        stage_row_async(H[(y0 - 1) & 3], hD, b, y0 - 1, L);
-        stage_row_async(H[y0 & 3], hD, b, y0, L);
-        for (int y = y0; y < y1; ++y) {
-            if (y + 1 < y1) { // slot (y + 1) & 3 held row y - 3: its last reader finished before the barrier below
-                stage_row_async(H[(y + 1) & 3], hD, b, y + 1, L);
-                asm volatile("cp.async.wait_group 1;" ::: "memory");
-            } else {
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
-            }
-            __syncthreads();
-            for (int j = tid; j < L * 4; j += blockDim.x) {
-                const int x = j >> 2, c0 = (j & 3) * 8;
-                float acc = 0.f;
-#pragma unroll
-                for (int t = 0; t < kTapsB; ++t) {
-                    const uint4 v =
-                        *reinterpret_cast<const uint4 *>(&H[(y + tap_dy(t)) & 3][(x + tap_dx(t) + 2) * kCh + c0]);
-                    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&v);
-                    const float4 wa = *reinterpret_cast<const float4 *>(&W[t * kCh + c0]);
-                    const float4 wb = *reinterpret_cast<const float4 *>(&W[t * kCh + c0 + 4]);
-                    const float wq[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        acc += wq[2 * q] * bf(h2[q].x) + wq[2 * q + 1] * bf(h2[q].y);
-                }
-                part[j] = acc;
-            }
-            __syncthreads();
-            for (int x = tid; x < L; x += blockDim.x) {
-                const float acc = b0 + ((part[4 * x] + part[4 * x + 1]) + (part[4 * x + 2] + part[4 * x + 3]));
-                const size_t p = ((size_t)b * L + y) * L + x;
-                const float sv = negate ? -(float)spins[p] : (float)spins[p];
-                f[p] = acc;
-                ll[p] = log_sigmoid(sv * acc);
-                if (dF)
-                    dF[p] = -inv_n * sv * sigmoid(-sv * acc);
-            }
-        }
     }
 }
 
@@ -1846,22 +1811,26 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
     k_layer1_fwd<<<segs, 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n, L);
     const TmaConvGeom tg = tma_conv_geom(L);
     const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tg.YB, (size_t)w->sms * tg.ctas_per_sm);
-    for (int l = 1; l <= D - 2; ++l) {
+    const LastLayerArgs none{};
+    const LastLayerArgs last{w->wD, w->bias + (D - 1) * kCh, w->spins, negate, w->f, w->ll, dF, 1.0f / n};
+    for (int l = 1; l <= D - 1; ++l) { // hidden layers 1 .. D-2, then the last layer
         CUtensorMap in_map;
         const cudaError_t e = activation_map(&in_map, w->H + (l - 1) * layer, n, L, tg.P, tg.R + 2);
         if (e != cudaSuccess)
             return e;
-        const bf16 *wl = w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh;
-        if (tg.ctas_per_sm == 2)
-            k_conv32_tma<2><<<tcg, 192, tg.smem_bytes, w->stream>>>(in_map, w->H + l * layer, wl, w->bias + l * kCh,
-                                                                   n, tg, w->err);
+        const bool is_last = l == D - 1;
+        bf16 *out = is_last ? nullptr : w->H + l * layer;
+        const bf16 *wl = is_last ? nullptr : w->wh + (size_t)(l - 1) * kTapsB * kCh * kCh;
+        const float *bl = is_last ? nullptr : w->bias + l * kCh;
+        if (tg.ctas_per_sm == 2 && is_last)
+            k_conv32_tma<2, true><<<tcg, 192, tg.smem_bytes, w->stream>>>(in_map, out, wl, bl, last, n, tg, w->err);
+        else if (tg.ctas_per_sm == 2)
+            k_conv32_tma<2, false><<<tcg, 192, tg.smem_bytes, w->stream>>>(in_map, out, wl, bl, none, n, tg, w->err);
+        else if (is_last)
+            k_conv32_tma<1, true><<<tcg, 192, tg.smem_bytes, w->stream>>>(in_map, out, wl, bl, last, n, tg, w->err);
         else
-            k_conv32_tma<1><<<tcg, 192, tg.smem_bytes, w->stream>>>(in_map, w->H + l * layer, wl, w->bias + l * kCh,
-                                                                   n, tg, w->err);
+            k_conv32_tma<1, false><<<tcg, 192, tg.smem_bytes, w->stream>>>(in_map, out, wl, bl, none, n, tg, w->err);
     }
-    k_layerD_fwd<<<segs, 256, 0, w->stream>>>(w->H + (D - 2) * layer, w->wD,
-                                                                    w->bias + (D - 1) * kCh, w->spins, negate, w->f,
-                                                                    w->ll, dF, 1.0f / n, n, L);
     k_logq<<<n, 256, 0, w->stream>>>(w->ll, logq, L);
     return cudaGetLastError();
 }
@@ -1995,7 +1964,12 @@ mc_status mc_van_create(mc_van **out, int32_t L, int32_t batch, int32_t depth, u
     cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(w->ws, 0, o.hist, w->stream); // params, Adam state, buffers
     if (e == cudaSuccess)
-        e = raise_smem_limit(tma_conv_geom(L).ctas_per_sm == 2 ? (const void *)k_conv32_tma<2> : (const void *)k_conv32_tma<1>,
+        e = raise_smem_limit(tma_conv_geom(L).ctas_per_sm == 2 ? (const void *)k_conv32_tma<2, false>
+                                                               : (const void *)k_conv32_tma<1, false>,
+                             tma_conv_geom(L).smem_bytes);
+    if (e == cudaSuccess)
+        e = raise_smem_limit(tma_conv_geom(L).ctas_per_sm == 2 ? (const void *)k_conv32_tma<2, true>
+                                                               : (const void *)k_conv32_tma<1, true>,
                              tma_conv_geom(L).smem_bytes);
     if (e == cudaSuccess)
         e = raise_smem_limit((const void *)k_conv32_bwd_tc, tc_conv_geom(L, 8).smem_bytes);

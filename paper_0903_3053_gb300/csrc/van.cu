@@ -89,78 +89,6 @@ __global__ void k_prep_weights(const float *p, DevParams P, bf16 *wh, float *w1,
 }
 
 // ------------------------------------------------------------------ forward
-// Rows of one sample handled by one CTA item of the edge-layer kernels: the
-// item streams its rows through a 4-slot ring in shared memory (rows y-2, y-1,
-// y and the next row, loaded while row y is computed), so every input row is
-// read once per item instead of once per output row.
-constexpr int kSegRows = 16;
-
-// Layer 1: 1 -> 32 channels, mask A, ReLU.  4 threads per position, 8 output
-// channels each; the sampled spins of the ring rows are int8 in shared memory.
-__global__ void __launch_bounds__(256) k_layer1_fwd(const int8_t *spins, int negate, const float *w1,
-                                                    const float *b1, bf16 *h1, int n, int L)
-{
-    __shared__ __align__(16) float W[kTapsA * kCh]; // [t][o], read as float4
-    __shared__ float Bs[kCh];
-    __shared__ int8_t S[4][kMaxL + 4]; // ring slot y & 3: row y, 2 zero columns each side
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kCh * kTapsA; i += blockDim.x)
-        W[(i % kTapsA) * kCh + i / kTapsA] = w1[i]; // w1 is [o][t]
-    if (tid < kCh)
-        Bs[tid] = b1[tid];
-    const int segs = (L + kSegRows - 1) / kSegRows;
-    auto fetch = [&](int b, int yy) -> int8_t { // element tid of padded row yy: the (negated) spin, 0 outside
-        const int xx = tid - 2;
-        if (tid < L + 4 && yy >= 0 && yy < L && xx >= 0 && xx < L) {
-            const int8_t v = spins[((size_t)b * L + yy) * L + xx];
-            return negate ? (int8_t)-v : v;
-        }
-        return (int8_t)0;
-    };
-    for (int item = blockIdx.x; item < n * segs; item += gridDim.x) {
-        const int b = item / segs, y0 = (item - b * segs) * kSegRows, y1 = min(y0 + kSegRows, L);
-        const int8_t r2 = fetch(b, y0 - 2), r1 = fetch(b, y0 - 1), r0 = fetch(b, y0);
-        __syncthreads(); // the previous item's readers are done with the ring
-        if (tid < L + 4) {
-            S[(y0 - 2) & 3][tid] = r2;
-            S[(y0 - 1) & 3][tid] = r1;
-            S[y0 & 3][tid] = r0;
-        }
-        for (int y = y0; y < y1; ++y) {
-            const int8_t nxt = fetch(b, y + 1); // row y + 1, in flight while row y is computed
-            __syncthreads();
-            for (int j = tid; j < L * 4; j += blockDim.x) {
-                const int x = j >> 2, o0 = (j & 3) * 8;
-                float acc[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    acc[q] = Bs[o0 + q];
-#pragma unroll
-                for (int t = 0; t < kTapsA; ++t) {
-                    const float v = (float)S[(y + tap_dy(t)) & 3][x + tap_dx(t) + 2];
-                    const float4 wa = *reinterpret_cast<const float4 *>(&W[t * kCh + o0]);
-                    const float4 wb = *reinterpret_cast<const float4 *>(&W[t * kCh + o0 + 4]);
-                    const float wq[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        acc[q] += wq[q] * v;
-                }
-                uint4 pk;
-                uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const __nv_bfloat162 h2 =
-                        __floats2bfloat162_rn(fmaxf(acc[2 * q], 0.f), fmaxf(acc[2 * q + 1], 0.f));
-                    pw[q] = *reinterpret_cast<const uint32_t *>(&h2);
-                }
-                *reinterpret_cast<uint4 *>(h1 + (((size_t)b * L + y) * L + x) * kCh + o0) = pk;
-            }
-            if (tid < L + 4) // slot (y + 1) & 3 held row y - 3, which row y does not read
-                S[(y + 1) & 3][tid] = nxt;
-        }
-    }
-}
-
 // 32 -> 32 masked convolutions on the fifth-generation tensor cores: implicit
 // GEMMs D[q][o] = sum_{t,c} A_t[q][c] W[t][o][c] with tcgen05.mma (M = 128
 // positions, N = 32 channels, K = 16, BF16 in, FP32 accumulator in tensor
@@ -211,6 +139,120 @@ TcConvGeom tc_conv_geom(int L, int nplanes)
         }
     }
     return best;
+}
+
+// Layer 1 (1 -> 32 channels, mask A, ReLU) on the fifth-generation tensor
+// cores: one MMA per tile of 128 consecutive positions (M = 128, N = 32,
+// K = 16: the 12 taps and 4 zeros).  Each thread builds its position's A row
+// from the (negated) spins -- +-1 or 0 outside the lattice, exact in BF16 --
+// into two K-major chunk planes; B holds the layer's weights (BF16 values, as
+// k_prep_weights leaves them) as [chunk][out channel] rows.  After the MMA each
+// thread reads its position's 32 accumulator columns from its tensor-memory
+// lane, adds the bias, applies ReLU and stores the 64-byte BF16 row.  Several
+// CTAs per SM overlap one another's MMA waits; every wait is bounded and a
+// timeout latches *err.
+constexpr int kL1Threads = 128;
+constexpr uint32_t kL1Cols = 32;
+
+__global__ void __launch_bounds__(kL1Threads, 8) k_layer1_tc(const int8_t *__restrict__ spins, int negate,
+                                                             const float *__restrict__ w1, const float *__restrict__ b1,
+                                                             bf16 *__restrict__ h1, int n, int L, int *err)
+{
+    __shared__ __align__(128) uint4 A[2][kL1Threads]; // chunk planes: taps 0-7, taps 8-15
+    __shared__ __align__(128) uint4 B[2][kCh];        // chunk planes: [out channel] taps 0-7, 8-15
+    __shared__ float Bias[kCh];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid < kCh)
+        Bias[tid] = b1[tid];
+    if (tid < 2 * kCh) { // w1 is [o][t]
+        const int pl = tid / kCh, o = tid % kCh;
+        bf16 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int t = 8 * pl + k;
+            v[k] = __float2bfloat16(t < kTapsA ? w1[o * kTapsA + t] : 0.f);
+        }
+        B[pl][o] = *reinterpret_cast<uint4 *>(v);
+    }
+    const uint32_t bar_s = smem_u32(&bar);
+    if (warp == 0)
+        tc::tmem_alloc(smem_u32(&tslot), kL1Cols);
+    if (tid == 0)
+        tc::mbar_init(bar_s, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *reinterpret_cast<volatile uint32_t *>(&tslot);
+    const uint64_t adesc = tc::smem_desc(smem_u32(&A[0][0]), kL1Threads * 16, 128);
+    const uint64_t bdesc = tc::smem_desc(smem_u32(&B[0][0]), kCh * 16, 128);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kCh);
+    const long long total = (long long)n * L * L, tiles = (total + kL1Threads - 1) / kL1Threads;
+    int ok = 1;
+    uint32_t uses = 0;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++uses) {
+        const long long p = tile * kL1Threads + tid;
+        const bool live = p < total;
+        int b = 0, y = 0, x = 0;
+        if (live) {
+            b = (int)(p / ((long long)L * L));
+            const int r = (int)(p - (long long)b * L * L);
+            y = r / L;
+            x = r - y * L;
+        }
+        bf16 a[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            float v = 0.f;
+            if (t < kTapsA && live) {
+                const int yy = y + tap_dy(t), xx = x + tap_dx(t);
+                if (yy >= 0 && xx >= 0 && xx < L) {
+                    const int s = spins[((size_t)b * L + yy) * L + xx];
+                    v = (float)(negate ? -s : s);
+                }
+            }
+            a[t] = __float2bfloat16(v);
+        }
+        A[0][tid] = *reinterpret_cast<uint4 *>(&a[0]);
+        A[1][tid] = *reinterpret_cast<uint4 *>(&a[8]);
+        tc::fence_smem_for_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            tc::mma_bf16(tbase, adesc, bdesc, idesc, 0u);
+            tc::commit(bar_s);
+        }
+        if (!__syncthreads_and(tc::mbar_wait(bar_s, uses & 1u, kTcMaxPolls))) { // block-uniform
+            ok = 0;
+            break;
+        }
+        tc::fence_after_sync();
+        float v[kCh];
+        tc::ld_32x32b_x32(tbase + ((uint32_t)(32 * warp) << 16), v);
+        if (live) {
+            uint4 pk[4];
+            uint32_t *pw = reinterpret_cast<uint32_t *>(pk);
+#pragma unroll
+            for (int c = 0; c < kCh; c += 2) {
+                const __nv_bfloat162 h =
+                    __floats2bfloat162_rn(fmaxf(v[c] + Bias[c], 0.f), fmaxf(v[c + 1] + Bias[c + 1], 0.f));
+                pw[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(h1 + (size_t)p * kCh);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                dst[k] = pk[k];
+        }
+        tc::fence_before_sync(); // this tile's tensor-memory reads precede the next MMA
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0)
+        atomicExch(err, 1);
+    tc::fence_after_sync();
+    if (warp == 0)
+        tc::tmem_free(tbase, kL1Cols);
 }
 
 // ---------------------------------------------------------------- TMA-pipelined forward convolution
@@ -1807,8 +1849,9 @@ cudaError_t forward(mc_van *w, int n, int negate, double *logq, float *dF)
     }
     const int L = w->L, D = w->D;
     const size_t layer = (size_t)w->nmax * L * L * kCh;
-    const unsigned segs = (unsigned)std::min<size_t>((size_t)n * ((L + kSegRows - 1) / kSegRows), (size_t)w->sms * 8);
-    k_layer1_fwd<<<segs, 256, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n, L);
+    const unsigned l1g =
+        (unsigned)std::min<long long>(((long long)n * L * L + kL1Threads - 1) / kL1Threads, (long long)w->sms * 8);
+    k_layer1_tc<<<l1g, kL1Threads, 0, w->stream>>>(w->spins, negate, w->w1, w->bias, w->H, n, L, w->err);
     const TmaConvGeom tg = tma_conv_geom(L);
     const unsigned tcg = (unsigned)std::min<size_t>((size_t)n * tg.YB, (size_t)w->sms * tg.ctas_per_sm);
     const LastLayerArgs none{};

@@ -377,6 +377,16 @@ def test_full_size_L64_forward_and_gradients_per_element():
     _grad_check(64, 8, 34)
 
 
+@pytest.mark.parametrize("L,n,seed", [(2, 16, 66), (128, 1, 74)])
+def test_extreme_sides_forward_and_gradients_per_element(L, n, seed):
+    """The same at the smallest and the largest lattice side, where the
+    tensor-core kernels' geometry changes: one padded row tile and a single
+    16-position K step at L = 2; at L = 128 the forward convolution runs one
+    CTA per SM (two would cost too many tiles) and the weight gradient's ring
+    holds only two stages."""
+    _grad_check(L, n, seed)
+
+
 def _sampler_uniforms(seed, rnd, n, L):
     return van.sampler_uniforms(seed, rnd, range(n), L)
 

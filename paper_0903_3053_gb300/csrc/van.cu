@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(128, 2) k_conv32_bwd_tc(const bf16 *__restrict
                                                           const bf16 *__restrict__ W, const bf16 *__restrict__ mask,
                                                           int n, TcConvGeom g, int *err)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t sb = smem_u32(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t abytes = 8 * g.plane_bytes; // planes 0-3: hi, 4-7: lo

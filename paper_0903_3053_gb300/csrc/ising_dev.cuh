@@ -79,12 +79,12 @@ __device__ __forceinline__ void int8_group(int8_t *s, const IsingChain &ch, cons
 // site accepted) is fixed up by the caller.
 __device__ __forceinline__ void ge_chain2(uint32_t &g2, uint32_t &g4, uint32_t r, uint32_t nT2, uint32_t nT4)
 {
-    uint32_t t;
-    asm("add.cc.u32 %2, %3, %4;\n\t"
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %2, %3;\n\t"
         "addc.u32 %0, %0, %0;\n\t"
-        "add.cc.u32 %2, %3, %5;\n\t"
-        "addc.u32 %1, %1, %1;"
-        : "+r"(g2), "+r"(g4), "=&r"(t)
+        "add.cc.u32 t, %2, %4;\n\t"
+        "addc.u32 %1, %1, %1;\n\t}"
+        : "+r"(g2), "+r"(g4)
         : "r"(r), "r"(nT2), "r"(nT4));
 }
 

@@ -80,9 +80,11 @@ __device__ __forceinline__ void latch_error(DevState *st, int code, int info)
 }
 
 // Lattice load policy.  Kernels that never read a location written during the
-// same launch use the read-only path (kLdReadOnly); the persistent batch
-// kernel, whose later phases read what earlier phases (possibly on other SMs
-// of the cluster) wrote, loads through L2, the device's point of coherence.
+// same launch use the read-only path (kLdReadOnly).  Kernels whose later phases
+// read what earlier phases wrote (possibly on other SMs of the cluster) either
+// load through L2, the device's point of coherence (kLdCoherent: the SU(2)
+// resident kernel, where L1-cacheable loads measured no faster), or use plain
+// loads ordered by the barrier's acquire (kLdPlain: the batch kernel).
 constexpr int kLdReadOnly = 0, kLdPlain = 1, kLdCoherent = 2;
 
 // Threads per block of the SU(2) plaquette measurement; each thread measures

@@ -9,10 +9,12 @@
 // layers 2..D-1 are 5x5 convolutions 32 -> 32 with mask B (mask A plus the
 // centre), each followed by bias and ReLU; layer D is 5x5, 32 -> 1, mask B,
 // giving the logit f_k with p(s_k = +1 | s_<k) = sigmoid(f_k).
-// Activations are BF16, channels innermost ([n][y][x][32]); the 32 -> 32
-// layers run on the tensor cores (forward: tcgen05.mma with a tensor-memory
-// accumulator; gradients and the sampler's 32-sample tiles: mma.sync
-// m16n8k16), BF16 in, FP32 accumulate; log q is accumulated in FP64.
+// Activations are BF16, channels innermost ([n][y][x][32]).  Every layer of
+// the forward pass and the 32 -> 32 layers' data and weight gradients run on
+// the fifth-generation tensor cores (tcgen05.mma with a tensor-memory
+// accumulator); the sampler's per-position 32-sample tiles use mma.sync
+// m16n8k16 (M = 32 is below a tcgen05 tile); BF16 in, FP32 accumulate; log q
+// is accumulated in FP64.  The edge layers' gradients run on the CUDA cores.
 #pragma once
 #include <cuda_bf16.h>
 

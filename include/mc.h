@@ -134,10 +134,11 @@ MC_API mc_status mc_sweep(mc_ctx *ctx, int64_t n_sweeps, int32_t measure_every);
  * (resident for small lattices).  An SU(2) context that records heat-bath
  * tries (mc_su2_record_tries) always sweeps in grid mode.  threads_per_block
  * = 0 keeps the default (256 for Ising, 128 for SU(2), at most 256 for SU(2)):
- * the block size of grid mode, and for Ising resident mode the largest block,
- * which is otherwise the largest chain's work units (int8: groups of four
- * same-colour sites; MSC32: pairs of rows) rounded up to a warp.  The SU(2)
- * resident kernel always runs 1024-thread CTAs.  Results are bit-identical in
+ * the block size of grid mode, and for Ising resident mode the largest block.
+ * Without one, an Ising resident CTA has the largest chain's work units (int8:
+ * groups of four same-colour sites; MSC32: pairs of rows) rounded up to a
+ * warp, at most 1024 threads when no more chains than SMs share the GPU and at
+ * most 256 otherwise.  The SU(2) resident kernel always runs 1024-thread CTAs.  Results are bit-identical in
  * every mode and for every block size. */
 MC_API mc_status mc_set_mode(mc_ctx *ctx, int32_t mode, int32_t threads_per_block);
 

@@ -520,6 +520,8 @@ mc_status mc_set_mode(mc_ctx *c, int32_t mode, int32_t threads_per_block)
             return fail(MC_EINVAL, "threads_per_block must be a multiple of 32 in [32, " + std::to_string(maxt) + "]");
     }
     c->mode = mode;
+    if (threads_per_block != 0)
+        c->threads_set = true;
     if (threads_per_block != 0 && threads_per_block != c->threads) {
         c->threads = threads_per_block;
         mc_status s = upload_tables(c);

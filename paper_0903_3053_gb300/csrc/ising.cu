@@ -416,11 +416,15 @@ bool ising_resident_fits(const mc_ctx *c, int *smem_bytes)
 
 // Threads of a resident CTA: the work units of the largest chain (int8: groups
 // of four same-colour sites; MSC32: row pairs) rounded up to a warp, at most
-// the configured block size.  Threads past the last unit would idle through
-// every half-sweep and hold the SM's warp slots: a 64^2 MSC32 lattice has 32
-// row pairs, and with one-warp CTAs a batch of 4096 such chains is resident on
-// the 152 SMs in one wave (1.23e12 against 0.96e12 spin flips/s with 256-thread
-// CTAs, four waves of one working warp each).
+// the block size -- the caller's (mc_set_mode), else 1024 when every chain has
+// an SM to itself and the default (256) when chains share SMs.  Threads past
+// the last unit would idle through every half-sweep and hold the SM's warp
+// slots: a 64^2 MSC32 lattice has 32 row pairs, and with one-warp CTAs a batch
+// of 4096 such chains is resident on the 152 SMs in one wave (1.23e12 against
+// 0.96e12 spin flips/s with 256-thread CTAs, four waves of one working warp
+// each).  With a CTA per SM to spare, more threads shorten each half-sweep:
+// one 64^2 int8 chain 2.44 against 2.99 us per sweep with 512 threads, one
+// 256^2 MSC32 chain 7.8 against 9.2 us.
 static int resident_threads(const mc_ctx *c)
 {
     uint32_t units = 0;
@@ -428,8 +432,12 @@ static int resident_threads(const mc_ctx *c)
         const uint32_t u = c->layout == MC_LAYOUT_INT8 ? ((((ch.Lx * ch.Ly) >> 1) + 3) >> 2) : ch.W * (ch.Ly >> 1);
         units = u > units ? u : units;
     }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int cap = c->threads_set || c->n_chains > sms ? c->threads : 1024;
     const int t = (int)((units + 31) / 32 * 32);
-    return t < 32 ? 32 : (t < c->threads ? t : c->threads);
+    return t < 32 ? 32 : (t < cap ? t : cap);
 }
 
 // Raise the dynamic shared-memory limit of the resident kernels (outside any

@@ -175,6 +175,7 @@ struct mc_ctx {
     long long rec_written = 0, rec_read = 0;
     int mode = MC_MODE_AUTO;
     int threads = mc::kDefaultThreads;
+    bool threads_set = false;            // threads chosen by the caller (mc_set_mode), not the default
     bool record_tries = false;
     int n_or = 0;                        // SU(2): overrelaxation sweeps after each heat-bath sweep
     int su2_res_cluster = 0;             // SU(2) resident mode: CTAs per chain (0 = not prepared)
